@@ -1,0 +1,208 @@
+/* gapla.h - C ABI of the GB300 (sm_103a) layer-assignment library.
+ *
+ * What it computes (arxiv 2507.13375, GAP-LA):
+ *   Layer assignment takes a GCell grid with per-layer edge capacities and a
+ *   2D GCell routing tree per net, and gives every straight 2D segment a metal
+ *   layer of its direction, keeping the planar projection (Sec. II-B, II-D).
+ *   One round = the bottom-up tree DP of Alg. 3 with the look-ahead cost of
+ *   Sec. III-D, the top-down backtrack of Alg. 4, and the demand/via update of
+ *   the demand map D against the capacity map C of Alg. 2.  The Elmore RC-tree
+ *   delay of Sec. III-D (d_34 = R_34 (C4+C5+C6+C7)) and its adjoint are exposed
+ *   for timing sensitivities.
+ *
+ * Conventions for every call:
+ *   - Every call returns la_status; LA_OK = 0.  On failure la_last_error(ctx)
+ *     holds a one-line message.  Invalid input (LA_ERR_INVALID) leaves the
+ *     context as it was.  After LA_ERR_CUDA, LA_ERR_TIMEOUT or
+ *     LA_ERR_DEVICE_CHECK the context is poisoned: every later call except
+ *     la_destroy / la_last_error returns LA_ERR_STATE.
+ *   - "device" pointers are CUDA device memory owned by the caller (for
+ *     example torch tensors on the context's device); "host" pointers are
+ *     ordinary host memory owned by the caller.  The library never frees or
+ *     keeps a caller pointer after the call returns, except where stated.
+ *   - Work is enqueued on the context's stream (la_create / la_set_stream);
+ *     calls return once the work is enqueued, unless stated otherwise.  The
+ *     library owns its context and the device memory it allocates for the
+ *     loaded grid, forest and round tables (la_device_bytes reports it).
+ *   - Node order: every per-node array is in the caller's input node order
+ *     (net-major, net-local ids as given in la_net_desc).
+ *
+ * Layers are 0-based.  dir[l] = 0 means horizontal (H), 1 vertical (V).
+ * Public edge layout ("E entries"): layer by layer; an H layer is [y][x] with
+ * X-1 edges per row, a V layer is [x][y] with Y-1 edges per column.
+ */
+#ifndef GAPLA_H
+#define GAPLA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LA_OK = 0,
+  LA_ERR_INVALID = 1,      /* bad argument or malformed input; nothing changed      */
+  LA_ERR_CUDA = 2,         /* a CUDA runtime call failed                            */
+  LA_ERR_OOM = 3,          /* device allocation failed                              */
+  LA_ERR_STATE = 4,        /* call out of order, or context poisoned                */
+  LA_ERR_TIMEOUT = 5,      /* a bounded device-side wait ran out                    */
+  LA_ERR_DEVICE_CHECK = 6  /* a kernel's own bounds/consistency check failed        */
+} la_status;
+
+#define LA_MAX_LAYERS 16
+
+typedef struct la_ctx la_ctx;
+
+/* Create a context on CUDA device `device`, enqueuing on `stream`
+ * (a cudaStream_t; NULL = the legacy default stream). */
+la_status la_create(la_ctx** out, int device, void* stream);
+/* Destroy a context and free every device allocation it owns.  NULL is a no-op. */
+la_status la_destroy(la_ctx* ctx);
+/* Last error message of `ctx` (or of the last failed la_create on this thread
+ * when ctx is NULL).  Valid until the next call on the same context. */
+const char* la_last_error(const la_ctx* ctx);
+/* Change the stream later calls enqueue on. */
+la_status la_set_stream(la_ctx* ctx, void* stream);
+/* Device bytes currently held by the context. */
+la_status la_device_bytes(const la_ctx* ctx, size_t* bytes);
+/* Synchronise the stream and check the device error word; LA_OK if clean. */
+la_status la_check(la_ctx* ctx);
+
+/* ---------------------------------------------------------------------------
+ * Grid: the GCell grid graph with per-layer edge capacity (Sec. II-A, Alg. 2
+ * inputs r, c, vr, X, Y, L, C) and the overflow weight ofw(l) of Eq. 3.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+  int32_t X, Y, L;         /* 2 <= X, Y <= 16384; 2 <= L <= LA_MAX_LAYERS           */
+  const int8_t* dir;       /* host, L: preferred direction, 0 = H, 1 = V            */
+  const int32_t* cap;      /* device, E entries, public edge layout, each >= 0      */
+  const double* unit_r;    /* host, L: wire resistance per GCell edge (ohm), >= 0    */
+  const double* unit_c;    /* host, L: wire capacitance per GCell edge (fF), >= 0    */
+  const double* via_r;     /* host, L-1: resistance of the via between l and l+1     */
+  double via_c;            /* capacitance of one via (fF), >= 0                      */
+  const double* ofw;       /* host, L: overflow weight of Eq. 3, >= 0                */
+} la_grid_desc;
+
+/* Load (or replace) the grid.  Copies `cap` into the library's internal
+ * layout; resets the demand snapshot D and the history H to zero.  Any loaded
+ * forest is dropped.  Errors: LA_ERR_INVALID for sizes/values out of range. */
+la_status la_load_grid(la_ctx* ctx, const la_grid_desc* grid);
+
+/* ---------------------------------------------------------------------------
+ * Nets: the layer-assignment directed tree of Sec. III-B (Fig. 5): each net's
+ * 2D route with extra nodes at bends, so that every tree edge is a straight
+ * horizontal or vertical run of GCell edges.  Node 0 of a net is its root and
+ * carries the driver pin; parent[v] < v inside a net.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+  int64_t num_nets;        /* N >= 1                                                */
+  int64_t num_nodes;       /* V = net_ptr[N]                                        */
+  const int64_t* net_ptr;  /* device, N+1: nodes of net n are [net_ptr[n], net_ptr[n+1]) */
+  const int32_t* x;        /* device, V: GCell column, 0 <= x < X                    */
+  const int32_t* y;        /* device, V: GCell row,    0 <= y < Y                    */
+  const int32_t* parent;   /* device, V: net-local parent id; -1 exactly at local 0  */
+  const int8_t* pin_layer; /* device, V: layer of the node's pin, -1 = no pin; the
+                              root must have one (the driver pin)                    */
+  const double* sink_cap;  /* device, V: sink pin capacitance (fF) >= 0              */
+  const double* kappa;     /* device, V: sink criticality >= 0 (edge weights, Eq. 4) */
+  const double* r_drv;     /* device, N: driver resistance (ohm) >= 0                */
+} la_net_desc;
+
+/* Load the forest (after la_load_grid).  Validates it on the device (parent
+ * order, straight segments of length >= 1 inside the grid, pins in range),
+ * levelises every tree (level = height above the deepest leaf, Alg. 2) and
+ * builds the children lists, segment geometry, and the Eq. 4 edge weights W
+ * and the look-ahead upstream resistances r_est (Sec. III-D).  Synchronises
+ * the stream.  LA_ERR_INVALID if the forest is malformed (message names the
+ * first bad node). */
+la_status la_load_nets(la_ctx* ctx, const la_net_desc* nets);
+
+/* ---------------------------------------------------------------------------
+ * One layer-assignment round (Alg. 2 over one batch holding every net).
+ * ------------------------------------------------------------------------- */
+enum { LA_MODE_PLAIN = 0,     /* one kernel launch per tree level (Alg. 2 as printed) */
+       LA_MODE_BATCHED = 1 }; /* size-bucketed persistent kernels                     */
+enum { LA_WEIGHTS_EQ4 = 0,     /* W = max sink criticality below (Eq. 4), r_est from
+                                  distance x average unit R (Sec. III-D)              */
+       LA_WEIGHTS_ADJOINT = 1 };/* W and r_est from the last la_reweight_adjoint        */
+
+typedef struct {
+  double w_cong;           /* congestion weight w^cong (Alg. 2)                      */
+  double w_via;            /* cost per via                                           */
+  double w_cap;            /* capacitance weight w^cap (Alg. 2)                      */
+  double w_d;              /* delay weight w^d (Alg. 2, Sec. III-D)                  */
+  double hist_w;           /* weight of the overflow history in the penalty          */
+  int32_t mode;            /* LA_MODE_*                                              */
+  int32_t weights;         /* LA_WEIGHTS_*                                           */
+  int32_t reset;           /* 1: start from D = 0 and H = 0 (first round)            */
+  int32_t reserved;
+} la_round_params;
+
+typedef struct {
+  double total_cost;       /* sum over nets of the root look-ahead cost J_n          */
+  double tof;              /* Eq. 3 total overflow over every (layer, edge)          */
+  int64_t relu_overflow;   /* Eq. 2 total overflow, sum of max(0, D - C)             */
+  int64_t vias;            /* sum over nodes of t - b                                */
+  int64_t wl;              /* GCell edges of wire                                    */
+  int64_t wl_per_layer[LA_MAX_LAYERS];
+  double ms;               /* device time of the round (CUDA events)                 */
+} la_round_stats;
+
+/* Run one round against the current snapshot (D, H): every net sees the same
+ * snapshot.  Afterwards D is the demand of the new assignment and
+ * H += max(0, D - C).  If `stats` is non-NULL the call synchronises and fills
+ * it; with NULL it only enqueues.  Weights must be >= 0 and finite. */
+la_status la_assign_round(la_ctx* ctx, const la_round_params* params, la_round_stats* stats);
+
+/* Copy the last round's assignment out (device, V each): layer[v] = layer of
+ * v's junction (its segment's layer; the driver pin layer at a root), and the
+ * via stack [b[v], t[v]] at v.  Any pointer may be NULL. */
+la_status la_get_assignment(la_ctx* ctx, int8_t* layer, int8_t* b, int8_t* t);
+/* Set the assignment (device, V each, same meaning) that la_rc_from_assignment,
+ * la_elmore* and la_reweight_adjoint use.  Checked on the device: layers of the
+ * right direction, stacks holding the junction layer, the pin and every child's
+ * layer.  Synchronises. */
+la_status la_set_assignment(la_ctx* ctx, const int8_t* layer, const int8_t* b, const int8_t* t);
+/* Per-net root look-ahead cost J_n of the last round (device, N). */
+la_status la_get_net_cost(la_ctx* ctx, double* J);
+/* Copy the snapshot out / in (device, E entries each, public layout): demand D
+ * and overflow history H.  la_set_state makes (D, H) the snapshot of the next
+ * round.  Either pointer may be NULL (NULL in set = leave unchanged). */
+la_status la_get_state(la_ctx* ctx, int32_t* demand, int32_t* history);
+la_status la_set_state(la_ctx* ctx, const int32_t* demand, const int32_t* history);
+
+/* ---------------------------------------------------------------------------
+ * Elmore delay on the RC tree of the current assignment (Sec. II-C, III-D):
+ * driver resistance into the root junction; per segment v a via resistor
+ * from the parent junction to the segment start (C_seg/2 there), the wire
+ * R_seg to v's junction (C_seg/2 plus the via caps there), and at a pin node a
+ * via resistor to the pin point holding the sink cap.
+ * All arrays: device, V entries, input node order; root entries of R_seg and
+ * C_seg are ignored.
+ * ------------------------------------------------------------------------- */
+/* R_seg[v] = len_v * unit_r[layer v], C_seg[v] = len_v * unit_c[layer v]
+ * (0 at roots). */
+la_status la_rc_from_assignment(la_ctx* ctx, double* R_seg, double* C_seg);
+/* delay[v] = Elmore delay at v's pin point (pin nodes) or junction (others). */
+la_status la_elmore(la_ctx* ctx, const double* R_seg, const double* C_seg, double* delay);
+/* Adjoint of la_elmore: given g = dL/d delay, writes dL/dR_seg and dL/dC_seg
+ * (0 at roots).  Recomputes the downstream caps level by level instead of
+ * keeping them from the forward pass. */
+la_status la_elmore_backward(la_ctx* ctx, const double* R_seg, const double* C_seg,
+                             const double* grad_delay, double* dR_seg, double* dC_seg);
+/* Timing sensitivities for the next round: with g = kappa on the current
+ * assignment's RC tree, W[v] = sum of kappa below v (dT/dR = W * Cdown) and
+ * r_est[v] = sum over resistors above v's junction of R * W (dT/dC at v).
+ * Later rounds with weights = LA_WEIGHTS_ADJOINT use them. */
+la_status la_reweight_adjoint(la_ctx* ctx);
+/* Copy the DP weights out (device, V each): W[v] and r_est[v] of the given
+ * source (LA_WEIGHTS_EQ4 or LA_WEIGHTS_ADJOINT). */
+la_status la_get_weights(la_ctx* ctx, int32_t source, double* W, double* rho);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GAPLA_H */
