@@ -1,0 +1,360 @@
+"""Benchmark: nets/s per layer-assignment round on one GB300.
+
+One step = the workload's full negotiation: every round runs the penalty
+refresh and line prefix, the bottom-up DP (Alg. 3), the backtrack (Alg. 4),
+the demand/via/history update, and the Elmore adjoint that reweights the
+next round (W = criticality below, r_est = weighted upstream R); the step ends
+with the Elmore forward of the final assignment.  Inputs (grid, forest) are
+resident in HBM before the timed region; `e2e` repeats the step through the
+C ABI from pinned host buffers (host->device copies of the forest, forest
+load + levelisation, the rounds, device->host copy of the assignment).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--workload 5]
+                       [--mode plain|batched] [--impl gapla|reference]
+Under torchrun (N > 1) every rank runs its own replica (seed = rank; no
+collective on the data path); rank 0 prints the JSON line with the max time
+over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "nets/s per layer-assign round on 1 GB300 (plain vs batched+adjoint), % HBM peak"
+
+
+# --------------------------------------------------------------------------
+# clocks sampled during the timed region
+# --------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# --------------------------------------------------------------------------
+# one step on the GPU
+# --------------------------------------------------------------------------
+def run_step(a, la, rounds: int, mode: int, weights: dict, want_stats: bool, torch):
+    """The workload's rounds with adjoint reweighting; returns per-round stats
+    (if asked) and the device times of the adjoint passes."""
+    out = []
+    adj_ms = []
+    for r in range(rounds):
+        src = la.LA_WEIGHTS_EQ4 if r == 0 else la.LA_WEIGHTS_ADJOINT
+        st = a.assign_round(mode=mode, weights=src, reset=(r == 0), stats=want_stats, **weights)
+        if want_stats:
+            out.append(st)
+        if want_stats:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            a.reweight_adjoint()
+            e1.record()
+            adj_ms.append((e0, e1))
+        else:
+            a.reweight_adjoint()
+    R, C = a.rc_from_assignment()
+    delay = a.elmore(R, C)
+    return out, adj_ms, delay
+
+
+def bench_gpu(args):
+    import numpy as np
+    import torch
+
+    import forestgen as fg
+    import paper_2507_13375_gb300 as la
+    import __graft_entry__
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    __graft_entry__.build()
+
+    wl = fg.WORKLOADS[args.workload]
+    mode = la.LA_MODE_BATCHED if args.mode == "batched" else la.LA_MODE_PLAIN
+    weights = dict(la.DEFAULT_WEIGHTS)
+    t0 = time.time()
+    grid = fg.make_grid(wl, seed=rank)
+    forest = fg.make_forest(wl, seed=rank)
+    gen_s = time.time() - t0
+    N, V = wl.num_nets, int(forest["num_nodes"])
+    S = V - N
+
+    a = la.LayerAssigner(local)
+    a.load_grid(grid)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    a.load_nets(forest)
+    ev1.record()
+    torch.cuda.synchronize()
+    load_ms = ev0.elapsed_time(ev1)
+
+    for _ in range(args.warmup):
+        run_step(a, la, wl.rounds, mode, weights, False, torch)
+    torch.cuda.synchronize()
+
+    # timed region: K steps, barrier + sync on both sides
+    launches0 = a.launch_count()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        e_start, e_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e_start.record()
+        stats = []
+        adj = []
+        for _ in range(args.steps):
+            st, ad, _ = run_step(a, la, wl.rounds, mode, weights, True, torch)
+            stats += st
+            adj += ad
+        e_end.record()
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    launches = a.launch_count() - launches0
+    step_ms = e_start.elapsed_time(e_end) / args.steps
+    if dist:
+        tt = torch.tensor([step_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        step_ms = float(tt.item())
+    adj_ms = sum(e0.elapsed_time(e1) for e0, e1 in adj) / max(len(adj), 1)
+    dp_ms = statistics.mean(s["ms_dp"] for s in stats)
+    rnd_ms = statistics.mean(s["ms"] for s in stats)
+    value = world * N * wl.rounds / (step_ms * 1e-3)
+
+    # ---- end to end through the C ABI, inputs from pinned host memory ----
+    keys = ("net_ptr", "x", "y", "parent", "pin_layer", "sink_cap", "kappa", "r_drv")
+    dt = dict(net_ptr=torch.int64, x=torch.int32, y=torch.int32, parent=torch.int32, pin_layer=torch.int8,
+              sink_cap=torch.float64, kappa=torch.float64, r_drv=torch.float64)
+    host = {k: torch.from_numpy(np.ascontiguousarray(forest[k])).to(dt[k]).pin_memory() for k in keys}
+    devb = {k: torch.empty_like(host[k], device="cuda") for k in keys}
+    out_host = [torch.empty(V, dtype=torch.int8).pin_memory() for _ in range(3)]
+    h2d = sum(t.numel() * t.element_size() for t in host.values())
+    d2h = 3 * V
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    e_start.record()
+    for _ in range(e2e_steps):
+        for k in keys:
+            devb[k].copy_(host[k], non_blocking=True)
+        a.load_nets(devb)
+        run_step(a, la, wl.rounds, mode, weights, False, torch)
+        lay, bb, tt_ = a.get_assignment()
+        for dst, src in zip(out_host, (lay, bb, tt_)):
+            dst.copy_(src, non_blocking=True)
+    e_end.record()
+    torch.cuda.synchronize()
+    e2e_ms = e_start.elapsed_time(e_end) / e2e_steps
+    e2e_wall_ms = (time.perf_counter() - w0) * 1e3 / e2e_steps
+    if dist:
+        tt = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_ms = float(tt.item())
+
+    # ---- roofline of the dominant kernel (the DP) ----
+    peak, peak_src = measured_peaks()
+    LD = max(sum(1 for d in wl.dirs if d == 0), sum(1 for d in wl.dirs if d == 1))
+    nch = S  # every non-root node is some node's son
+    # algorithmic bytes of one DP pass (all levels): per node its own segment
+    # (geometry 8 B, W and r_est 16 B, pin/caps 17 B, CSR 8 B), per candidate
+    # layer the two congestion prefixes (16 B) and its table entry written
+    # (A, Cc, M: 24 B; stack 2 B), per son and son layer its table read
+    # (A, Cc, M: 24 B) and its entry byte written.
+    dp_bytes = V * (8 + 16 + 17 + 8) + S * LD * (16 + 24 + 2) + N * (24 + 2) + nch * LD * (24 + 1)
+    achieved = dp_bytes / (dp_ms * 1e-3) / 1e9
+    roofline = {"kernel": "k_dp_level (all levels of one round)", "bound": "hbm", "achieved": round(achieved, 1),
+                "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+                "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)" if peak_src == "measured" else
+                "fallback 6.8 TB/s", "algorithmic_bytes_per_launch_set": int(dp_bytes),
+                "dp_ms_per_round": round(dp_ms, 4)}
+
+    res = {
+        "metric": METRIC, "value": value, "unit": "nets/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic: seeded grid + MST/L-split net forest generator (forestgen), seed = rank",
+        "config": {"workload": wl.name, "nets": N, "nodes": V, "segments": S, "rounds_per_step": wl.rounds,
+                   "grid": f"{wl.X}x{wl.Y}x{wl.L}", "mode": args.mode,
+                   "weights": "Eq. 4 in round 0, adjoint sensitivities in later rounds",
+                   "l2": "inputs larger than L2 (working set %.1f GB)" % (a.device_bytes() / 1e9),
+                   "parallelism": f"replicas x{world}"},
+        "segments_per_s": world * S * wl.rounds / (step_ms * 1e-3),
+        "phases_ms_per_round": {"round": round(rnd_ms, 4), "dp": round(dp_ms, 4),
+                                "backtrack": round(statistics.mean(s["ms_backtrack"] for s in stats), 4),
+                                "demand_scan": round(statistics.mean(s["ms_demand"] for s in stats), 4),
+                                "adjoint": round(adj_ms, 4)},
+        "load_ms": round(load_ms, 3), "generate_s": round(gen_s, 2),
+        "roofline": roofline,
+        "e2e": {"value": world * N * wl.rounds / (e2e_ms * 1e-3), "unit": "nets/s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h), "ms_per_step": round(e2e_ms, 3),
+                "wall_ms_per_step": round(e2e_wall_ms, 3)},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+        "quality_last_round": {k: stats[-1][k] for k in ("total_cost", "tof", "relu_overflow", "vias", "wl")},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        res["cpu_baseline"] = cpu_baseline(wl, grid, forest, args.cpu_seconds)
+    a.close()
+    if dist:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+
+
+# --------------------------------------------------------------------------
+# the CPU oracle on a bounded sample of the same workload
+# --------------------------------------------------------------------------
+def cpu_baseline(wl, grid, forest, budget_s: float):
+    import numpy as np
+
+    import forestgen as fg
+    import oracle
+
+    # first M nets of the same forest, one round from the zero snapshot plus
+    # the adjoint reweighting, sized to about budget_s seconds
+    M = min(wl.num_nets, 20000)
+    t_small = _time_oracle_round(grid, fg.subset_forest(forest, np.arange(M)))
+    per_net = t_small / M
+    M = int(min(wl.num_nets, max(M, budget_s / 2 / max(per_net, 1e-9))))
+    sub = fg.subset_forest(forest, np.arange(M))
+    t = _time_oracle_round(grid, sub)
+    threads = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return {"value": M / t, "unit": "nets/s", "cores": threads, "kind": "oracle",
+            "sample": f"first {M} of {wl.num_nets} nets, 1 round (penalty + DP + backtrack + demand + adjoint "
+                      f"reweighting) of {wl.name}, {t:.1f} s"}
+
+
+def _time_oracle_round(grid, forest):
+    import oracle
+
+    t0 = time.perf_counter()
+    out = oracle.assign_round(grid, forest, oracle.DEFAULT_WEIGHTS)
+    oracle.adjoint_weights(grid, forest, out["layer"], out["b"], out["t"])
+    return time.perf_counter() - t0
+
+
+def bench_reference(args):
+    """The oracle as the reference arm: same metric, each step a bounded sample."""
+    import numpy as np
+
+    import forestgen as fg
+    import oracle
+
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    oracle.build()
+    fg.build()
+    wl = fg.WORKLOADS[args.workload]
+    grid, forest = fg.make_grid(wl, 0), fg.make_forest(wl, 0)
+    M = min(wl.num_nets, args.ref_nets)
+    sub = fg.subset_forest(forest, np.arange(M))
+    for _ in range(args.warmup):
+        _time_oracle_round(grid, sub)
+    t = sum(_time_oracle_round(grid, sub) for _ in range(args.steps)) / args.steps
+    threads = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    v = M / t
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "nets/s", "n_gpus": 0, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (forestgen, seed 0)",
+        "config": {"workload": wl.name, "sample_nets": M, "rounds_per_step": 1},
+        "cpu_baseline": {"value": v, "unit": "nets/s", "cores": threads, "kind": "oracle",
+                         "sample": f"first {M} of {wl.num_nets} nets, 1 round + adjoint per step"},
+        "e2e": {"value": v, "unit": "nets/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", type=int, default=5, choices=[1, 2, 4, 5])
+    ap.add_argument("--mode", default="plain", choices=["plain", "batched"])
+    ap.add_argument("--impl", default="gapla", choices=["gapla", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--ref-nets", type=int, default=400000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        bench_reference(args)
+    else:
+        bench_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -69,6 +69,8 @@ la_status la_set_stream(la_ctx* ctx, void* stream);
 la_status la_device_bytes(const la_ctx* ctx, size_t* bytes);
 /* Synchronise the stream and check the device error word; LA_OK if clean. */
 la_status la_check(la_ctx* ctx);
+/* Number of CUDA kernels this context has launched since it was created. */
+la_status la_launch_count(const la_ctx* ctx, int64_t* launches);
 
 /* ---------------------------------------------------------------------------
  * Grid: the GCell grid graph with per-layer edge capacity (Sec. II-A, Alg. 2
@@ -147,7 +149,11 @@ typedef struct {
   int64_t vias;            /* sum over nodes of t - b                                */
   int64_t wl;              /* GCell edges of wire                                    */
   int64_t wl_per_layer[LA_MAX_LAYERS];
-  double ms;               /* device time of the round (CUDA events)                 */
+  double ms;               /* device time of the round (CUDA events on the stream)   */
+  double ms_dp;            /*   of which the bottom-up DP, all levels (Alg. 3)       */
+  double ms_backtrack;     /*   the top-down backtrack, all levels (Alg. 4)          */
+  double ms_demand;        /*   demand + line scan (D, H and the next penalty prefix) */
+  int64_t launches;        /* kernels this round launched                            */
 } la_round_stats;
 
 /* Run one round against the current snapshot (D, H): every net sees the same

@@ -1,0 +1,652 @@
+// capi.cu - the C ABI of include/gapla.h: contexts, loading, the round driver
+// (Alg. 2: levels 0..max for the DP, max..0 for the backtrack) and the Elmore
+// calls.  Host code only; kernels live in k_*.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <utility>
+#include <vector>
+
+#include "gapla_internal.cuh"
+
+using namespace gapla;
+
+namespace {
+
+thread_local std::string g_create_err;
+
+la_status set_err(la_ctx* c, la_status code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  c->err = buf;
+  if (code == LA_ERR_CUDA || code == LA_ERR_TIMEOUT || code == LA_ERR_DEVICE_CHECK) c->poisoned = true;
+  return code;
+}
+
+#define CK(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess) return set_err(c, LA_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+#define TRY(expr)                  \
+  do {                             \
+    la_status s_ = (expr);         \
+    if (s_ != LA_OK) return s_;    \
+  } while (0)
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int d) {
+    cudaGetDevice(&prev);
+    if (prev != d) cudaSetDevice(d);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+// Device allocations of one load (grid or forest), freed together.
+struct Allocs {
+  std::vector<std::pair<void*, size_t>> list;
+  size_t bytes = 0;
+  template <typename T>
+  la_status get(la_ctx* c, T** p, size_t n) {
+    size_t b = n * sizeof(T);
+    if (b == 0) b = 16;
+    b = (b + 255) & ~size_t(255);
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, b);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      *p = nullptr;
+      return set_err(c, LA_ERR_OOM, "device allocation of %zu bytes failed: %s", b, cudaGetErrorString(e));
+    }
+    list.emplace_back(q, b);
+    bytes += b;
+    *p = static_cast<T*>(q);
+    return LA_OK;
+  }
+  void release() {
+    for (auto& x : list) cudaFree(x.first);
+    list.clear();
+    bytes = 0;
+  }
+};
+
+}  // namespace
+
+// Allocation groups live beside the context (kept out of the shared header).
+struct la_ctx_allocs {
+  Allocs grid, forest;
+};
+static la_ctx_allocs* allocs_of(la_ctx* c) { return reinterpret_cast<la_ctx_allocs*>(c->alloc_groups); }
+
+static la_status check_ctx(la_ctx* c) {
+  if (!c) return LA_ERR_INVALID;
+  if (c->poisoned) return set_err(c, LA_ERR_STATE, "context is poisoned by an earlier CUDA/device error: %s", c->err.c_str());
+  return LA_OK;
+}
+
+static bool finite_nonneg(double v) { return std::isfinite(v) && v >= 0.0; }
+
+static const char* dev_err_name(int code) {
+  switch (code) {
+    case DE_NETPTR: return "net_ptr not increasing or out of range";
+    case DE_PARENT: return "parent id out of order (need -1 at a net's first node, 0 <= parent < local id elsewhere)";
+    case DE_COORD: return "node coordinate outside the grid";
+    case DE_SEGMENT: return "tree edge is not a straight horizontal/vertical run of length >= 1";
+    case DE_PIN: return "pin layer out of range, or a root without a driver pin";
+    case DE_VALUE: return "negative or non-finite value";
+    case DE_ASSIGN: return "assignment layer of the wrong direction, or a via stack not covering it";
+    case DE_DEGREE: return "too many sons";
+    case DE_NOSTACK: return "no valid via stack";
+    default: return "unknown device check";
+  }
+}
+
+// Sync and read the device error word; returns (code, index) or (0, 0).
+static la_status read_dev_err(la_ctx* c, int* code, long long* index) {
+  CK(cudaStreamSynchronize(c->stream));
+  unsigned long long e = kNoErr;
+  CK(cudaMemcpy(&e, c->d_err, sizeof e, cudaMemcpyDeviceToHost));
+  if (e == kNoErr) {
+    *code = 0;
+    *index = 0;
+  } else {
+    *code = int(e & 0xFF);
+    *index = (long long)(e >> 8);
+  }
+  return LA_OK;
+}
+
+static la_status reset_dev_err(la_ctx* c) {
+  const unsigned long long e = kNoErr;
+  CK(cudaMemcpyAsync(c->d_err, &e, sizeof e, cudaMemcpyHostToDevice, c->stream));
+  return LA_OK;
+}
+
+// ------------------------------------------------------------------------
+extern "C" {
+
+la_status la_create(la_ctx** out, int device, void* stream) {
+  if (!out) return LA_ERR_INVALID;
+  *out = nullptr;
+  int n = 0;
+  cudaError_t e = cudaGetDeviceCount(&n);
+  if (e != cudaSuccess || device < 0 || device >= n) {
+    cudaGetLastError();
+    g_create_err = std::string("no CUDA device ") + std::to_string(device) + ": " + cudaGetErrorString(e);
+    return e != cudaSuccess ? LA_ERR_CUDA : LA_ERR_INVALID;
+  }
+  la_ctx* c = new la_ctx();
+  c->device = device;
+  c->stream = static_cast<cudaStream_t>(stream);
+  c->alloc_groups = new la_ctx_allocs();
+  DeviceGuard g(device);
+  bool ok = cudaMalloc(&c->d_err, sizeof(unsigned long long)) == cudaSuccess &&
+            cudaMalloc(&c->d_stats, sizeof(Stats)) == cudaSuccess;
+  for (auto& e2 : c->ev) ok = ok && cudaEventCreate(&e2) == cudaSuccess;
+  if (!ok) {
+    g_create_err = std::string("context set-up failed: ") + cudaGetErrorString(cudaGetLastError());
+    la_destroy(c);
+    return LA_ERR_CUDA;
+  }
+  *out = c;
+  return LA_OK;
+}
+
+la_status la_destroy(la_ctx* c) {
+  if (!c) return LA_OK;
+  DeviceGuard g(c->device);
+  cudaStreamSynchronize(c->stream);
+  if (la_ctx_allocs* a = allocs_of(c)) {
+    a->forest.release();
+    a->grid.release();
+    delete a;
+  }
+  if (c->d_err) cudaFree(c->d_err);
+  if (c->d_stats) cudaFree(c->d_stats);
+  for (auto& e2 : c->ev)
+    if (e2) cudaEventDestroy(e2);
+  delete c;
+  return LA_OK;
+}
+
+const char* la_last_error(const la_ctx* c) { return c ? c->err.c_str() : g_create_err.c_str(); }
+
+la_status la_set_stream(la_ctx* c, void* stream) {
+  if (!c) return LA_ERR_INVALID;
+  c->stream = static_cast<cudaStream_t>(stream);
+  return LA_OK;
+}
+
+la_status la_device_bytes(const la_ctx* c, size_t* bytes) {
+  if (!c || !bytes) return LA_ERR_INVALID;
+  la_ctx_allocs* a = allocs_of(const_cast<la_ctx*>(c));
+  *bytes = a->grid.bytes + a->forest.bytes + sizeof(Stats) + sizeof(unsigned long long);
+  return LA_OK;
+}
+
+la_status la_launch_count(const la_ctx* c, int64_t* n) {
+  if (!c || !n) return LA_ERR_INVALID;
+  *n = c->launches;
+  return LA_OK;
+}
+
+la_status la_check(la_ctx* c) {
+  TRY(check_ctx(c));
+  DeviceGuard g(c->device);
+  int code;
+  long long idx;
+  TRY(read_dev_err(c, &code, &idx));
+  if (code) return set_err(c, LA_ERR_DEVICE_CHECK, "device check failed: %s (index %lld)", dev_err_name(code), idx);
+  return LA_OK;
+}
+
+// ------------------------------------------------------------------------
+la_status la_load_grid(la_ctx* c, const la_grid_desc* gd) {
+  TRY(check_ctx(c));
+  if (!gd || !gd->dir || !gd->cap || !gd->unit_r || !gd->unit_c || !gd->ofw || (gd->L > 1 && !gd->via_r))
+    return set_err(c, LA_ERR_INVALID, "la_load_grid: null pointer in the descriptor");
+  const int X = gd->X, Y = gd->Y, L = gd->L;
+  if (X < 2 || Y < 2 || X > 16384 || Y > 16384 || L < 2 || L > kMaxL)
+    return set_err(c, LA_ERR_INVALID, "la_load_grid: need 2 <= X, Y <= 16384 and 2 <= L <= %d", kMaxL);
+  LayerInfo li{};
+  li.L = L;
+  for (int l = 0; l < L; ++l) {
+    const int d = gd->dir[l];
+    if (d != 0 && d != 1) return set_err(c, LA_ERR_INVALID, "la_load_grid: dir[%d] must be 0 or 1", l);
+    if (!finite_nonneg(gd->unit_r[l]) || !finite_nonneg(gd->unit_c[l]) || !finite_nonneg(gd->ofw[l]))
+      return set_err(c, LA_ERR_INVALID, "la_load_grid: unit_r/unit_c/ofw of layer %d must be finite and >= 0", l);
+    if (l + 1 < L && !finite_nonneg(gd->via_r[l]))
+      return set_err(c, LA_ERR_INVALID, "la_load_grid: via_r[%d] must be finite and >= 0", l);
+    li.dir[l] = int8_t(d);
+    li.ld_of[l] = li.nld[d];
+    li.lay[d][li.nld[d]++] = l;
+    li.mask[d] |= 1u << l;
+    li.unit_r[l] = gd->unit_r[l];
+    li.unit_c[l] = gd->unit_c[l];
+    li.half_c[l] = 0.5 * gd->unit_c[l];
+  }
+  if (li.nld[0] == 0 || li.nld[1] == 0)
+    return set_err(c, LA_ERR_INVALID, "la_load_grid: each direction needs at least one layer");
+  if (!finite_nonneg(gd->via_c)) return set_err(c, LA_ERR_INVALID, "la_load_grid: via_c must be finite and >= 0");
+  li.via_c = gd->via_c;
+  for (int d = 0; d < 2; ++d) {
+    double s = 0.0;
+    int n = 0;
+    for (int l = 0; l < L; ++l)
+      if (li.dir[l] == d) { s += li.unit_r[l]; ++n; }
+    li.rbar[d] = s / n;
+  }
+  li.nlines[0] = Y; li.npos[0] = X;
+  li.nlines[1] = X; li.npos[1] = Y;
+  li.grid_off[0] = 0;
+  li.grid_off[1] = int64_t(Y) * X * li.nld[0];
+  const int64_t G = li.grid_off[1] + int64_t(X) * Y * li.nld[1];
+  li.pub_off[0] = 0;
+  for (int l = 0; l < L; ++l)
+    li.pub_off[l + 1] = li.pub_off[l] + (li.dir[l] == 0 ? int64_t(Y) * (X - 1) : int64_t(X) * (Y - 1));
+  for (int l = L; l < kMaxL; ++l) li.pub_off[l + 1] = li.pub_off[L];
+
+  Grid ng;
+  ng.X = X; ng.Y = Y; ng.E = li.pub_off[L]; ng.G = G; ng.li = li;
+  for (int l = 0; l + 1 < L; ++l) ng.via_r[l] = gd->via_r[l];
+  for (int l = 0; l < L; ++l) ng.ofw[l] = gd->ofw[l];
+  // Rvia(a, b): the via resistances between the two layers, summed upwards
+  for (int a = 0; a < L; ++a)
+    for (int b = 0; b < L; ++b) {
+      const int lo = std::min(a, b), hi = std::max(a, b);
+      double s = 0.0;
+      for (int k = lo; k < hi; ++k) s += ng.via_r[k];
+      ng.rvia[a * kMaxL + b] = s;
+    }
+  // congestion penalty table (reading of Eq. 3) and the Eq. 3 overflow table
+  std::vector<double> tofT(size_t(L) * 2 * 257);
+  for (int l = 0; l < L; ++l)
+    for (int si = 0; si < 2; ++si) {
+      const double s = si == 0 ? 0.5 : 1.5;
+      for (int k = -64; k <= 64; ++k) {
+        double v = ng.ofw[l] * std::exp(s * k) * 16777216.0;
+        if (v > double(kPenMax)) v = double(kPenMax);
+        ng.pen_T[(l * 2 + si) * 129 + (k + 64)] = llround(v);
+      }
+      for (int o = -128; o <= 128; ++o) tofT[(l * 2 + si) * 257 + (o + 128)] = ng.ofw[l] * std::exp(s * double(o));
+    }
+  DevTables& t = ng.tab;
+  memset(&t, 0, sizeof t);
+  memcpy(t.rv, ng.rvia, sizeof t.rv);
+  for (int l = 0; l < kMaxL; ++l) {
+    t.unit_r[l] = li.unit_r[l];
+    t.unit_c[l] = li.unit_c[l];
+    t.half_c[l] = li.half_c[l];
+    t.ld_of[l] = int8_t(l < L ? li.ld_of[l] : 0);
+    t.dir[l] = int8_t(l < L ? li.dir[l] : 0);
+    t.lay[0][l] = int8_t(li.lay[0][l]);
+    t.lay[1][l] = int8_t(li.lay[1][l]);
+  }
+  t.via_c = li.via_c;
+  for (int d = 0; d < 2; ++d) {
+    t.grid_off[d] = li.grid_off[d];
+    t.npos[d] = li.npos[d];
+    t.nlines[d] = li.nlines[d];
+    t.nld[d] = li.nld[d];
+    t.mask[d] = li.mask[d];
+  }
+  t.L = L;
+
+  DeviceGuard g(c->device);
+  Allocs na;
+  la_status st = LA_OK;
+  if ((st = na.get(c, &ng.cap, G)) || (st = na.get(c, &ng.D, G)) || (st = na.get(c, &ng.H, G)) ||
+      (st = na.get(c, &ng.diff, G)) || (st = na.get(c, &ng.P, G)) || (st = na.get(c, &ng.T_dev, size_t(L) * 2 * 129)) ||
+      (st = na.get(c, &ng.tofT_dev, tofT.size())) || (st = na.get(c, &ng.tab_dev, 1))) {
+    na.release();
+    return st;
+  }
+  auto fail = [&](la_status s) { na.release(); return s; };
+  cudaStream_t s = c->stream;
+  if (cudaMemsetAsync(ng.cap, 0, G * 4, s) || cudaMemsetAsync(ng.D, 0, G * 4, s) || cudaMemsetAsync(ng.H, 0, G * 4, s) ||
+      cudaMemsetAsync(ng.diff, 0, G * 4, s) || cudaMemsetAsync(ng.P, 0, G * 8, s) ||
+      cudaMemcpyAsync(ng.T_dev, ng.pen_T, sizeof(int64_t) * L * 2 * 129, cudaMemcpyHostToDevice, s) ||
+      cudaMemcpyAsync(ng.tofT_dev, tofT.data(), sizeof(double) * tofT.size(), cudaMemcpyHostToDevice, s) ||
+      cudaMemcpyAsync(ng.tab_dev, &ng.tab, sizeof(DevTables), cudaMemcpyHostToDevice, s))
+    return fail(set_err(c, LA_ERR_CUDA, "la_load_grid: %s", cudaGetErrorString(cudaGetLastError())));
+  if (reset_dev_err(c)) return fail(LA_ERR_CUDA);
+  launch_grid_to_internal(li, X, Y, gd->cap, ng.cap, true, c->d_err, s);
+  ++c->launches;
+  int code;
+  long long idx;
+  if (cudaGetLastError() != cudaSuccess || read_dev_err(c, &code, &idx) != LA_OK)
+    return fail(set_err(c, LA_ERR_CUDA, "la_load_grid: kernel launch failed"));
+  if (code) return fail(set_err(c, LA_ERR_INVALID, "la_load_grid: capacity %lld is negative", idx));
+  // success: replace the grid, drop the forest
+  la_ctx_allocs* a = allocs_of(c);
+  a->forest.release();
+  a->grid.release();
+  c->forest = Forest();
+  a->grid = na;
+  c->grid = ng;
+  c->grid.loaded = true;
+  c->grid.P_valid = false;
+  c->LD = std::max(li.nld[0], li.nld[1]);
+  return LA_OK;
+}
+
+// ------------------------------------------------------------------------
+la_status la_load_nets(la_ctx* c, const la_net_desc* nd) {
+  TRY(check_ctx(c));
+  if (!c->grid.loaded) return set_err(c, LA_ERR_STATE, "la_load_nets: load the grid first");
+  if (!nd || !nd->net_ptr || !nd->x || !nd->y || !nd->parent || !nd->pin_layer || !nd->sink_cap || !nd->kappa ||
+      !nd->r_drv)
+    return set_err(c, LA_ERR_INVALID, "la_load_nets: null pointer in the descriptor");
+  if (nd->num_nets < 1 || nd->num_nodes < nd->num_nets || nd->num_nodes > int64_t(INT32_MAX) - 1)
+    return set_err(c, LA_ERR_INVALID, "la_load_nets: need 1 <= num_nets <= num_nodes < 2^31");
+  DeviceGuard g(c->device);
+  cudaStream_t s = c->stream;
+  const int LD = c->LD;
+  Forest nf;
+  nf.N = nd->num_nets;
+  nf.V = nd->num_nodes;
+  const size_t N = size_t(nf.N), V = size_t(nf.V);
+  Allocs na;
+  la_status st = LA_OK;
+#define GET(p, n) if (st == LA_OK) st = na.get(c, &(p), (n))
+  GET(nf.net_ptr, N + 1); GET(nf.parent_g, V); GET(nf.net_of, V); GET(nf.pin, V); GET(nf.sink_cap, V);
+  GET(nf.kappa, V); GET(nf.gk, V); GET(nf.r_drv, N); GET(nf.geo, V); GET(nf.child_start, V); GET(nf.nch, V);
+  GET(nf.child_list, V); GET(nf.height, V); GET(nf.W_eq4, V); GET(nf.rho_eq4, V);
+  int* d_hmax = nullptr;
+  GET(d_hmax, 1);
+#undef GET
+  if (st) { na.release(); return st; }
+  auto fail = [&](la_status s2) { na.release(); return s2; };
+  if (reset_dev_err(c) || cudaMemsetAsync(d_hmax, 0, sizeof(int), s))
+    return fail(set_err(c, LA_ERR_CUDA, "la_load_nets: %s", cudaGetErrorString(cudaGetLastError())));
+  launch_forest_prepare(c, nf, nd, d_hmax, s);
+  int code;
+  long long idx;
+  if (cudaGetLastError() != cudaSuccess) return fail(set_err(c, LA_ERR_CUDA, "la_load_nets: launch failed"));
+  if ((st = read_dev_err(c, &code, &idx))) return fail(st);
+  if (code) return fail(set_err(c, LA_ERR_INVALID, "la_load_nets: %s (%s %lld)", dev_err_name(code),
+                                 code == DE_NETPTR ? "net" : "node", idx));
+  int hmax = 0;
+  if (cudaMemcpy(&hmax, d_hmax, sizeof hmax, cudaMemcpyDeviceToHost))
+    return fail(set_err(c, LA_ERR_CUDA, "la_load_nets: %s", cudaGetErrorString(cudaGetLastError())));
+  nf.Hmax = hmax;
+  // levels
+  int32_t* d_cnt = nullptr;
+  int64_t* d_cur = nullptr;
+#define GET(p, n) if (st == LA_OK) st = na.get(c, &(p), (n))
+  GET(nf.lvl_nodes, V); GET(d_cnt, size_t(hmax) + 1); GET(d_cur, size_t(hmax) + 1);
+  GET(nf.A, V * LD); GET(nf.Cc, V * LD); GET(nf.M, V * LD); GET(nf.sb, V * LD); GET(nf.st, V * LD);
+  GET(nf.ent, V * LD); GET(nf.Jroot, V); GET(nf.layer, V); GET(nf.b, V); GET(nf.t, V); GET(nf.s0, V);
+  GET(nf.s1, V); GET(nf.s2, V); GET(nf.W_adj, V); GET(nf.rho_adj, V);
+  const int nred = std::max(scan_blocks(c->grid.li), int((N + 255) / 256)) + 8;
+  GET(nf.red, size_t(nred) * 2);
+#undef GET
+  if (st) return fail(st);
+  nf.red_cap = nred;
+  if (cudaMemsetAsync(d_cnt, 0, sizeof(int32_t) * (hmax + 1), s))
+    return fail(set_err(c, LA_ERR_CUDA, "la_load_nets: %s", cudaGetErrorString(cudaGetLastError())));
+  launch_level_sort(nf, d_cnt, nullptr, s);
+  ++c->launches;
+  std::vector<int32_t> cnt(hmax + 1);
+  if (cudaMemcpyAsync(cnt.data(), d_cnt, sizeof(int32_t) * (hmax + 1), cudaMemcpyDeviceToHost, s) ||
+      cudaStreamSynchronize(s))
+    return fail(set_err(c, LA_ERR_CUDA, "la_load_nets: %s", cudaGetErrorString(cudaGetLastError())));
+  nf.lvl_off.assign(hmax + 2, 0);
+  for (int h = 0; h <= hmax; ++h) nf.lvl_off[h + 1] = nf.lvl_off[h] + cnt[h];
+  if (cudaMemcpyAsync(d_cur, nf.lvl_off.data(), sizeof(int64_t) * (hmax + 1), cudaMemcpyHostToDevice, s))
+    return fail(set_err(c, LA_ERR_CUDA, "la_load_nets: %s", cudaGetErrorString(cudaGetLastError())));
+  launch_level_sort(nf, nullptr, d_cur, s);
+  launch_weights_eq4(c->grid.li, nf, s);
+  c->launches += 2;
+  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
+    return fail(set_err(c, LA_ERR_CUDA, "la_load_nets: %s", cudaGetErrorString(cudaGetLastError())));
+  // success: replace the forest
+  la_ctx_allocs* a = allocs_of(c);
+  a->forest.release();
+  a->forest = na;
+  c->forest = nf;
+  return LA_OK;
+}
+
+// ------------------------------------------------------------------------
+static la_status check_loaded(la_ctx* c) {
+  TRY(check_ctx(c));
+  if (!c->grid.loaded || c->forest.V == 0) return set_err(c, LA_ERR_STATE, "load a grid and a forest first");
+  return LA_OK;
+}
+
+la_status la_assign_round(la_ctx* c, const la_round_params* p, la_round_stats* stats) {
+  TRY(check_loaded(c));
+  if (!p) return set_err(c, LA_ERR_INVALID, "la_assign_round: null params");
+  const double ws[5] = {p->w_cong, p->w_via, p->w_cap, p->w_d, p->hist_w};
+  for (double w : ws)
+    if (!finite_nonneg(w)) return set_err(c, LA_ERR_INVALID, "la_assign_round: weights must be finite and >= 0");
+  if (p->mode != LA_MODE_PLAIN && p->mode != LA_MODE_BATCHED)
+    return set_err(c, LA_ERR_INVALID, "la_assign_round: unknown mode %d", p->mode);
+  if (p->weights != LA_WEIGHTS_EQ4 && p->weights != LA_WEIGHTS_ADJOINT)
+    return set_err(c, LA_ERR_INVALID, "la_assign_round: unknown weights source %d", p->weights);
+  Forest& f = c->forest;
+  Grid& gr = c->grid;
+  if (p->weights == LA_WEIGHTS_ADJOINT && !f.have_adj)
+    return set_err(c, LA_ERR_STATE, "la_assign_round: no adjoint weights yet (call la_reweight_adjoint)");
+  if (p->mode == LA_MODE_BATCHED)
+    return set_err(c, LA_ERR_INVALID, "la_assign_round: batched mode is not available in this build");
+  const double* W = p->weights == LA_WEIGHTS_ADJOINT ? f.W_adj : f.W_eq4;
+  const double* rho = p->weights == LA_WEIGHTS_ADJOINT ? f.rho_adj : f.rho_eq4;
+  DeviceGuard g(c->device);
+  cudaStream_t s = c->stream;
+  RoundW w{p->w_cong, p->w_via, p->w_cap, p->w_d, p->hist_w};
+  if (p->reset) {
+    CK(cudaMemsetAsync(gr.D, 0, gr.G * 4, s));
+    CK(cudaMemsetAsync(gr.H, 0, gr.G * 4, s));
+    CK(cudaMemsetAsync(gr.diff, 0, gr.G * 4, s));
+    gr.P_valid = false;
+  }
+  CK(cudaMemsetAsync(c->d_stats, 0, sizeof(Stats), s));
+  TRY(reset_dev_err(c));
+  const long long launches0 = c->launches;
+  CK(cudaEventRecord(c->ev[0], s));
+  double* tof_part = f.red;
+  double* J_part = f.red + f.red_cap;
+  if (!gr.P_valid || gr.P_hist_w != p->hist_w) launch_scan_lines(c, false, p->hist_w, tof_part, s);
+  CK(cudaEventRecord(c->ev[1], s));
+  for (int h = 0; h <= f.Hmax; ++h) launch_dp_level(c, w, W, rho, h, s);
+  CK(cudaEventRecord(c->ev[2], s));
+  for (int h = f.Hmax; h >= 0; --h) launch_backtrack_level(c, h, s);
+  CK(cudaEventRecord(c->ev[3], s));
+  launch_demand(c, s);
+  launch_scan_lines(c, true, p->hist_w, tof_part, s);
+  launch_sum_roots(c, J_part, nullptr, s);
+  CK(cudaEventRecord(c->ev[4], s));
+  CK(cudaGetLastError());
+  gr.P_valid = true;
+  gr.P_hist_w = p->hist_w;
+  f.have_assign = true;
+  if (!stats) return LA_OK;
+  CK(cudaStreamSynchronize(s));
+  int code;
+  long long idx;
+  TRY(read_dev_err(c, &code, &idx));
+  if (code) return set_err(c, LA_ERR_DEVICE_CHECK, "la_assign_round: %s (index %lld)", dev_err_name(code), idx);
+  Stats hs;
+  CK(cudaMemcpy(&hs, c->d_stats, sizeof hs, cudaMemcpyDeviceToHost));
+  const int nsb = scan_blocks(gr.li), njb = int((f.N + 255) / 256);
+  std::vector<double> part(size_t(f.red_cap) * 2);
+  CK(cudaMemcpy(part.data(), f.red, sizeof(double) * part.size(), cudaMemcpyDeviceToHost));
+  double tof = 0.0, J = 0.0;
+  for (int i = 0; i < nsb; ++i) tof += part[i];
+  for (int i = 0; i < njb; ++i) J += part[f.red_cap + i];
+  float ms = 0.f, ms_dp = 0.f, ms_bt = 0.f, ms_dem = 0.f;
+  CK(cudaEventElapsedTime(&ms, c->ev[0], c->ev[4]));
+  CK(cudaEventElapsedTime(&ms_dp, c->ev[1], c->ev[2]));
+  CK(cudaEventElapsedTime(&ms_bt, c->ev[2], c->ev[3]));
+  CK(cudaEventElapsedTime(&ms_dem, c->ev[3], c->ev[4]));
+  memset(stats, 0, sizeof *stats);
+  stats->total_cost = J;
+  stats->tof = tof;
+  stats->relu_overflow = (int64_t)hs.relu;
+  stats->vias = (int64_t)hs.vias;
+  stats->wl = (int64_t)hs.wl;
+  for (int l = 0; l < LA_MAX_LAYERS; ++l) stats->wl_per_layer[l] = (int64_t)hs.wl_layer[l];
+  stats->ms = ms;
+  stats->ms_dp = ms_dp;
+  stats->ms_backtrack = ms_bt;
+  stats->ms_demand = ms_dem;
+  stats->launches = c->launches - launches0;
+  return LA_OK;
+}
+
+la_status la_get_assignment(la_ctx* c, int8_t* layer, int8_t* b, int8_t* t) {
+  TRY(check_loaded(c));
+  if (!c->forest.have_assign) return set_err(c, LA_ERR_STATE, "no assignment yet");
+  DeviceGuard g(c->device);
+  const size_t V = size_t(c->forest.V);
+  if (layer) CK(cudaMemcpyAsync(layer, c->forest.layer, V, cudaMemcpyDeviceToDevice, c->stream));
+  if (b) CK(cudaMemcpyAsync(b, c->forest.b, V, cudaMemcpyDeviceToDevice, c->stream));
+  if (t) CK(cudaMemcpyAsync(t, c->forest.t, V, cudaMemcpyDeviceToDevice, c->stream));
+  return LA_OK;
+}
+
+la_status la_set_assignment(la_ctx* c, const int8_t* layer, const int8_t* b, const int8_t* t) {
+  TRY(check_loaded(c));
+  if (!layer || !b || !t) return set_err(c, LA_ERR_INVALID, "la_set_assignment: null pointer");
+  DeviceGuard g(c->device);
+  const size_t V = size_t(c->forest.V);
+  TRY(reset_dev_err(c));
+  launch_check_assignment(c, layer, b, t, c->stream);
+  CK(cudaGetLastError());
+  int code;
+  long long idx;
+  TRY(read_dev_err(c, &code, &idx));
+  if (code) return set_err(c, LA_ERR_INVALID, "la_set_assignment: %s (node %lld)", dev_err_name(code), idx);
+  CK(cudaMemcpyAsync(c->forest.layer, layer, V, cudaMemcpyDeviceToDevice, c->stream));
+  CK(cudaMemcpyAsync(c->forest.b, b, V, cudaMemcpyDeviceToDevice, c->stream));
+  CK(cudaMemcpyAsync(c->forest.t, t, V, cudaMemcpyDeviceToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->forest.have_assign = true;
+  return LA_OK;
+}
+
+la_status la_get_net_cost(la_ctx* c, double* J) {
+  TRY(check_loaded(c));
+  if (!J) return set_err(c, LA_ERR_INVALID, "la_get_net_cost: null pointer");
+  if (!c->forest.have_assign) return set_err(c, LA_ERR_STATE, "no round run yet");
+  DeviceGuard g(c->device);
+  launch_sum_roots(c, c->forest.red + c->forest.red_cap, J, c->stream);
+  CK(cudaGetLastError());
+  return LA_OK;
+}
+
+la_status la_get_state(la_ctx* c, int32_t* demand, int32_t* history) {
+  TRY(check_ctx(c));
+  if (!c->grid.loaded) return set_err(c, LA_ERR_STATE, "load a grid first");
+  DeviceGuard g(c->device);
+  Grid& gr = c->grid;
+  if (demand) launch_grid_to_internal(gr.li, gr.X, gr.Y, demand, gr.D, false, c->d_err, c->stream);
+  if (history) launch_grid_to_internal(gr.li, gr.X, gr.Y, history, gr.H, false, c->d_err, c->stream);
+  c->launches += (demand != nullptr) + (history != nullptr);
+  CK(cudaGetLastError());
+  return LA_OK;
+}
+
+la_status la_set_state(la_ctx* c, const int32_t* demand, const int32_t* history) {
+  TRY(check_ctx(c));
+  if (!c->grid.loaded) return set_err(c, LA_ERR_STATE, "load a grid first");
+  DeviceGuard g(c->device);
+  Grid& gr = c->grid;
+  // stage through the difference array (all zero between rounds) so that a
+  // negative value leaves the snapshot unchanged
+  TRY(reset_dev_err(c));
+  int code;
+  long long idx;
+  const int32_t* src[2] = {demand, history};
+  int32_t* dst[2] = {gr.D, gr.H};
+  for (int k = 0; k < 2; ++k) {
+    if (!src[k]) continue;
+    CK(cudaMemsetAsync(gr.diff, 0, gr.G * 4, c->stream));
+    launch_grid_to_internal(gr.li, gr.X, gr.Y, src[k], gr.diff, true, c->d_err, c->stream);
+    ++c->launches;
+    CK(cudaGetLastError());
+    TRY(read_dev_err(c, &code, &idx));
+    if (code) {
+      CK(cudaMemsetAsync(gr.diff, 0, gr.G * 4, c->stream));
+      return set_err(c, LA_ERR_INVALID, "la_set_state: value at edge %lld is negative", idx);
+    }
+    CK(cudaMemcpyAsync(dst[k], gr.diff, gr.G * 4, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemsetAsync(gr.diff, 0, gr.G * 4, c->stream));
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  gr.P_valid = false;
+  return LA_OK;
+}
+
+// ------------------------------------------------------------------------
+static la_status check_assigned(la_ctx* c) {
+  TRY(check_loaded(c));
+  if (!c->forest.have_assign) return set_err(c, LA_ERR_STATE, "no assignment yet (run a round or la_set_assignment)");
+  return LA_OK;
+}
+
+la_status la_rc_from_assignment(la_ctx* c, double* R, double* C) {
+  TRY(check_assigned(c));
+  if (!R || !C) return set_err(c, LA_ERR_INVALID, "la_rc_from_assignment: null pointer");
+  DeviceGuard g(c->device);
+  launch_rc_from_assignment(c, R, C, c->stream);
+  CK(cudaGetLastError());
+  return LA_OK;
+}
+
+la_status la_elmore(la_ctx* c, const double* R, const double* C, double* delay) {
+  TRY(check_assigned(c));
+  if (!R || !C || !delay) return set_err(c, LA_ERR_INVALID, "la_elmore: null pointer");
+  DeviceGuard g(c->device);
+  launch_elmore_fwd(c, R, C, delay, c->stream);
+  CK(cudaGetLastError());
+  return LA_OK;
+}
+
+la_status la_elmore_backward(la_ctx* c, const double* R, const double* C, const double* gd, double* dR, double* dC) {
+  TRY(check_assigned(c));
+  if (!R || !C || !gd || !dR || !dC) return set_err(c, LA_ERR_INVALID, "la_elmore_backward: null pointer");
+  DeviceGuard g(c->device);
+  launch_elmore_bwd(c, R, C, gd, dR, dC, nullptr, nullptr, c->stream);
+  CK(cudaGetLastError());
+  return LA_OK;
+}
+
+la_status la_reweight_adjoint(la_ctx* c) {
+  TRY(check_assigned(c));
+  DeviceGuard g(c->device);
+  Forest& f = c->forest;
+  // R and C of the assignment in scratch s1/s2; the adjoint with g = kappa at pins
+  launch_rc_from_assignment(c, f.s1, f.s2, c->stream);
+  launch_elmore_bwd(c, f.s1, f.s2, f.gk, nullptr, nullptr, f.W_adj, f.rho_adj, c->stream);
+  CK(cudaGetLastError());
+  f.have_adj = true;
+  return LA_OK;
+}
+
+la_status la_get_weights(la_ctx* c, int32_t source, double* W, double* rho) {
+  TRY(check_loaded(c));
+  Forest& f = c->forest;
+  if (source != LA_WEIGHTS_EQ4 && source != LA_WEIGHTS_ADJOINT)
+    return set_err(c, LA_ERR_INVALID, "la_get_weights: unknown source %d", source);
+  if (source == LA_WEIGHTS_ADJOINT && !f.have_adj) return set_err(c, LA_ERR_STATE, "no adjoint weights yet");
+  DeviceGuard g(c->device);
+  const size_t bytes = sizeof(double) * size_t(f.V);
+  if (W) CK(cudaMemcpyAsync(W, source ? f.W_adj : f.W_eq4, bytes, cudaMemcpyDeviceToDevice, c->stream));
+  if (rho) CK(cudaMemcpyAsync(rho, source ? f.rho_adj : f.rho_eq4, bytes, cudaMemcpyDeviceToDevice, c->stream));
+  return LA_OK;
+}
+
+}  // extern "C"

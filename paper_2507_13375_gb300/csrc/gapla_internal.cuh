@@ -1,0 +1,232 @@
+// gapla_internal.cuh - internal data layout and device helpers of the GB300
+// layer-assignment library (the public C ABI is include/gapla.h).
+//
+// HBM layout
+//   Grid arrays are stored per preferred direction d (0 = H, 1 = V) as
+//   [line][pos][ld]: line = row y (H) or column x (V); pos = GCell edge offset
+//   along the line (npos = X for H, Y for V; the last pos is a sentinel used by
+//   the demand difference array); ld = index of the layer among the layers of
+//   direction d.  All layers of one direction that a segment may take are thus
+//   adjacent in memory: the DP reads the congestion prefix of all of them at a
+//   segment end with one contiguous load.
+//   Per-node tables (A, Cc, M, via stacks) are [node][LD] with LD = the larger
+//   per-direction layer count; entries of a son are [son][LD] indexed by the
+//   parent's candidate index.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/gapla.h"
+
+namespace gapla {
+
+constexpr int kMaxL = LA_MAX_LAYERS;
+constexpr int64_t kPenMax = int64_t(1) << 48;
+
+// Device error word: (index << 8) | code, smallest wins (atomicMin).
+enum DevErr : int {
+  DE_NONE = 0,
+  DE_NETPTR = 1,      // net_ptr not increasing / out of range
+  DE_PARENT = 2,      // parent id out of order
+  DE_COORD = 3,       // x / y outside the grid
+  DE_SEGMENT = 4,     // segment not straight or of zero length
+  DE_PIN = 5,         // pin layer out of range, or root without a pin
+  DE_VALUE = 6,       // negative or non-finite cap / criticality / driver R
+  DE_ASSIGN = 7,      // assignment layer of the wrong direction / stack not covering
+  DE_DEGREE = 8,      // more sons than the kernels support
+  DE_NOSTACK = 9,     // DP found no valid stack (internal)
+};
+constexpr unsigned long long kNoErr = ~0ull;
+
+// Everything a kernel needs about the layer stack; passed by value.
+struct LayerInfo {
+  int L;
+  int nld[2];                 // layers per direction
+  int lay[2][kMaxL];          // the layers of each direction, ascending
+  int ld_of[kMaxL];           // index of layer l within its direction
+  int8_t dir[kMaxL];
+  uint32_t mask[2];           // bitmask of the layers of each direction
+  double unit_r[kMaxL], unit_c[kMaxL], half_c[kMaxL];
+  double rbar[2];             // mean unit R of each direction (look-ahead r_est)
+  double via_c;
+  int32_t nlines[2], npos[2]; // per direction
+  int64_t grid_off[2];        // offset of direction d's [line][pos][ld] block (elements)
+  int64_t pub_off[kMaxL + 1]; // offset of layer l in the public edge layout
+};
+
+// Small per-grid tables every DP/backtrack/demand kernel reads with
+// thread-varying indices; kernels copy them to shared memory (load_tables).
+struct DevTables {
+  double rv[kMaxL * kMaxL];   // Rvia(a, b) = sum of via R between layers a and b
+  double unit_r[kMaxL], unit_c[kMaxL], half_c[kMaxL];
+  double via_c;
+  int64_t grid_off[2];
+  int32_t npos[2], nlines[2], nld[2];
+  uint32_t mask[2];
+  int32_t L, pad_;
+  int8_t lay[2][kMaxL];
+  int8_t ld_of[kMaxL];
+  int8_t dir[kMaxL];
+};
+static_assert(sizeof(DevTables) % 8 == 0, "DevTables is copied as 8-byte words");
+
+// Segment geometry of a non-root node, packed:
+// bit 63: direction, bits 32..47 line, 16..31 lo, 0..15 len.
+__host__ __device__ inline uint64_t pack_geo(int d, int line, int lo, int len) {
+  return (uint64_t(d) << 63) | (uint64_t(uint32_t(line)) << 32) | (uint64_t(uint32_t(lo)) << 16) |
+         uint64_t(uint32_t(len));
+}
+__host__ __device__ inline int geo_dir(uint64_t g) { return int(g >> 63); }
+__host__ __device__ inline int geo_line(uint64_t g) { return int((g >> 32) & 0xFFFF); }
+__host__ __device__ inline int geo_lo(uint64_t g) { return int((g >> 16) & 0xFFFF); }
+__host__ __device__ inline int geo_len(uint64_t g) { return int(g & 0xFFFF); }
+
+struct Forest {
+  int64_t N = 0, V = 0;
+  int Hmax = 0;                         // max height (levels 0..Hmax)
+  std::vector<int64_t> lvl_off;         // host copy, Hmax + 2 entries
+  // device arrays (node ids are int32: V < 2^31)
+  int64_t* net_ptr = nullptr;           // N + 1
+  int32_t* parent_g = nullptr;          // global parent id, -1 at roots
+  int32_t* net_of = nullptr;            // net of each node
+  int8_t* pin = nullptr;
+  double* sink_cap = nullptr;
+  double* kappa = nullptr;
+  double* gk = nullptr;                 // kappa at pin nodes, 0 elsewhere (adjoint seed)
+  double* r_drv = nullptr;              // per net
+  uint64_t* geo = nullptr;              // packed segment geometry (0 at roots)
+  int32_t* child_start = nullptr;       // first son slot in child_list
+  int32_t* nch = nullptr;               // number of sons
+  int32_t* child_list = nullptr;        // son ids, increasing within a parent
+  int32_t* height = nullptr;
+  int32_t* lvl_nodes = nullptr;         // nodes sorted by level
+  double* W_eq4 = nullptr;
+  double* rho_eq4 = nullptr;
+  double* W_adj = nullptr;
+  double* rho_adj = nullptr;
+  bool have_adj = false;
+  // round tables
+  double* A = nullptr;                  // [V][LD]
+  double* Cc = nullptr;
+  double* M = nullptr;
+  int8_t* sb = nullptr;                 // [V][LD] chosen stack bottom
+  int8_t* st = nullptr;                 // [V][LD] chosen stack top
+  int8_t* ent = nullptr;                // [V][LD] layer of this son per parent candidate
+  double* Jroot = nullptr;              // [V], valid at roots
+  int8_t* layer = nullptr;              // [V]
+  int8_t* b = nullptr;
+  int8_t* t = nullptr;
+  bool have_assign = false;
+  // Elmore scratch
+  double* s0 = nullptr;                 // [V]
+  double* s1 = nullptr;
+  double* s2 = nullptr;
+  double* red = nullptr;                // reduction partials: [red_cap] tof, [red_cap] J
+  int red_cap = 0;
+};
+
+struct Grid {
+  bool loaded = false;
+  int X = 0, Y = 0;
+  int64_t E = 0;                        // public edge count
+  int64_t G = 0;                        // internal element count (both directions)
+  LayerInfo li;
+  double via_r[kMaxL] = {0};
+  double ofw[kMaxL] = {0};
+  double rvia[kMaxL * kMaxL] = {0};     // Rvia(a, b) table
+  int64_t pen_T[kMaxL * 2 * 129] = {0}; // penalty table
+  int32_t* cap = nullptr;               // internal layout, G elements
+  int32_t* D = nullptr;
+  int32_t* H = nullptr;
+  int32_t* diff = nullptr;
+  int64_t* P = nullptr;
+  int64_t* T_dev = nullptr;             // penalty table on the device
+  double* tofT_dev = nullptr;           // ofw_l exp(s over) for over in [-128, 128]
+  DevTables tab;                        // host copy
+  DevTables* tab_dev = nullptr;
+  bool P_valid = false;                 // P holds the prefix of the current (D, H, hist_w)
+  double P_hist_w = -1.0;
+};
+
+struct Stats {  // device accumulators of one round
+  unsigned long long vias, wl, relu;
+  unsigned long long wl_layer[kMaxL];
+};
+
+}  // namespace gapla
+
+struct la_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool poisoned = false;
+  std::string err;
+  size_t bytes = 0;
+  gapla::Grid grid;
+  gapla::Forest forest;
+  unsigned long long* d_err = nullptr;  // device error word
+  gapla::Stats* d_stats = nullptr;
+  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  int LD = 0;
+  long long launches = 0;               // kernels launched (host-side count)
+  void* alloc_groups = nullptr;         // device allocations, grouped per load
+};
+
+namespace gapla {
+
+// ------------------------------- kernels --------------------------------
+// k_load.cu
+// to_internal: public -> internal (and negative values are reported in err);
+// otherwise internal -> public (pub is written).
+void launch_grid_to_internal(const LayerInfo& li, int X, int Y, const int32_t* pub, int32_t* inter,
+                             bool to_internal, unsigned long long* err, cudaStream_t s);
+void launch_forest_prepare(la_ctx* c, Forest& f, const la_net_desc* d, int* d_hmax, cudaStream_t s);
+void launch_level_sort(Forest& f, int32_t* lvl_cnt, int64_t* lvl_cursor, cudaStream_t s);
+void launch_weights_eq4(const LayerInfo& li, Forest& f, cudaStream_t s);
+void launch_check_assignment(la_ctx* c, const int8_t* layer, const int8_t* b, const int8_t* t,
+                             cudaStream_t s);
+// k_round.cu
+struct RoundW {
+  double w_cong, w_via, w_cap, w_d, hist_w;
+};
+void launch_scan_lines(la_ctx* c, bool from_diff, double hist_w, double* red_tof, cudaStream_t s);
+void launch_dp_level(la_ctx* c, const RoundW& w, const double* W, const double* rho, int level,
+                     cudaStream_t s);
+void launch_backtrack_level(la_ctx* c, int level, cudaStream_t s);
+void launch_demand(la_ctx* c, cudaStream_t s);
+void launch_sum_roots(la_ctx* c, double* part, double* J_out, cudaStream_t s);
+int scan_blocks(const LayerInfo& li);
+// k_elmore.cu
+void launch_rc_from_assignment(la_ctx* c, double* R, double* C, cudaStream_t s);
+void launch_elmore_fwd(la_ctx* c, const double* R, const double* C, double* delay, cudaStream_t s);
+void launch_elmore_bwd(la_ctx* c, const double* R, const double* C, const double* g, double* dR,
+                       double* dC, double* Wsum_out, double* UJ_out, cudaStream_t s);
+
+// small device helpers
+__device__ __forceinline__ void dev_error(unsigned long long* err, int code, int64_t index) {
+  unsigned long long key = (static_cast<unsigned long long>(index) << 8) | static_cast<unsigned long long>(code);
+  atomicMin(err, key);
+}
+// Order of non-negative doubles through their bit patterns (integer compare,
+// no FP64 pipe): a < b  <=>  bits(a) < bits(b) for a, b >= +0, not NaN.
+__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
+
+// Copy the tables to shared memory; every thread of the block must call it.
+__device__ __forceinline__ void load_tables(DevTables& s, const DevTables* g) {
+  const unsigned long long* src = reinterpret_cast<const unsigned long long*>(g);
+  unsigned long long* dst = reinterpret_cast<unsigned long long*>(&s);
+  for (int i = threadIdx.x; i < int(sizeof(DevTables) / 8); i += blockDim.x) dst[i] = src[i];
+  __syncthreads();
+}
+
+// Butterfly warp sum: the same lanes pair up on every run (deterministic).
+template <typename T>
+__device__ __forceinline__ T warp_sum(T x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+}  // namespace gapla

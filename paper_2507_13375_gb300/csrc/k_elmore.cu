@@ -1,0 +1,153 @@
+// k_elmore.cu - Elmore delay on the RC tree of an assignment (Sec. II-C, and the
+// worked example d_34 = R_34 (C4 + C5 + C6 + C7) of Sec. III-D) and its adjoint.
+//
+// RC tree: driver R into the root junction J_root; for a segment v, a via
+// resistor Rvia(l_p, l_v) from J_p to X_v (C_seg/2 at X_v), the wire R_seg[v]
+// from X_v to J_v (C_seg/2 + vc (t - b) + the pin cap below J_v); at a pin
+// node a via resistor Rvia(l_v, p_v) to the pin point holding the sink cap.
+// Level passes: downstream caps bottom-up (levels ascending), delays and
+// upstream weighted resistances top-down (levels descending).  Sums over sons
+// run in son order, as in the oracle.
+#include "gapla_internal.cuh"
+
+namespace gapla {
+
+__global__ void k_rc(int64_t V, const DevTables* __restrict__ tab, const int32_t* __restrict__ parent_g,
+                     const uint64_t* __restrict__ geo, const int8_t* __restrict__ layer, double* __restrict__ R,
+                     double* __restrict__ C) {
+  const int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (v >= V) return;
+  if (parent_g[v] < 0) {
+    R[v] = 0.0;
+    C[v] = 0.0;
+    return;
+  }
+  const int l = layer[v];
+  const double len = double(geo_len(geo[v]));
+  R[v] = len * tab->unit_r[l];
+  C[v] = len * tab->unit_c[l];
+}
+
+void launch_rc_from_assignment(la_ctx* c, double* R, double* C, cudaStream_t s) {
+  Forest& f = c->forest;
+  k_rc<<<(unsigned)((f.V + 255) / 256), 256, 0, s>>>(f.V, c->grid.tab_dev, f.parent_g, f.geo, f.layer, R, C);
+  ++c->launches;
+}
+
+struct ElmArgs {
+  const int32_t *nodes, *parent_g, *child_start, *nch, *child_list, *net_of;
+  int64_t count;
+  const int8_t *layer, *b, *t, *pin;
+  const double *sink_cap, *r_drv, *R, *C, *g;
+  const DevTables* tab;
+  double *CdJ, *Ws, *dJ, *delay, *UJ, *dR, *dC;
+};
+
+// Bottom-up: Cd_J(v) = C_seg[v]/2 + vc (t - b) + Cs_v + sum over sons of
+// (C_seg[c]/2 + Cd_J(c)); with g, also Ws(v) = g_v + sum over sons of Ws(c).
+__global__ void k_elm_up(ElmArgs a) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= a.count) return;
+  const int v = a.nodes[i];
+  double s = a.parent_g[v] < 0 ? 0.0 : 0.5 * a.C[v];
+  s = s + a.tab->via_c * double(a.t[v] - a.b[v]);
+  s = s + a.sink_cap[v];
+  const int cs = a.child_start[v], nc = a.nch[v];
+  for (int j = 0; j < nc; ++j) {
+    const int c = a.child_list[cs + j];
+    s = s + (0.5 * a.C[c] + a.CdJ[c]);
+  }
+  a.CdJ[v] = s;
+  if (a.Ws) {
+    double w = a.g[v];
+    for (int j = 0; j < nc; ++j) w = w + a.Ws[a.child_list[cs + j]];
+    a.Ws[v] = w;
+  }
+}
+
+// Top-down forward: delay at junctions, then at the pin point.
+__global__ void k_elm_delay(ElmArgs a) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= a.count) return;
+  const int v = a.nodes[i];
+  const int p = a.parent_g[v];
+  const int lv = a.layer[v];
+  double dj;
+  if (p < 0) {
+    dj = a.r_drv[a.net_of[v]] * a.CdJ[v];
+  } else {
+    const double dX = a.dJ[p] + a.tab->rv[a.layer[p] * kMaxL + lv] * (0.5 * a.C[v] + a.CdJ[v]);
+    dj = dX + a.R[v] * a.CdJ[v];
+  }
+  a.dJ[v] = dj;
+  const int pin = a.pin[v];
+  a.delay[v] = pin >= 0 ? dj + a.tab->rv[lv * kMaxL + pin] * a.sink_cap[v] : dj;
+}
+
+// Top-down adjoint: U_J(root) = R_drv Ws(root); U_X(v) = U_J(p) + Rvia Ws(v);
+// U_J(v) = U_X(v) + R_seg[v] Ws(v); dR = Cd_J Ws; dC = (U_X + U_J) / 2.
+__global__ void k_elm_adj(ElmArgs a) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= a.count) return;
+  const int v = a.nodes[i];
+  const int p = a.parent_g[v];
+  if (p < 0) {
+    a.UJ[v] = a.r_drv[a.net_of[v]] * a.Ws[v];
+    if (a.dR) { a.dR[v] = 0.0; a.dC[v] = 0.0; }
+    return;
+  }
+  const double w = a.Ws[v];
+  const double UX = a.UJ[p] + a.tab->rv[a.layer[p] * kMaxL + a.layer[v]] * w;
+  const double uj = UX + a.R[v] * w;
+  a.UJ[v] = uj;
+  if (a.dR) {
+    a.dR[v] = a.CdJ[v] * w;
+    a.dC[v] = 0.5 * (UX + uj);
+  }
+}
+
+static ElmArgs elm_args(la_ctx* c, const double* R, const double* C) {
+  Forest& f = c->forest;
+  ElmArgs a{};
+  a.parent_g = f.parent_g; a.child_start = f.child_start; a.nch = f.nch; a.child_list = f.child_list;
+  a.net_of = f.net_of; a.layer = f.layer; a.b = f.b; a.t = f.t; a.pin = f.pin; a.sink_cap = f.sink_cap;
+  a.r_drv = f.r_drv; a.R = R; a.C = C; a.tab = c->grid.tab_dev;
+  return a;
+}
+
+template <typename K>
+static void per_level(la_ctx* c, ElmArgs a, K kernel, bool ascending, cudaStream_t s) {
+  Forest& f = c->forest;
+  for (int q = 0; q <= f.Hmax; ++q) {
+    const int h = ascending ? q : f.Hmax - q;
+    a.nodes = f.lvl_nodes + f.lvl_off[h];
+    a.count = f.lvl_off[h + 1] - f.lvl_off[h];
+    if (a.count == 0) continue;
+    kernel<<<(unsigned)((a.count + 255) / 256), 256, 0, s>>>(a);
+    ++c->launches;
+  }
+}
+
+void launch_elmore_fwd(la_ctx* c, const double* R, const double* C, double* delay, cudaStream_t s) {
+  ElmArgs a = elm_args(c, R, C);
+  a.CdJ = c->forest.s0;
+  a.dJ = c->forest.s1;
+  a.delay = delay;
+  per_level(c, a, k_elm_up, true, s);
+  per_level(c, a, k_elm_delay, false, s);
+}
+
+void launch_elmore_bwd(la_ctx* c, const double* R, const double* C, const double* g, double* dR, double* dC,
+                       double* Ws_out, double* UJ_out, cudaStream_t s) {
+  ElmArgs a = elm_args(c, R, C);
+  a.g = g;
+  a.CdJ = c->forest.s0;
+  a.Ws = Ws_out ? Ws_out : c->forest.s1;
+  a.UJ = UJ_out ? UJ_out : c->forest.s2;
+  a.dR = dR;
+  a.dC = dC;
+  per_level(c, a, k_elm_up, true, s);
+  per_level(c, a, k_elm_adj, false, s);
+}
+
+}  // namespace gapla

@@ -1,0 +1,486 @@
+// k_round.cu - one layer-assignment round on the GPU: congestion penalty and
+// line prefix (reading of Eq. 3), the bottom-up DP of Alg. 3 (Kernel 1 and
+// Kernel 2 fused: per node and parent-edge layer, enumerate the via stacks,
+// let every son take its best layer by look-ahead cost (Sec. III-D), keep the
+// stack of least f'), the top-down backtrack of Alg. 4, and the demand / via
+// update of the demand map D (Alg. 2).
+//
+// Arithmetic is FP64 with the oracle's expression trees: nvcc --fmad=false,
+// fma() exactly where the oracle calls fma().  Minima over non-negative
+// doubles compare their bit patterns as int64 (exact, and it keeps the
+// comparisons off the FP64 pipe, which GB300 runs at 1/64 of FP32).
+#include <climits>
+
+#include "gapla_internal.cuh"
+
+namespace gapla {
+
+// ---------------------------------------------------------------------------
+// Penalty + prefix per line.  One warp per (direction, line); lane j handles
+// edge position chunk*32 + j for every layer of the direction, so each step
+// reads 32 * nld contiguous elements.  from_diff = 1 also folds the demand
+// difference array into D (and clears it), updates H += max(0, D - C) and
+// accumulates the overflow statistics of the new demand.
+// ---------------------------------------------------------------------------
+struct ScanArgs {
+  int32_t *cap, *D, *H, *diff;
+  int64_t* P;
+  const int64_t* T;         // [L][2][129]
+  const double* tofT;       // [L][2][257] = ofw_l exp(s over), over in [-128, 128]
+  int64_t HW;
+  int from_diff;
+  double* tof_part;         // one per block
+  unsigned long long* relu;
+};
+
+template <typename Tv>
+__device__ __forceinline__ Tv warp_incl_scan(Tv x, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    Tv y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  return x;
+}
+
+__global__ void __launch_bounds__(256) k_scan_lines(const DevTables* __restrict__ tab, ScanArgs a) {
+  __shared__ double s_tof[8];
+  __shared__ unsigned long long s_relu[8];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int64_t gl = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int nl0 = tab->nlines[0];
+  const int64_t nl_total = int64_t(nl0) + tab->nlines[1];
+  double tof = 0.0;
+  unsigned long long relu = 0;
+  if (gl < nl_total) {
+    const int d = gl < nl0 ? 0 : 1;
+    const int64_t line = gl - (d ? nl0 : 0);
+    const int nld = tab->nld[d], npos = tab->npos[d];
+    const int64_t base = tab->grid_off[d] + line * npos * nld;
+    int lays[kMaxL];
+#pragma unroll
+    for (int q = 0; q < kMaxL; ++q) lays[q] = tab->lay[d][q];
+    int32_t carryD[kMaxL];
+    int64_t carryP[kMaxL];
+#pragma unroll
+    for (int q = 0; q < kMaxL; ++q) { carryD[q] = 0; carryP[q] = 0; }
+    for (int c0 = 0; c0 < npos; c0 += 32) {
+      const int pos = c0 + lane;
+      const bool valid = pos < npos;
+      const bool edge = pos < npos - 1;
+#pragma unroll
+      for (int q = 0; q < kMaxL; ++q) {
+        if (q >= nld) break;
+        const int64_t idx = base + int64_t(pos) * nld + q;
+        const int l = lays[q];
+        int32_t Dv;
+        if (a.from_diff) {
+          int32_t dv = 0;
+          if (valid) { dv = a.diff[idx]; a.diff[idx] = 0; }
+          Dv = warp_incl_scan<int32_t>(dv, lane) + carryD[q];
+          carryD[q] = __shfl_sync(0xffffffffu, Dv, 31);
+          if (edge) a.D[idx] = Dv;
+        } else {
+          Dv = edge ? a.D[idx] : 0;
+        }
+        int64_t pen = 0;
+        if (edge) {
+          const int32_t c = a.cap[idx];
+          int32_t h = a.H[idx];
+          const int si = c > 0 ? 0 : 1;
+          if (a.from_diff) {
+            const int32_t over = Dv - c;
+            if (over > 0) { h += over; a.H[idx] = h; relu += (unsigned long long)over; }
+            if (over >= -128 && over <= 128) tof += a.tofT[(l * 2 + si) * 257 + (over + 128)];
+            else tof += a.tofT[(l * 2 + si) * 257 + 128] * exp((si ? 1.5 : 0.5) * double(over));
+          }
+          int kk = Dv + 1 - c;
+          kk = kk < -64 ? -64 : (kk > 64 ? 64 : kk);
+          const int64_t tv = a.T[(l * 2 + si) * 129 + (kk + 64)];
+          if (h > 0 && a.HW > 0 && int64_t(h) > (kPenMax - tv) / a.HW) pen = kPenMax;
+          else pen = tv + a.HW * int64_t(h);
+          if (pen > kPenMax) pen = kPenMax;
+        }
+        const int64_t incl = warp_incl_scan<int64_t>(pen, lane);
+        if (valid) a.P[idx] = carryP[q] + (incl - pen);
+        carryP[q] += __shfl_sync(0xffffffffu, incl, 31);
+      }
+    }
+  }
+  // deterministic block reduction of the statistics
+  tof = warp_sum(tof);
+  relu = warp_sum(relu);
+  if (lane == 0) { s_tof[wib] = tof; s_relu[wib] = relu; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    unsigned long long r = 0;
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) { t += s_tof[w]; r += s_relu[w]; }
+    a.tof_part[blockIdx.x] = t;
+    if (r) atomicAdd(a.relu, r);
+  }
+}
+
+int scan_blocks(const LayerInfo& li) {
+  const int64_t lines = int64_t(li.nlines[0]) + li.nlines[1];
+  return int((lines * 32 + 255) / 256);
+}
+
+void launch_scan_lines(la_ctx* c, bool from_diff, double hist_w, double* tof_part, cudaStream_t s) {
+  Grid& g = c->grid;
+  ScanArgs a;
+  a.cap = g.cap; a.D = g.D; a.H = g.H; a.diff = g.diff; a.P = g.P; a.T = g.T_dev; a.tofT = g.tofT_dev;
+  a.HW = llround(hist_w * 16777216.0);
+  a.from_diff = from_diff ? 1 : 0;
+  a.tof_part = tof_part;
+  a.relu = &c->d_stats->relu;
+  k_scan_lines<<<scan_blocks(g.li), 256, 0, s>>>(g.tab_dev, a);
+  ++c->launches;
+}
+
+// ---------------------------------------------------------------------------
+// DP over one level (Alg. 3).  One thread per (node, candidate junction layer):
+// the segment's layers, or the driver pin layer at a root.
+// ---------------------------------------------------------------------------
+struct DPArgs {
+  int LD;
+  const int32_t* nodes;
+  int64_t count;
+  const int32_t *parent_g, *child_start, *nch, *child_list;
+  const int8_t* pin;
+  const double *sink_cap, *kappa, *W, *rho;
+  const uint64_t* geo;
+  const int64_t* P;
+  const DevTables* tab;
+  double *A, *Cc, *M, *Jroot;
+  int8_t *sb, *st, *ent;
+  double w_cong_s, w_cap, w_d, sigma0;
+  unsigned long long* err;
+};
+
+// (fp, k, b) lexicographic order of Kernel 2 (least f', fewest vias, lowest b).
+__device__ __forceinline__ bool stack_better(long long f, int k, int b, long long bf, int bk, int bb) {
+  return f < bf || (f == bf && (k < bk || (k == bk && b < bb)));
+}
+
+template <int LMAX>
+__global__ void __launch_bounds__(256) k_dp_level(LayerInfo li, DPArgs a) {
+  __shared__ DevTables s;
+  load_tables(s, a.tab);
+  const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t node_i = k / a.LD;
+  const int ldi = int(k - node_i * a.LD);
+  if (node_i >= a.count) return;
+  const int v = a.nodes[node_i];
+  const int L = li.L, LD = a.LD;
+  const bool is_root = a.parent_g[v] < 0;
+  const int pin = a.pin[v];
+  const uint64_t gv = a.geo[v];
+  const int d = geo_dir(gv);
+  int l;
+  if (is_root) {
+    if (ldi != 0) return;
+    l = pin;
+  } else {
+    if (ldi >= s.nld[d]) return;
+    l = s.lay[d][ldi];
+  }
+  const double* rvl = &s.rv[l * kMaxL];
+  const double wd_rho = a.w_d * a.rho[v];
+  const double sigma_v = fma(wd_rho, s.via_c, a.sigma0);
+  const double Cs = a.sink_cap[v];
+  const double sinkf = pin >= 0 ? ((a.w_d * a.kappa[v]) * rvl[pin]) * Cs : 0.0;
+  const double z = fma(wd_rho, Cs, sinkf);
+  const int lo_req = pin >= 0 ? min(l, pin) : l;
+  const int hi_req = pin >= 0 ? max(l, pin) : l;
+  const int cs = a.child_start[v], nc = a.nch[v];
+
+  long long bfp = LLONG_MAX;
+  int bb = lo_req, bt = hi_req, bk = INT_MAX;
+  if (nc == 0) {
+    // a leaf: every stack costs tail(t - b); the smallest one wins
+    bfp = dbits(fma(double(hi_req - lo_req), sigma_v, z));
+  } else if (nc == 1) {
+    // one son: only stacks that are the hull of (junction, pin, son layer lc)
+    // with lc the son's own choice inside that hull can win (ties go to fewer
+    // vias); evaluate exactly those.
+    const int c = a.child_list[cs];
+    const int dc = geo_dir(a.geo[c]);
+    const int nldc = s.nld[dc];
+    const double* Ac = a.A + int64_t(c) * LD;
+    const double* Ccc = a.Cc + int64_t(c) * LD;
+    const double* Mc = a.M + int64_t(c) * LD;
+    double key[LMAX];
+#pragma unroll
+    for (int j = 0; j < LMAX; ++j) {
+      if (j < nldc) {
+        const int lc = s.lay[dc][j];
+        key[j] = fma(Mc[j], rvl[lc], fma(wd_rho, Ccc[j], Ac[j]));
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < LMAX; ++j) {
+      if (j < nldc) {
+        const int lc = s.lay[dc][j];
+        const int b0 = min(lo_req, lc), t0 = max(hi_req, lc);
+        const long long kj = dbits(key[j]);
+        bool consistent = true;
+#pragma unroll
+        for (int j2 = 0; j2 < LMAX; ++j2) {
+          if (j2 < nldc && j2 != j) {
+            const int l2 = s.lay[dc][j2];
+            if (l2 >= b0 && l2 <= t0) {
+              const long long k2 = dbits(key[j2]);
+              if (k2 < kj || (k2 == kj && j2 < j)) consistent = false;
+            }
+          }
+        }
+        if (consistent) {
+          const long long f = dbits(key[j] + fma(double(t0 - b0), sigma_v, z));
+          if (stack_better(f, t0 - b0, b0, bfp, bk, bb)) { bfp = f; bk = t0 - b0; bb = b0; bt = t0; }
+        }
+      }
+    }
+  } else {
+    // general case: every stack [b, t] with b <= lo_req <= hi_req <= t;
+    // S[t] accumulates, son by son in order, the son's least key in [b, t].
+    for (int b = 0; b <= lo_req; ++b) {
+      double S[LMAX];
+      bool ok[LMAX];
+#pragma unroll
+      for (int t = 0; t < LMAX; ++t) { S[t] = 0.0; ok[t] = true; }
+      for (int j = 0; j < nc; ++j) {
+        const int c = a.child_list[cs + j];
+        const int dc = geo_dir(a.geo[c]);
+        const uint32_t mask = s.mask[dc];
+        const double* Ac = a.A + int64_t(c) * LD;
+        const double* Ccc = a.Cc + int64_t(c) * LD;
+        const double* Mc = a.M + int64_t(c) * LD;
+        long long rbits = LLONG_MAX;
+        double rkey = 0.0;
+        bool have = false;
+#pragma unroll
+        for (int lc = 0; lc < LMAX; ++lc) {
+          if (lc < L && lc >= b) {
+            if ((mask >> lc) & 1u) {
+              const int jj = s.ld_of[lc];
+              const double key = fma(Mc[jj], rvl[lc], fma(wd_rho, Ccc[jj], Ac[jj]));
+              const long long kb = dbits(key);
+              if (!have || kb < rbits) { have = true; rbits = kb; rkey = key; }
+            }
+            if (lc >= hi_req) {
+              if (!have) ok[lc] = false;
+              else S[lc] = S[lc] + rkey;
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < LMAX; ++t) {
+        if (t < L && t >= hi_req && ok[t]) {
+          const long long f = dbits(S[t] + fma(double(t - b), sigma_v, z));
+          if (stack_better(f, t - b, b, bfp, bk, bb)) { bfp = f; bk = t - b; bb = b; bt = t; }
+        }
+      }
+    }
+  }
+
+  // the winning stack: each son's layer inside [bb, bt], and the table entry
+  double sg = 0.0, sc = 0.0;
+  for (int j = 0; j < nc; ++j) {
+    const int c = a.child_list[cs + j];
+    const int dc = geo_dir(a.geo[c]);
+    const uint32_t mask = s.mask[dc];
+    const double* Ac = a.A + int64_t(c) * LD;
+    const double* Ccc = a.Cc + int64_t(c) * LD;
+    const double* Mc = a.M + int64_t(c) * LD;
+    long long rbits = LLONG_MAX;
+    int rl = -1;
+#pragma unroll
+    for (int lc = 0; lc < LMAX; ++lc) {
+      if (lc >= bb && lc <= bt && ((mask >> lc) & 1u)) {
+        const int jj = s.ld_of[lc];
+        const long long kb = dbits(fma(Mc[jj], rvl[lc], fma(wd_rho, Ccc[jj], Ac[jj])));
+        if (rl < 0 || kb < rbits) { rl = lc; rbits = kb; }
+      }
+    }
+    if (rl < 0) {  // cannot happen for a valid stack; report instead of indexing with -1
+      dev_error(a.err, DE_NOSTACK, v);
+      return;
+    }
+    const int jj = s.ld_of[rl];
+    a.ent[int64_t(c) * LD + ldi] = int8_t(rl);
+    sg = sg + fma(Mc[jj], rvl[rl], Ac[jj]);
+    sc = sc + Ccc[jj];
+  }
+  const int kk = bt - bb;
+  const double fv = sg + fma(double(kk), a.sigma0, sinkf);
+  const double cv = sc + fma(double(kk), s.via_c, Cs);
+  const int64_t o = int64_t(v) * LD + ldi;
+  a.sb[o] = int8_t(bb);
+  a.st[o] = int8_t(bt);
+  if (is_root) {
+    a.Jroot[v] = __longlong_as_double(bfp);
+    return;
+  }
+  const int len = geo_len(gv), line = geo_line(gv), lo = geo_lo(gv);
+  const double R = double(len) * s.unit_r[l];
+  const double C = double(len) * s.unit_c[l];
+  const double Ch = double(len) * s.half_c[l];
+  const double wdW = a.w_d * a.W[v];
+  const double alpha = wdW * R;
+  const double gamma = fma(alpha, Ch, a.w_cap * C);
+  const int nldd = s.nld[d];
+  const int64_t pb = s.grid_off[d] + int64_t(line) * s.npos[d] * nldd + ldi;
+  const int64_t K = a.P[pb + int64_t(lo + len) * nldd] - a.P[pb + int64_t(lo) * nldd];
+  const double seg = fma(a.w_cong_s, double(K), gamma);
+  a.A[o] = fma(alpha, cv, fv + seg);
+  const double ccv = C + cv;
+  a.Cc[o] = ccv;
+  a.M[o] = wdW * ccv;
+}
+
+void launch_dp_level(la_ctx* c, const RoundW& w, const double* W, const double* rho, int level, cudaStream_t s) {
+  Forest& f = c->forest;
+  const int64_t n = f.lvl_off[level + 1] - f.lvl_off[level];
+  if (n == 0) return;
+  DPArgs a;
+  a.LD = c->LD;
+  a.nodes = f.lvl_nodes + f.lvl_off[level];
+  a.count = n;
+  a.parent_g = f.parent_g; a.child_start = f.child_start; a.nch = f.nch; a.child_list = f.child_list;
+  a.pin = f.pin; a.sink_cap = f.sink_cap; a.kappa = f.kappa; a.W = W; a.rho = rho; a.geo = f.geo;
+  a.P = c->grid.P; a.tab = c->grid.tab_dev;
+  a.A = f.A; a.Cc = f.Cc; a.M = f.M; a.Jroot = f.Jroot; a.sb = f.sb; a.st = f.st; a.ent = f.ent;
+  a.w_cong_s = w.w_cong * 0x1.0p-24;
+  a.w_cap = w.w_cap;
+  a.w_d = w.w_d;
+  a.sigma0 = w.w_via + w.w_cap * c->grid.li.via_c;
+  a.err = c->d_err;
+  const int T = 256;
+  const int64_t threads = n * a.LD;
+  const unsigned B = (unsigned)((threads + T - 1) / T);
+  const int L = c->grid.li.L;
+  if (L <= 6) k_dp_level<6><<<B, T, 0, s>>>(c->grid.li, a);
+  else if (L <= 12) k_dp_level<12><<<B, T, 0, s>>>(c->grid.li, a);
+  else k_dp_level<16><<<B, T, 0, s>>>(c->grid.li, a);
+  ++c->launches;
+}
+
+// ---------------------------------------------------------------------------
+// Backtrack (Alg. 4): top-down, one thread per node of the level.
+// ---------------------------------------------------------------------------
+__global__ void k_backtrack_level(const int32_t* __restrict__ nodes, int64_t count, int LD,
+                                  const DevTables* __restrict__ tab, const int32_t* __restrict__ parent_g,
+                                  const int8_t* __restrict__ pin, const int8_t* __restrict__ ent,
+                                  const int8_t* __restrict__ sb, const int8_t* __restrict__ st,
+                                  int8_t* __restrict__ layer, int8_t* __restrict__ b, int8_t* __restrict__ t) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const int v = nodes[i];
+  const int gp = parent_g[v];
+  int l, idx;
+  if (gp < 0) {
+    l = pin[v];
+    idx = 0;
+  } else {
+    const int lp = layer[gp];
+    const int pidx = parent_g[gp] < 0 ? 0 : tab->ld_of[lp];
+    l = ent[int64_t(v) * LD + pidx];
+    idx = tab->ld_of[l];
+  }
+  layer[v] = int8_t(l);
+  b[v] = sb[int64_t(v) * LD + idx];
+  t[v] = st[int64_t(v) * LD + idx];
+}
+
+void launch_backtrack_level(la_ctx* c, int level, cudaStream_t s) {
+  Forest& f = c->forest;
+  const int64_t n = f.lvl_off[level + 1] - f.lvl_off[level];
+  if (n == 0) return;
+  const int T = 256;
+  k_backtrack_level<<<(unsigned)((n + T - 1) / T), T, 0, s>>>(f.lvl_nodes + f.lvl_off[level], n, c->LD,
+                                                            c->grid.tab_dev, f.parent_g, f.pin, f.ent, f.sb,
+                                                            f.st, f.layer, f.b, f.t);
+  ++c->launches;
+}
+
+// ---------------------------------------------------------------------------
+// Demand: +1 at the segment's first edge and -1 past its last edge in the
+// difference array of its line and layer (the line scan folds it into D),
+// plus vias and wirelength per layer.  Integer atomics: exact in any order.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_demand(int64_t V, int L, const DevTables* __restrict__ tab,
+                                                const int32_t* __restrict__ parent_g,
+                                                const uint64_t* __restrict__ geo, const int8_t* __restrict__ layer,
+                                                const int8_t* __restrict__ b, const int8_t* __restrict__ t,
+                                                int32_t* __restrict__ diff, Stats* stats) {
+  __shared__ unsigned long long s_wl[kMaxL];
+  __shared__ unsigned long long s_v[8];
+  if (threadIdx.x < kMaxL) s_wl[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  unsigned long long vias = 0;
+  if (v < V) {
+    vias = (unsigned long long)(t[v] - b[v]);
+    if (parent_g[v] >= 0) {
+      const uint64_t g = geo[v];
+      const int d = geo_dir(g), len = geo_len(g);
+      const int l = layer[v];
+      const int nld = tab->nld[d];
+      const int64_t base = tab->grid_off[d] + (int64_t(geo_line(g)) * tab->npos[d] + geo_lo(g)) * nld + tab->ld_of[l];
+      atomicAdd(diff + base, 1);
+      atomicAdd(diff + base + int64_t(len) * nld, -1);
+      atomicAdd(&s_wl[l], (unsigned long long)len);
+    }
+  }
+  vias = warp_sum(vias);
+  if ((threadIdx.x & 31) == 0) s_v[threadIdx.x >> 5] = vias;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long sv = 0;
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) sv += s_v[w];
+    if (sv) atomicAdd(&stats->vias, sv);
+  }
+  if (threadIdx.x < L && s_wl[threadIdx.x]) {
+    atomicAdd(&stats->wl_layer[threadIdx.x], s_wl[threadIdx.x]);
+    atomicAdd(&stats->wl, s_wl[threadIdx.x]);
+  }
+}
+
+void launch_demand(la_ctx* c, cudaStream_t s) {
+  Forest& f = c->forest;
+  const int T = 256;
+  k_demand<<<(unsigned)((f.V + T - 1) / T), T, 0, s>>>(f.V, c->grid.li.L, c->grid.tab_dev, f.parent_g, f.geo,
+                                                     f.layer, f.b, f.t, c->grid.diff, c->d_stats);
+  ++c->launches;
+}
+
+// Per-block partial sums of the root costs J_n, in net order (deterministic).
+__global__ void __launch_bounds__(256) k_sum_roots(int64_t N, const int64_t* __restrict__ net_ptr,
+                                                   const double* __restrict__ Jroot, double* __restrict__ part,
+                                                   double* __restrict__ J_out) {
+  __shared__ double s_p[8];
+  const int64_t n = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  double x = 0.0;
+  if (n < N) {
+    x = Jroot[net_ptr[n]];
+    if (J_out) J_out[n] = x;
+  }
+  x = warp_sum(x);
+  if ((threadIdx.x & 31) == 0) s_p[threadIdx.x >> 5] = x;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) t += s_p[w];
+    part[blockIdx.x] = t;
+  }
+}
+
+void launch_sum_roots(la_ctx* c, double* part, double* J_out, cudaStream_t s) {
+  Forest& f = c->forest;
+  k_sum_roots<<<(unsigned)((f.N + 255) / 256), 256, 0, s>>>(f.N, f.net_ptr, f.Jroot, part, J_out);
+  ++c->launches;
+}
+
+}  // namespace gapla

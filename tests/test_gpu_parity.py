@@ -1,0 +1,242 @@
+"""GPU (CUDA, sm_103a) vs the FP64 CPU oracle, element by element.
+
+Layers, via stacks, demand, history and vias must match bit for bit; the
+per-net costs J (FP64, same expression trees on both sides) are compared
+exactly too, and the total cost within 1e-9 relative."""
+import numpy as np
+import pytest
+
+import forestgen as fg
+import oracle
+from util_inputs import edge_case_forest, merge_forests, random_snapshot, simple_grid
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def la():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2507_13375_gb300 as la
+
+    la.library()
+    return la
+
+
+def gpu_round(a, weights, reset=False, weights_src=0):
+    st = a.assign_round(reset=reset, weights=weights_src, **weights)
+    layer, b, t = (x.cpu().numpy() for x in a.get_assignment())
+    D, H = (x.cpu().numpy() for x in a.get_state())
+    J = a.get_net_cost().cpu().numpy()
+    return dict(layer=layer, b=b, t=t, D=D, H=H, J=J, stats=st)
+
+
+def assert_same_round(got, ref, label=""):
+    assert np.array_equal(got["layer"], ref["layer"]), f"{label}: layers differ at " \
+        f"{np.nonzero(got['layer'] != ref['layer'])[0][:10]}"
+    assert np.array_equal(got["b"], ref["b"]) and np.array_equal(got["t"], ref["t"]), f"{label}: via stacks"
+    assert np.array_equal(got["J"], ref["J"]), f"{label}: max |dJ|/J = " \
+        f"{np.max(np.abs(got['J'] - ref['J']) / np.maximum(np.abs(ref['J']), 1e-300))}"
+    assert np.array_equal(got["D"], ref["D"]), f"{label}: demand"
+    assert np.array_equal(got["H"], ref["H"]), f"{label}: history"
+    s, r = got["stats"], ref["stats"]
+    assert s["vias"] == r["vias"] and s["wl"] == r["wl"] and s["relu_overflow"] == r["relu_overflow"]
+    assert list(s["wl_per_layer"][: len(r["wl_per_layer"])]) == list(r["wl_per_layer"])
+    assert s["tof"] == pytest.approx(r["tof"], rel=1e-12)
+    assert s["total_cost"] == pytest.approx(r["total_cost"], rel=1e-9)
+
+
+def ref_round(grid, forest, weights, D=None, H=None, W=None, rho=None):
+    """The oracle's round; its stats carry total_cost = sum of J."""
+    return oracle.assign_round(grid, forest, weights, D=D, H=H, W=W, rho=rho)
+
+
+def _assigner(la, grid, forest):
+    a = la.LayerAssigner(0)
+    a.load_grid(grid)
+    a.load_nets(forest)
+    return a
+
+
+def test_round_config1(la):
+    wl = fg.WORKLOADS[1]
+    grid, forest = fg.make_grid(wl, 0), fg.make_forest(wl, 0)
+    a = _assigner(la, grid, forest)
+    got = gpu_round(a, la.DEFAULT_WEIGHTS, reset=True)
+    ref = ref_round(grid, forest, la.DEFAULT_WEIGHTS)
+    assert_same_round(got, ref)
+
+
+@pytest.mark.parametrize("weights", [dict(w_d=0.0), dict(w_d=5e-2, w_cong=1e-2), dict(w_via=0.0, w_cap=0.0),
+                                     dict(hist_w=3.0, w_d=2e-3)])
+def test_round_random_snapshot(la, weights):
+    """Congested random snapshot (D, H) and several weight mixes, 3 rounds,
+    each round's oracle fed the GPU's previous (D, H)."""
+    wl = fg.WORKLOADS[2].scaled(20000)
+    grid, forest = fg.make_grid(wl, 3), fg.make_forest(wl, 3)
+    ww = dict(la.DEFAULT_WEIGHTS, **weights)
+    a = _assigner(la, grid, forest)
+    D, H = random_snapshot(len(grid["cap"]), 3, dmax=18, hmax=4)
+    a.set_state(D, H)
+    for r in range(3):
+        got = gpu_round(a, ww)
+        ref = ref_round(grid, forest, ww, D=D, H=H)
+        assert_same_round(got, ref, f"round {r}")
+        D, H = got["D"], got["H"]
+
+
+def test_multi_round_config2_full(la):
+    """500k nets, 3 negotiation rounds; round r's oracle starts from the GPU's
+    round r-1 snapshot."""
+    wl = fg.WORKLOADS[2]
+    grid, forest = fg.make_grid(wl, 0), fg.make_forest(wl, 0)
+    a = _assigner(la, grid, forest)
+    D = H = None
+    for r in range(wl.rounds):
+        got = gpu_round(a, la.DEFAULT_WEIGHTS, reset=(r == 0))
+        ref = ref_round(grid, forest, la.DEFAULT_WEIGHTS, D=D, H=H)
+        assert_same_round(got, ref, f"round {r}")
+        D, H = got["D"], got["H"]
+
+
+@pytest.mark.parametrize("L", [2, 4, 6, 12, 16])
+def test_edge_cases_and_layer_counts(la, L):
+    X, Y = 24, 20
+    rng = np.random.default_rng(L)
+    unit_r = list(np.round(rng.uniform(0.5, 9.0, L), 3))
+    unit_c = list(np.round(rng.uniform(0.1, 0.3, L), 3))
+    grid = simple_grid(X, Y, L, unit_r, unit_c, list(rng.uniform(0.5, 4.0, L - 1)), 0.04)
+    grid["cap"] = rng.integers(0, 5, len(grid["cap"])).astype(np.int32)
+    forest = merge_forests([edge_case_forest(X, Y, L, seed=L),
+                            fg.make_forest(fg.Workload("e", X, Y, L, (1, 4), 0.0, 300, 0, 2, 9, 0.0, False,
+                                                       tuple(unit_r), tuple(unit_c), 1), seed=L)])
+    a = _assigner(la, grid, forest)
+    for r in range(2):
+        D, H = (None, None) if r == 0 else (got["D"], got["H"])
+        got = gpu_round(a, dict(la.DEFAULT_WEIGHTS, w_d=2e-2), reset=(r == 0))
+        ref = ref_round(grid, forest, dict(la.DEFAULT_WEIGHTS, w_d=2e-2), D=D, H=H)
+        assert_same_round(got, ref, f"L={L} r={r}")
+
+
+def test_non_alternating_directions(la):
+    X, Y, L = 16, 16, 6
+    dirs = np.array([0, 0, 1, 1, 0, 1], np.int8)
+    E = sum(Y * (X - 1) if d == 0 else X * (Y - 1) for d in dirs)
+    rng = np.random.default_rng(5)
+    grid = dict(X=X, Y=Y, L=L, dir=dirs, cap=rng.integers(0, 6, E).astype(np.int32),
+                unit_r=np.array([6.0, 5.0, 4.0, 3.0, 1.0, 0.7]), unit_c=np.array([0.2, 0.21, 0.18, 0.17, 0.15, 0.16]),
+                via_r=np.array([1.0, 2.0, 1.5, 3.0, 0.5]), via_c=0.03, ofw=np.array([1.0, 2.0, 1.0, 0.5, 1.0, 1.5]))
+    wl = fg.Workload("nd", X, Y, L, (1, 4), 0.0, 400, 0, 2, 7, 0.0, False, tuple(grid["unit_r"]),
+                     tuple(grid["unit_c"]), 1)
+    forest = fg.make_forest(wl, 9)
+    a = _assigner(la, grid, forest)
+    got = gpu_round(a, dict(la.DEFAULT_WEIGHTS, w_d=1e-2), reset=True)
+    ref = ref_round(grid, forest, dict(la.DEFAULT_WEIGHTS, w_d=1e-2))
+    assert_same_round(got, ref)
+
+
+def test_elmore_and_adjoint_config3(la):
+    """Config 3: the 500k-net forest of config 2 with a fixed assignment;
+    FP64 delays and d(sum kappa delay)/d(R, C) against the oracle, and central
+    differences through the GPU path on 1000 sampled nets."""
+    wl = fg.WORKLOADS[3]
+    grid, forest = fg.make_grid(wl, 0), fg.make_forest(wl, 0)
+    a = _assigner(la, grid, forest)
+    a.assign_round(reset=True, **la.DEFAULT_WEIGHTS)
+    layer, b, t = (x.cpu().numpy() for x in a.get_assignment())
+    R, C = a.rc_from_assignment()
+    Rr, Cr = oracle.rc_from_assignment(grid, forest, layer)
+    assert np.array_equal(R.cpu().numpy(), Rr) and np.array_equal(C.cpu().numpy(), Cr)
+    g = np.where(forest["pin_layer"] >= 0, forest["kappa"], 0.0)
+    gt = torch.from_numpy(g).cuda()
+    Rg, Cg = R.clone().requires_grad_(True), C.clone().requires_grad_(True)
+    delay = la.ElmoreFn.apply(a, Rg, Cg)
+    (delay * gt).sum().backward()
+    d_ref = oracle.elmore(grid, forest, layer, b, t, Rr, Cr)
+    dR_ref, dC_ref, _, _ = oracle.elmore_backward(grid, forest, layer, b, t, Rr, Cr, g)
+    np.testing.assert_allclose(delay.detach().cpu().numpy(), d_ref, rtol=1e-10, atol=0)
+    np.testing.assert_allclose(Rg.grad.cpu().numpy(), dR_ref, rtol=1e-10, atol=0)
+    np.testing.assert_allclose(Cg.grad.cpu().numpy(), dC_ref, rtol=1e-10, atol=0)
+    # central differences on 1000 sampled nets (T is affine in each R and C)
+    rng = np.random.default_rng(0)
+    ptr = forest["net_ptr"]
+    nets = rng.choice(forest["num_nets"], 1000, replace=False)
+    cand = np.array([ptr[n] + 1 + rng.integers(0, ptr[n + 1] - ptr[n] - 1) for n in nets if ptr[n + 1] - ptr[n] > 1])
+    R0, C0 = R.clone(), C.clone()
+
+    def dT(Rp, Cp, Rm, Cm):
+        # delays differ only inside the perturbed net: subtract first, then sum
+        return float(torch.dot(a.elmore(Rp, Cp) - a.elmore(Rm, Cm), gt))
+
+    dRg, dCg = Rg.grad.cpu().numpy(), Cg.grad.cpu().numpy()
+    checked = 0
+    for v in cand[:1000]:
+        for which, arr, grad in ((0, R0, dRg), (1, C0, dCg)):
+            h = 1e-3 * float(arr[v])
+            if h == 0.0:
+                continue
+            p, m = arr.clone(), arr.clone()
+            p[v] += h
+            m[v] -= h
+            fd = (dT(p, C0, m, C0) if which == 0 else dT(R0, p, R0, m)) / (2 * h)
+            assert grad[v] == pytest.approx(fd, rel=1e-6, abs=1e-300), (which, int(v))
+            checked += 1
+    assert checked >= 1500
+
+
+def test_adjoint_reweighted_round(la):
+    """Rounds reweighted by the adjoint sensitivities (W = sum of kappa below,
+    r_est = weighted upstream R of the previous assignment)."""
+    wl = fg.WORKLOADS[2].scaled(30000)
+    grid, forest = fg.make_grid(wl, 4), fg.make_forest(wl, 4)
+    a = _assigner(la, grid, forest)
+    got = gpu_round(a, la.DEFAULT_WEIGHTS, reset=True)
+    for r in range(2):
+        a.reweight_adjoint()
+        W, rho = (x.cpu().numpy() for x in a.get_weights(la.LA_WEIGHTS_ADJOINT))
+        Wr, rhor = oracle.adjoint_weights(grid, forest, got["layer"], got["b"], got["t"])
+        assert np.array_equal(W, Wr) and np.array_equal(rho, rhor)
+        D, H = got["D"], got["H"]
+        got = gpu_round(a, la.DEFAULT_WEIGHTS, weights_src=la.LA_WEIGHTS_ADJOINT)
+        ref = ref_round(grid, forest, la.DEFAULT_WEIGHTS, D=D, H=H, W=Wr, rho=rhor)
+        assert_same_round(got, ref, f"adjoint {r}")
+
+
+def test_eq4_weights_match_oracle(la):
+    wl = fg.WORKLOADS[2].scaled(20000)
+    grid, forest = fg.make_grid(wl, 8), fg.make_forest(wl, 8)
+    a = _assigner(la, grid, forest)
+    W, rho = (x.cpu().numpy() for x in a.get_weights(la.LA_WEIGHTS_EQ4))
+    Wr, rhor = oracle.weights_eq4(grid, forest)
+    assert np.array_equal(W, Wr) and np.array_equal(rho, rhor)
+
+
+@pytest.mark.parametrize("case", ["bent_segment", "parent_order", "outside", "root_without_pin", "negative_cap",
+                                  "net_ptr"])
+def test_malformed_forest_is_rejected(la, case):
+    wl = fg.WORKLOADS[1].scaled(50)
+    grid, forest = fg.make_grid(wl, 1), fg.make_forest(wl, 1)
+    bad = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in forest.items()}
+    v = int(bad["net_ptr"][3]) + 1
+    if case == "bent_segment":
+        bad["x"][v] += 1
+        bad["y"][v] += 1
+    elif case == "parent_order":
+        bad["parent"][v] = v - int(bad["net_ptr"][3]) + 1
+    elif case == "outside":
+        bad["x"][v] = wl.X + 3
+    elif case == "root_without_pin":
+        bad["pin_layer"][int(bad["net_ptr"][5])] = -1
+    elif case == "negative_cap":
+        bad["sink_cap"][v] = -1.0
+    elif case == "net_ptr":
+        bad["net_ptr"][4] = bad["net_ptr"][6]
+    a = la.LayerAssigner(0)
+    a.load_grid(grid)
+    with pytest.raises(la.LaError) as e:
+        a.load_nets(bad)
+    assert e.value.status == la.LA_ERR_INVALID
+    # the context is still usable
+    a.load_nets(forest)
+    a.assign_round(reset=True)

@@ -67,3 +67,53 @@ def simple_grid(X, Y, L, unit_r, unit_c, via_r, via_c, cap=8):
                 cap=np.full(E, cap, np.int32), unit_r=np.array(unit_r, np.float64),
                 unit_c=np.array(unit_c, np.float64), via_r=np.array(via_r, np.float64),
                 via_c=float(via_c), ofw=np.ones(L, np.float64))
+
+
+def merge_forests(parts) -> dict:
+    """Concatenate one-or-more-net forests into one forest."""
+    out = {k: np.concatenate([p[k] for p in parts]) for k in
+           ("x", "y", "parent", "pin_layer", "sink_cap", "kappa", "r_drv")}
+    sizes = np.concatenate([np.diff(p["net_ptr"]) for p in parts])
+    out["net_ptr"] = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    out["num_nets"] = len(sizes)
+    out["num_nodes"] = int(out["net_ptr"][-1])
+    return out
+
+
+def edge_case_forest(X: int, Y: int, L: int, seed: int = 0) -> dict:
+    """Hand-made nets covering the degenerate shapes: a single-node net, a
+    2-pin straight net, a long zig-zag chain (deep tree), a star with four
+    sons, a Steiner node with three sons, pins on upper layers, and a sink
+    merged into the driver's GCell."""
+    rng = np.random.default_rng(seed)
+    nets = []
+    u = lambda: float(rng.uniform(0.1, 1.0))
+    # single node (all pins in the driver's GCell)
+    nets.append(forest_from_rows([(-1, 3, 3, 0, 2.0, 0.7)], r_drv=200.0))
+    # 2-pin straight
+    nets.append(forest_from_rows([(-1, 1, 1, 0, 0.0, 0.0), (0, 9, 1, 0, 3.0, u())], r_drv=120.0))
+    # zig-zag chain: H, V, H, V, ... with a pin every fourth node
+    rows = [(-1, 0, 0, 0, 0.0, 0.0)]
+    x, y = 0, 0
+    depth = min(X, Y) - 2
+    for i in range(1, depth):
+        if i % 2:
+            x += 1
+        else:
+            y += 1
+        pin = int(rng.integers(0, L)) if i % 4 == 0 else -1
+        rows.append((i - 1, x, y, pin, 1.5 if pin >= 0 else 0.0, u() if pin >= 0 else 0.0))
+    rows[-1] = rows[-1][:3] + (0, 2.5, u())
+    nets.append(forest_from_rows(rows, r_drv=300.0))
+    # star: driver in the middle, four straight sons
+    cx, cy = X // 2, Y // 2
+    nets.append(forest_from_rows([(-1, cx, cy, 0, 0.0, 0.0), (0, cx + 5, cy, 0, 1.0, u()),
+                                  (0, cx - 4, cy, 1, 2.0, u()), (0, cx, cy + 3, 0, 1.5, u()),
+                                  (0, cx, cy - 6, 2 % L, 2.5, u())], r_drv=90.0))
+    # Steiner node (no pin) with three sons, one of them carrying a further son
+    nets.append(forest_from_rows([(-1, 2, 2, 0, 0.0, 0.0), (0, 2, 8, -1, 0.0, 0.0), (1, 7, 8, 0, 1.0, u()),
+                                  (1, 2, 12 % Y, 0, 2.0, u()), (1, 0, 8, L - 1, 1.0, u()),
+                                  (4, 0, 10, 0, 3.0, u())], r_drv=60.0))
+    # sink merged into the driver node, and a son
+    nets.append(forest_from_rows([(-1, 5, 5, 0, 4.0, 0.9), (0, 5, 1, 0, 1.0, 0.2)], r_drv=400.0))
+    return merge_forests(nets)
