@@ -283,6 +283,7 @@ la_status la_load_grid(la_ctx* c, const la_grid_desc* gd) {
   DevTables& t = ng.tab;
   memset(&t, 0, sizeof t);
   memcpy(t.rv, ng.rvia, sizeof t.rv);
+  for (int k = 0; k < kMaxL; ++k) t.kd[k] = double(k);
   for (int l = 0; l < kMaxL; ++l) {
     t.unit_r[l] = li.unit_r[l];
     t.unit_c[l] = li.unit_c[l];
@@ -384,8 +385,10 @@ la_status la_load_nets(la_ctx* c, const la_net_desc* nd) {
   int32_t* d_cnt = nullptr;
   int64_t* d_cur = nullptr;
 #define GET(p, n) if (st == LA_OK) st = na.get(c, &(p), (n))
-  GET(nf.lvl_nodes, V); GET(d_cnt, size_t(hmax) + 1); GET(d_cur, size_t(hmax) + 1);
+  const size_t nbk = size_t(hmax + 1) * kClasses;
+  GET(nf.lvl_nodes, V); GET(d_cnt, nbk); GET(d_cur, nbk);
   GET(nf.A, V * LD); GET(nf.Cc, V * LD); GET(nf.M, V * LD); GET(nf.sb, V * LD); GET(nf.st, V * LD);
+  GET(nf.B, V * LD);
   GET(nf.ent, V * LD); GET(nf.Jroot, V); GET(nf.layer, V); GET(nf.b, V); GET(nf.t, V); GET(nf.s0, V);
   GET(nf.s1, V); GET(nf.s2, V); GET(nf.W_adj, V); GET(nf.rho_adj, V);
   const int nred = std::max(scan_blocks(c->grid.li), int((N + 255) / 256)) + 8;
@@ -393,17 +396,19 @@ la_status la_load_nets(la_ctx* c, const la_net_desc* nd) {
 #undef GET
   if (st) return fail(st);
   nf.red_cap = nred;
-  if (cudaMemsetAsync(d_cnt, 0, sizeof(int32_t) * (hmax + 1), s))
+  if (cudaMemsetAsync(d_cnt, 0, sizeof(int32_t) * nbk, s))
     return fail(set_err(c, LA_ERR_CUDA, "la_load_nets: %s", cudaGetErrorString(cudaGetLastError())));
   launch_level_sort(nf, d_cnt, nullptr, s);
   ++c->launches;
-  std::vector<int32_t> cnt(hmax + 1);
-  if (cudaMemcpyAsync(cnt.data(), d_cnt, sizeof(int32_t) * (hmax + 1), cudaMemcpyDeviceToHost, s) ||
+  std::vector<int32_t> cnt(nbk);
+  if (cudaMemcpyAsync(cnt.data(), d_cnt, sizeof(int32_t) * nbk, cudaMemcpyDeviceToHost, s) ||
       cudaStreamSynchronize(s))
     return fail(set_err(c, LA_ERR_CUDA, "la_load_nets: %s", cudaGetErrorString(cudaGetLastError())));
+  nf.cls_off.assign(nbk + 1, 0);
+  for (size_t k = 0; k < nbk; ++k) nf.cls_off[k + 1] = nf.cls_off[k] + cnt[k];
   nf.lvl_off.assign(hmax + 2, 0);
-  for (int h = 0; h <= hmax; ++h) nf.lvl_off[h + 1] = nf.lvl_off[h] + cnt[h];
-  if (cudaMemcpyAsync(d_cur, nf.lvl_off.data(), sizeof(int64_t) * (hmax + 1), cudaMemcpyHostToDevice, s))
+  for (int h = 0; h <= hmax + 1; ++h) nf.lvl_off[h] = nf.cls_off[size_t(h) * kClasses];
+  if (cudaMemcpyAsync(d_cur, nf.cls_off.data(), sizeof(int64_t) * nbk, cudaMemcpyHostToDevice, s))
     return fail(set_err(c, LA_ERR_CUDA, "la_load_nets: %s", cudaGetErrorString(cudaGetLastError())));
   launch_level_sort(nf, nullptr, d_cur, s);
   launch_weights_eq4(c->grid.li, nf, s);

@@ -61,6 +61,7 @@ struct LayerInfo {
 // thread-varying indices; kernels copy them to shared memory (load_tables).
 struct DevTables {
   double rv[kMaxL * kMaxL];   // Rvia(a, b) = sum of via R between layers a and b
+  double kd[kMaxL];           // 0.0, 1.0, ..., 15.0 (via counts as doubles)
   double unit_r[kMaxL], unit_c[kMaxL], half_c[kMaxL];
   double via_c;
   int64_t grid_off[2];
@@ -87,7 +88,8 @@ __host__ __device__ inline int geo_len(uint64_t g) { return int(g & 0xFFFF); }
 struct Forest {
   int64_t N = 0, V = 0;
   int Hmax = 0;                         // max height (levels 0..Hmax)
-  std::vector<int64_t> lvl_off;         // host copy, Hmax + 2 entries
+  std::vector<int64_t> lvl_off;         // host copy: level h is [lvl_off[h], lvl_off[h+1])
+  std::vector<int64_t> cls_off;         // host copy, 4 (Hmax+1) + 1 entries: (level, node class) buckets
   // device arrays (node ids are int32: V < 2^31)
   int64_t* net_ptr = nullptr;           // N + 1
   int32_t* parent_g = nullptr;          // global parent id, -1 at roots
@@ -112,6 +114,7 @@ struct Forest {
   double* A = nullptr;                  // [V][LD]
   double* Cc = nullptr;
   double* M = nullptr;
+  double* B = nullptr;                  // look-ahead base fma(w_d r_est(parent), Cc, A)
   int8_t* sb = nullptr;                 // [V][LD] chosen stack bottom
   int8_t* st = nullptr;                 // [V][LD] chosen stack top
   int8_t* ent = nullptr;                // [V][LD] layer of this son per parent candidate
@@ -183,6 +186,8 @@ namespace gapla {
 void launch_grid_to_internal(const LayerInfo& li, int X, int Y, const int32_t* pub, int32_t* inter,
                              bool to_internal, unsigned long long* err, cudaStream_t s);
 void launch_forest_prepare(la_ctx* c, Forest& f, const la_net_desc* d, int* d_hmax, cudaStream_t s);
+// Nodes bucketed by (level, class): class = 3 * is_root + min(sons, 2).
+constexpr int kClasses = 6;
 void launch_level_sort(Forest& f, int32_t* lvl_cnt, int64_t* lvl_cursor, cudaStream_t s);
 void launch_weights_eq4(const LayerInfo& li, Forest& f, cudaStream_t s);
 void launch_check_assignment(la_ctx* c, const int8_t* layer, const int8_t* b, const int8_t* t,

@@ -143,25 +143,47 @@ void launch_forest_prepare(la_ctx* c, Forest& f, const la_net_desc* d, int* d_hm
   ++c->launches;
 }
 
-__global__ void k_level_count(int64_t V, const int32_t* __restrict__ height, int32_t* __restrict__ cnt) {
-  const int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (v < V) atomicAdd(&cnt[height[v]], 1);
-}
-__global__ void k_level_place(int64_t V, const int32_t* __restrict__ height,
-                              unsigned long long* __restrict__ cursor, int32_t* __restrict__ out) {
-  const int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (v < V) out[atomicAdd(&cursor[height[v]], 1ull)] = int32_t(v);
+__device__ __forceinline__ int node_bucket(int64_t v, const int32_t* height, const int32_t* nch,
+                                           const int32_t* parent_g) {
+  const int cls = (parent_g[v] < 0 ? 3 : 0) + min(nch[v], 2);
+  return height[v] * kClasses + cls;
 }
 
-// lvl_cnt: Hmax+1 zeroed ints; lvl_cursor: Hmax+1 int64 holding the level
-// offsets on entry.  Within a level the order is whatever the atomics give:
-// nodes of one level never read each other's results.
+// Warp-aggregated counting: lanes with the same bucket add once.
+__global__ void k_level_count(int64_t V, const int32_t* __restrict__ height, const int32_t* __restrict__ nch,
+                              const int32_t* __restrict__ parent_g, int32_t* __restrict__ cnt) {
+  const int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const bool act = v < V;
+  const int key = act ? node_bucket(v, height, nch, parent_g) : -1;
+  const unsigned peers = __match_any_sync(0xffffffffu, key);
+  const int lane = threadIdx.x & 31;
+  if (act && lane == __ffs(peers) - 1) atomicAdd(&cnt[key], __popc(peers));
+}
+__global__ void k_level_place(int64_t V, const int32_t* __restrict__ height, const int32_t* __restrict__ nch,
+                              const int32_t* __restrict__ parent_g, unsigned long long* __restrict__ cursor,
+                              int32_t* __restrict__ out) {
+  const int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const bool act = v < V;
+  const int key = act ? node_bucket(v, height, nch, parent_g) : -1;
+  const unsigned peers = __match_any_sync(0xffffffffu, key);
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(peers) - 1;
+  unsigned long long base = 0;
+  if (act && lane == leader) base = atomicAdd(&cursor[key], (unsigned long long)__popc(peers));
+  base = __shfl_sync(peers, base, leader);
+  if (act) out[base + __popc(peers & ((1u << lane) - 1u))] = int32_t(v);
+}
+
+// lvl_cnt: kClasses (Hmax+1) zeroed ints; lvl_cursor: as many int64 holding
+// the bucket offsets on entry.  Within a bucket the order is whatever the
+// atomics give: nodes of one level never read each other's results.
 void launch_level_sort(Forest& f, int32_t* lvl_cnt, int64_t* lvl_cursor, cudaStream_t s) {
   const int T = 256;
   const unsigned B = (unsigned)((f.V + T - 1) / T);
-  if (lvl_cnt) k_level_count<<<B, T, 0, s>>>(f.V, f.height, lvl_cnt);
+  if (lvl_cnt) k_level_count<<<B, T, 0, s>>>(f.V, f.height, f.nch, f.parent_g, lvl_cnt);
   if (lvl_cursor)
-    k_level_place<<<B, T, 0, s>>>(f.V, f.height, reinterpret_cast<unsigned long long*>(lvl_cursor), f.lvl_nodes);
+    k_level_place<<<B, T, 0, s>>>(f.V, f.height, f.nch, f.parent_g,
+                                  reinterpret_cast<unsigned long long*>(lvl_cursor), f.lvl_nodes);
 }
 
 // Eq. 4 edge weights (max sink criticality below) and the distance-based

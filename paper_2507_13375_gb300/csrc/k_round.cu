@@ -139,8 +139,17 @@ void launch_scan_lines(la_ctx* c, bool from_diff, double hist_w, double* tof_par
 }
 
 // ---------------------------------------------------------------------------
-// DP over one level (Alg. 3).  One thread per (node, candidate junction layer):
-// the segment's layers, or the driver pin layer at a root.
+// DP over one level (Alg. 3).  One launch per (level, node class): DEG = 0
+// (leaf), 1 (one son), 2 (two or more sons); ROOT: one thread per root (its
+// junction is on the driver pin layer), otherwise one thread per (node, layer
+// of its segment's direction).
+//
+// FP64 economy (GB300 issues FP64 at 1/64 of FP32): every value is the
+// oracle's expression, but each is computed once.  A node writes, besides its
+// entry A, Cc, M, the look-ahead base B = fma(w_d r_est(parent), Cc, A) that
+// every candidate layer of its parent would otherwise recompute; the parent's
+// key for son layer lc is then one fma(M, Rvia(l, lc), B).  Minima compare
+// the bit patterns of non-negative doubles as integers.
 // ---------------------------------------------------------------------------
 struct DPArgs {
   int LD;
@@ -152,7 +161,7 @@ struct DPArgs {
   const uint64_t* geo;
   const int64_t* P;
   const DevTables* tab;
-  double *A, *Cc, *M, *Jroot;
+  double *A, *Cc, *M, *B, *Jroot;
   int8_t *sb, *st, *ent;
   double w_cong_s, w_cap, w_d, sigma0;
   unsigned long long* err;
@@ -163,23 +172,21 @@ __device__ __forceinline__ bool stack_better(long long f, int k, int b, long lon
   return f < bf || (f == bf && (k < bk || (k == bk && b < bb)));
 }
 
-template <int LMAX>
+template <int LMAX, int DEG, bool ROOT>
 __global__ void __launch_bounds__(256) k_dp_level(LayerInfo li, DPArgs a) {
   __shared__ DevTables s;
   load_tables(s, a.tab);
   const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  const int64_t node_i = k / a.LD;
-  const int ldi = int(k - node_i * a.LD);
+  const int64_t node_i = ROOT ? k : k / a.LD;
+  const int ldi = ROOT ? 0 : int(k - node_i * a.LD);
   if (node_i >= a.count) return;
   const int v = a.nodes[node_i];
   const int L = li.L, LD = a.LD;
-  const bool is_root = a.parent_g[v] < 0;
   const int pin = a.pin[v];
   const uint64_t gv = a.geo[v];
   const int d = geo_dir(gv);
   int l;
-  if (is_root) {
-    if (ldi != 0) return;
+  if constexpr (ROOT) {
     l = pin;
   } else {
     if (ldi >= s.nld[d]) return;
@@ -188,62 +195,68 @@ __global__ void __launch_bounds__(256) k_dp_level(LayerInfo li, DPArgs a) {
   const double* rvl = &s.rv[l * kMaxL];
   const double wd_rho = a.w_d * a.rho[v];
   const double sigma_v = fma(wd_rho, s.via_c, a.sigma0);
-  const double Cs = a.sink_cap[v];
-  const double sinkf = pin >= 0 ? ((a.w_d * a.kappa[v]) * rvl[pin]) * Cs : 0.0;
-  const double z = fma(wd_rho, Cs, sinkf);
+  double Cs = 0.0, sinkf = 0.0, z = 0.0;  // a node without a pin: all exactly 0
+  if (pin >= 0) {
+    Cs = a.sink_cap[v];
+    sinkf = ((a.w_d * a.kappa[v]) * rvl[pin]) * Cs;
+    z = fma(wd_rho, Cs, sinkf);
+  }
   const int lo_req = pin >= 0 ? min(l, pin) : l;
   const int hi_req = pin >= 0 ? max(l, pin) : l;
-  const int cs = a.child_start[v], nc = a.nch[v];
+  const int cs = a.child_start[v];
 
+  int bb = lo_req, bt = hi_req;
   long long bfp = LLONG_MAX;
-  int bb = lo_req, bt = hi_req, bk = INT_MAX;
-  if (nc == 0) {
+  double sg = 0.0, sc = 0.0;
+  if constexpr (DEG == 0) {
     // a leaf: every stack costs tail(t - b); the smallest one wins
-    bfp = dbits(fma(double(hi_req - lo_req), sigma_v, z));
-  } else if (nc == 1) {
-    // one son: only stacks that are the hull of (junction, pin, son layer lc)
-    // with lc the son's own choice inside that hull can win (ties go to fewer
-    // vias); evaluate exactly those.
+    bfp = dbits(fma(s.kd[hi_req - lo_req], sigma_v, z));
+  } else if constexpr (DEG == 1) {
+    // One son: only a stack that is the hull of (junction, pin, son layer
+    // lc), with lc the son's own least key inside it, can win (a larger stack
+    // with the same choice costs more and loses ties on t - b): evaluate those.
     const int c = a.child_list[cs];
     const int dc = geo_dir(a.geo[c]);
     const int nldc = s.nld[dc];
-    const double* Ac = a.A + int64_t(c) * LD;
-    const double* Ccc = a.Cc + int64_t(c) * LD;
+    const double* Bc = a.B + int64_t(c) * LD;
     const double* Mc = a.M + int64_t(c) * LD;
-    double key[LMAX];
+    long long key[LMAX];
 #pragma unroll
-    for (int j = 0; j < LMAX; ++j) {
-      if (j < nldc) {
-        const int lc = s.lay[dc][j];
-        key[j] = fma(Mc[j], rvl[lc], fma(wd_rho, Ccc[j], Ac[j]));
-      }
-    }
+    for (int j = 0; j < LMAX; ++j)
+      if (j < nldc) key[j] = dbits(fma(Mc[j], rvl[s.lay[dc][j]], Bc[j]));
+    int bj = 0, bk = INT_MAX;
 #pragma unroll
     for (int j = 0; j < LMAX; ++j) {
       if (j < nldc) {
         const int lc = s.lay[dc][j];
         const int b0 = min(lo_req, lc), t0 = max(hi_req, lc);
-        const long long kj = dbits(key[j]);
         bool consistent = true;
 #pragma unroll
         for (int j2 = 0; j2 < LMAX; ++j2) {
           if (j2 < nldc && j2 != j) {
             const int l2 = s.lay[dc][j2];
-            if (l2 >= b0 && l2 <= t0) {
-              const long long k2 = dbits(key[j2]);
-              if (k2 < kj || (k2 == kj && j2 < j)) consistent = false;
-            }
+            if (l2 >= b0 && l2 <= t0 && (key[j2] < key[j] || (key[j2] == key[j] && j2 < j))) consistent = false;
           }
         }
         if (consistent) {
-          const long long f = dbits(key[j] + fma(double(t0 - b0), sigma_v, z));
-          if (stack_better(f, t0 - b0, b0, bfp, bk, bb)) { bfp = f; bk = t0 - b0; bb = b0; bt = t0; }
+          const long long f = dbits(__longlong_as_double(key[j]) + fma(s.kd[t0 - b0], sigma_v, z));
+          if (stack_better(f, t0 - b0, b0, bfp, bk, bb)) { bfp = f; bk = t0 - b0; bb = b0; bt = t0; bj = j; }
         }
       }
     }
+    if (bfp == LLONG_MAX) {  // cannot happen (the least key overall is consistent); report it
+      dev_error(a.err, DE_NOSTACK, v);
+      return;
+    }
+    const int lc = s.lay[dc][bj];
+    a.ent[int64_t(c) * LD + ldi] = int8_t(lc);
+    sg = fma(Mc[bj], rvl[lc], a.A[int64_t(c) * LD + bj]);
+    sc = a.Cc[int64_t(c) * LD + bj];
   } else {
-    // general case: every stack [b, t] with b <= lo_req <= hi_req <= t;
+    // Two or more sons: every stack [b, t] with b <= lo_req <= hi_req <= t;
     // S[t] accumulates, son by son in order, the son's least key in [b, t].
+    const int nc = a.nch[v];
+    int bk = INT_MAX;
     for (int b = 0; b <= lo_req; ++b) {
       double S[LMAX];
       bool ok[LMAX];
@@ -251,26 +264,21 @@ __global__ void __launch_bounds__(256) k_dp_level(LayerInfo li, DPArgs a) {
       for (int t = 0; t < LMAX; ++t) { S[t] = 0.0; ok[t] = true; }
       for (int j = 0; j < nc; ++j) {
         const int c = a.child_list[cs + j];
-        const int dc = geo_dir(a.geo[c]);
-        const uint32_t mask = s.mask[dc];
-        const double* Ac = a.A + int64_t(c) * LD;
-        const double* Ccc = a.Cc + int64_t(c) * LD;
+        const uint32_t mask = s.mask[geo_dir(a.geo[c])];
+        const double* Bc = a.B + int64_t(c) * LD;
         const double* Mc = a.M + int64_t(c) * LD;
         long long rbits = LLONG_MAX;
-        double rkey = 0.0;
-        bool have = false;
 #pragma unroll
         for (int lc = 0; lc < LMAX; ++lc) {
           if (lc < L && lc >= b) {
             if ((mask >> lc) & 1u) {
               const int jj = s.ld_of[lc];
-              const double key = fma(Mc[jj], rvl[lc], fma(wd_rho, Ccc[jj], Ac[jj]));
-              const long long kb = dbits(key);
-              if (!have || kb < rbits) { have = true; rbits = kb; rkey = key; }
+              const long long kb = dbits(fma(Mc[jj], rvl[lc], Bc[jj]));
+              if (kb < rbits) rbits = kb;
             }
             if (lc >= hi_req) {
-              if (!have) ok[lc] = false;
-              else S[lc] = S[lc] + rkey;
+              if (rbits == LLONG_MAX) ok[lc] = false;
+              else S[lc] = j == 0 ? __longlong_as_double(rbits) : S[lc] + __longlong_as_double(rbits);
             }
           }
         }
@@ -278,93 +286,112 @@ __global__ void __launch_bounds__(256) k_dp_level(LayerInfo li, DPArgs a) {
 #pragma unroll
       for (int t = 0; t < LMAX; ++t) {
         if (t < L && t >= hi_req && ok[t]) {
-          const long long f = dbits(S[t] + fma(double(t - b), sigma_v, z));
+          const long long f = dbits(S[t] + fma(s.kd[t - b], sigma_v, z));
           if (stack_better(f, t - b, b, bfp, bk, bb)) { bfp = f; bk = t - b; bb = b; bt = t; }
         }
       }
     }
+    // each son's layer inside the winning stack
+    for (int j = 0; j < nc; ++j) {
+      const int c = a.child_list[cs + j];
+      const uint32_t mask = s.mask[geo_dir(a.geo[c])];
+      const double* Bc = a.B + int64_t(c) * LD;
+      const double* Mc = a.M + int64_t(c) * LD;
+      long long rbits = LLONG_MAX;
+      int rl = -1;
+#pragma unroll
+      for (int lc = 0; lc < LMAX; ++lc) {
+        if (lc >= bb && lc <= bt && ((mask >> lc) & 1u)) {
+          const long long kb = dbits(fma(Mc[s.ld_of[lc]], rvl[lc], Bc[s.ld_of[lc]]));
+          if (rl < 0 || kb < rbits) { rl = lc; rbits = kb; }
+        }
+      }
+      if (rl < 0) {  // cannot happen for a valid stack; report instead of indexing with -1
+        dev_error(a.err, DE_NOSTACK, v);
+        return;
+      }
+      const int jj = s.ld_of[rl];
+      a.ent[int64_t(c) * LD + ldi] = int8_t(rl);
+      const double g = fma(Mc[jj], rvl[rl], a.A[int64_t(c) * LD + jj]);
+      sg = j == 0 ? g : sg + g;
+      sc = j == 0 ? a.Cc[int64_t(c) * LD + jj] : sc + a.Cc[int64_t(c) * LD + jj];
+    }
   }
 
-  // the winning stack: each son's layer inside [bb, bt], and the table entry
-  double sg = 0.0, sc = 0.0;
-  for (int j = 0; j < nc; ++j) {
-    const int c = a.child_list[cs + j];
-    const int dc = geo_dir(a.geo[c]);
-    const uint32_t mask = s.mask[dc];
-    const double* Ac = a.A + int64_t(c) * LD;
-    const double* Ccc = a.Cc + int64_t(c) * LD;
-    const double* Mc = a.M + int64_t(c) * LD;
-    long long rbits = LLONG_MAX;
-    int rl = -1;
-#pragma unroll
-    for (int lc = 0; lc < LMAX; ++lc) {
-      if (lc >= bb && lc <= bt && ((mask >> lc) & 1u)) {
-        const int jj = s.ld_of[lc];
-        const long long kb = dbits(fma(Mc[jj], rvl[lc], fma(wd_rho, Ccc[jj], Ac[jj])));
-        if (rl < 0 || kb < rbits) { rl = lc; rbits = kb; }
-      }
-    }
-    if (rl < 0) {  // cannot happen for a valid stack; report instead of indexing with -1
-      dev_error(a.err, DE_NOSTACK, v);
-      return;
-    }
-    const int jj = s.ld_of[rl];
-    a.ent[int64_t(c) * LD + ldi] = int8_t(rl);
-    sg = sg + fma(Mc[jj], rvl[rl], Ac[jj]);
-    sc = sc + Ccc[jj];
-  }
+  // the table entry of the winning stack (0.0 + x == x for the x >= 0 here)
   const int kk = bt - bb;
-  const double fv = sg + fma(double(kk), a.sigma0, sinkf);
-  const double cv = sc + fma(double(kk), s.via_c, Cs);
+  const double fv = DEG == 0 ? fma(s.kd[kk], a.sigma0, sinkf) : sg + fma(s.kd[kk], a.sigma0, sinkf);
+  const double cv = DEG == 0 ? fma(s.kd[kk], s.via_c, Cs) : sc + fma(s.kd[kk], s.via_c, Cs);
   const int64_t o = int64_t(v) * LD + ldi;
   a.sb[o] = int8_t(bb);
   a.st[o] = int8_t(bt);
-  if (is_root) {
+  if constexpr (ROOT) {
     a.Jroot[v] = __longlong_as_double(bfp);
-    return;
+  } else {
+    const int len = geo_len(gv), line = geo_line(gv), lo = geo_lo(gv);
+    const double R = double(len) * s.unit_r[l];
+    const double C = double(len) * s.unit_c[l];
+    const double Ch = double(len) * s.half_c[l];
+    const double wdW = a.w_d * a.W[v];
+    const double alpha = wdW * R;
+    const double gamma = fma(alpha, Ch, a.w_cap * C);
+    const int nldd = s.nld[d];
+    const int64_t pb = s.grid_off[d] + int64_t(line) * s.npos[d] * nldd + ldi;
+    const int64_t K = a.P[pb + int64_t(lo + len) * nldd] - a.P[pb + int64_t(lo) * nldd];
+    const double seg = fma(a.w_cong_s, double(K), gamma);
+    const double Av = fma(alpha, cv, fv + seg);
+    const double ccv = C + cv;
+    a.A[o] = Av;
+    a.Cc[o] = ccv;
+    a.M[o] = wdW * ccv;
+    a.B[o] = fma(a.w_d * a.rho[a.parent_g[v]], ccv, Av);
   }
-  const int len = geo_len(gv), line = geo_line(gv), lo = geo_lo(gv);
-  const double R = double(len) * s.unit_r[l];
-  const double C = double(len) * s.unit_c[l];
-  const double Ch = double(len) * s.half_c[l];
-  const double wdW = a.w_d * a.W[v];
-  const double alpha = wdW * R;
-  const double gamma = fma(alpha, Ch, a.w_cap * C);
-  const int nldd = s.nld[d];
-  const int64_t pb = s.grid_off[d] + int64_t(line) * s.npos[d] * nldd + ldi;
-  const int64_t K = a.P[pb + int64_t(lo + len) * nldd] - a.P[pb + int64_t(lo) * nldd];
-  const double seg = fma(a.w_cong_s, double(K), gamma);
-  a.A[o] = fma(alpha, cv, fv + seg);
-  const double ccv = C + cv;
-  a.Cc[o] = ccv;
-  a.M[o] = wdW * ccv;
+}
+
+template <int LMAX, int DEG, bool ROOT>
+static void dp_launch(la_ctx* c, const DPArgs& a, cudaStream_t s) {
+  const int T = 256;
+  const int64_t threads = ROOT ? a.count : a.count * a.LD;
+  k_dp_level<LMAX, DEG, ROOT><<<(unsigned)((threads + T - 1) / T), T, 0, s>>>(c->grid.li, a);
+  ++c->launches;
+}
+
+template <int LMAX>
+static void dp_launch_class(la_ctx* c, const DPArgs& a, int cls, cudaStream_t s) {
+  switch (cls) {
+    case 0: dp_launch<LMAX, 0, false>(c, a, s); break;
+    case 1: dp_launch<LMAX, 1, false>(c, a, s); break;
+    case 2: dp_launch<LMAX, 2, false>(c, a, s); break;
+    case 3: dp_launch<LMAX, 0, true>(c, a, s); break;
+    case 4: dp_launch<LMAX, 1, true>(c, a, s); break;
+    default: dp_launch<LMAX, 2, true>(c, a, s); break;
+  }
 }
 
 void launch_dp_level(la_ctx* c, const RoundW& w, const double* W, const double* rho, int level, cudaStream_t s) {
   Forest& f = c->forest;
-  const int64_t n = f.lvl_off[level + 1] - f.lvl_off[level];
-  if (n == 0) return;
   DPArgs a;
   a.LD = c->LD;
-  a.nodes = f.lvl_nodes + f.lvl_off[level];
-  a.count = n;
   a.parent_g = f.parent_g; a.child_start = f.child_start; a.nch = f.nch; a.child_list = f.child_list;
   a.pin = f.pin; a.sink_cap = f.sink_cap; a.kappa = f.kappa; a.W = W; a.rho = rho; a.geo = f.geo;
   a.P = c->grid.P; a.tab = c->grid.tab_dev;
-  a.A = f.A; a.Cc = f.Cc; a.M = f.M; a.Jroot = f.Jroot; a.sb = f.sb; a.st = f.st; a.ent = f.ent;
+  a.A = f.A; a.Cc = f.Cc; a.M = f.M; a.B = f.B; a.Jroot = f.Jroot; a.sb = f.sb; a.st = f.st; a.ent = f.ent;
   a.w_cong_s = w.w_cong * 0x1.0p-24;
   a.w_cap = w.w_cap;
   a.w_d = w.w_d;
   a.sigma0 = w.w_via + w.w_cap * c->grid.li.via_c;
   a.err = c->d_err;
-  const int T = 256;
-  const int64_t threads = n * a.LD;
-  const unsigned B = (unsigned)((threads + T - 1) / T);
   const int L = c->grid.li.L;
-  if (L <= 6) k_dp_level<6><<<B, T, 0, s>>>(c->grid.li, a);
-  else if (L <= 12) k_dp_level<12><<<B, T, 0, s>>>(c->grid.li, a);
-  else k_dp_level<16><<<B, T, 0, s>>>(c->grid.li, a);
-  ++c->launches;
+  for (int cls = 0; cls < kClasses; ++cls) {
+    const size_t bk = size_t(level) * kClasses + cls;
+    const int64_t n = f.cls_off[bk + 1] - f.cls_off[bk];
+    if (n == 0) continue;
+    a.nodes = f.lvl_nodes + f.cls_off[bk];
+    a.count = n;
+    if (L <= 6) dp_launch_class<6>(c, a, cls, s);
+    else if (L <= 12) dp_launch_class<12>(c, a, cls, s);
+    else dp_launch_class<16>(c, a, cls, s);
+  }
 }
 
 // ---------------------------------------------------------------------------
