@@ -353,24 +353,29 @@ la_status la_load_nets(la_ctx* c, const la_net_desc* nd) {
   DeviceGuard g(c->device);
   cudaStream_t s = c->stream;
   const int LD = c->LD;
-  Forest nf;
-  nf.N = nd->num_nets;
-  nf.V = nd->num_nodes;
+  // tf: the forest in input order (validation, levels, Eq. 4 weights);
+  // nf: the same in internal (level, class) order, kept by the context.
+  Forest tf, nf;
+  tf.N = nf.N = nd->num_nets;
+  tf.V = nf.V = nd->num_nodes;
   const size_t N = size_t(nf.N), V = size_t(nf.V);
-  Allocs na;
+  Allocs na, ta;  // kept / temporary
   la_status st = LA_OK;
-#define GET(p, n) if (st == LA_OK) st = na.get(c, &(p), (n))
-  GET(nf.net_ptr, N + 1); GET(nf.parent_g, V); GET(nf.net_of, V); GET(nf.pin, V); GET(nf.sink_cap, V);
-  GET(nf.kappa, V); GET(nf.gk, V); GET(nf.r_drv, N); GET(nf.geo, V); GET(nf.child_start, V); GET(nf.nch, V);
-  GET(nf.child_list, V); GET(nf.height, V); GET(nf.W_eq4, V); GET(nf.rho_eq4, V);
+  auto fail = [&](la_status s2) { na.release(); ta.release(); return s2; };
+  auto cuda_fail = [&]() { return fail(set_err(c, LA_ERR_CUDA, "la_load_nets: %s", cudaGetErrorString(cudaGetLastError()))); };
+#define GETK(p, n) if (st == LA_OK) st = na.get(c, &(p), (n))
+#define GETT(p, n) if (st == LA_OK) st = ta.get(c, &(p), (n))
+  GETK(nf.net_ptr, N + 1); GETK(nf.r_drv, N);
+  GETT(tf.parent_g, V); GETT(tf.net_of, V); GETT(tf.pin, V); GETT(tf.sink_cap, V); GETT(tf.kappa, V);
+  GETT(tf.gk, V); GETT(tf.geo, V); GETT(tf.child_start, V); GETT(tf.nch, V); GETT(tf.child_list, V);
+  GETT(tf.height, V); GETT(tf.W_eq4, V); GETT(tf.rho_eq4, V);
   int* d_hmax = nullptr;
-  GET(d_hmax, 1);
-#undef GET
-  if (st) { na.release(); return st; }
-  auto fail = [&](la_status s2) { na.release(); return s2; };
-  if (reset_dev_err(c) || cudaMemsetAsync(d_hmax, 0, sizeof(int), s))
-    return fail(set_err(c, LA_ERR_CUDA, "la_load_nets: %s", cudaGetErrorString(cudaGetLastError())));
-  launch_forest_prepare(c, nf, nd, d_hmax, s);
+  GETT(d_hmax, 1);
+  if (st) return fail(st);
+  tf.net_ptr = nf.net_ptr;
+  tf.r_drv = nf.r_drv;
+  if (reset_dev_err(c) || cudaMemsetAsync(d_hmax, 0, sizeof(int), s)) return cuda_fail();
+  launch_forest_prepare(c, tf, nd, d_hmax, s);
   int code;
   long long idx;
   if (cudaGetLastError() != cudaSuccess) return fail(set_err(c, LA_ERR_CUDA, "la_load_nets: launch failed"));
@@ -378,43 +383,49 @@ la_status la_load_nets(la_ctx* c, const la_net_desc* nd) {
   if (code) return fail(set_err(c, LA_ERR_INVALID, "la_load_nets: %s (%s %lld)", dev_err_name(code),
                                  code == DE_NETPTR ? "net" : "node", idx));
   int hmax = 0;
-  if (cudaMemcpy(&hmax, d_hmax, sizeof hmax, cudaMemcpyDeviceToHost))
-    return fail(set_err(c, LA_ERR_CUDA, "la_load_nets: %s", cudaGetErrorString(cudaGetLastError())));
-  nf.Hmax = hmax;
-  // levels
+  if (cudaMemcpy(&hmax, d_hmax, sizeof hmax, cudaMemcpyDeviceToHost)) return cuda_fail();
+  nf.Hmax = tf.Hmax = hmax;
+  // levels: (level, class) buckets
   int32_t* d_cnt = nullptr;
   int64_t* d_cur = nullptr;
-#define GET(p, n) if (st == LA_OK) st = na.get(c, &(p), (n))
   const size_t nbk = size_t(hmax + 1) * kClasses;
-  GET(nf.lvl_nodes, V); GET(d_cnt, nbk); GET(d_cur, nbk);
-  GET(nf.A, V * LD); GET(nf.Cc, V * LD); GET(nf.M, V * LD); GET(nf.sb, V * LD); GET(nf.st, V * LD);
-  GET(nf.B, V * LD);
-  GET(nf.ent, V * LD); GET(nf.Jroot, V); GET(nf.layer, V); GET(nf.b, V); GET(nf.t, V); GET(nf.s0, V);
-  GET(nf.s1, V); GET(nf.s2, V); GET(nf.W_adj, V); GET(nf.rho_adj, V);
-  const int nred = std::max(scan_blocks(c->grid.li), int((N + 255) / 256)) + 8;
-  GET(nf.red, size_t(nred) * 2);
-#undef GET
+  GETT(d_cnt, nbk); GETT(d_cur, nbk);
+  GETK(nf.lvl_nodes, V);
   if (st) return fail(st);
-  nf.red_cap = nred;
-  if (cudaMemsetAsync(d_cnt, 0, sizeof(int32_t) * nbk, s))
-    return fail(set_err(c, LA_ERR_CUDA, "la_load_nets: %s", cudaGetErrorString(cudaGetLastError())));
-  launch_level_sort(nf, d_cnt, nullptr, s);
+  tf.lvl_nodes = nf.lvl_nodes;
+  if (cudaMemsetAsync(d_cnt, 0, sizeof(int32_t) * nbk, s)) return cuda_fail();
+  launch_level_sort(tf, d_cnt, nullptr, s);
   ++c->launches;
   std::vector<int32_t> cnt(nbk);
   if (cudaMemcpyAsync(cnt.data(), d_cnt, sizeof(int32_t) * nbk, cudaMemcpyDeviceToHost, s) ||
       cudaStreamSynchronize(s))
-    return fail(set_err(c, LA_ERR_CUDA, "la_load_nets: %s", cudaGetErrorString(cudaGetLastError())));
+    return cuda_fail();
   nf.cls_off.assign(nbk + 1, 0);
   for (size_t k = 0; k < nbk; ++k) nf.cls_off[k + 1] = nf.cls_off[k] + cnt[k];
   nf.lvl_off.assign(hmax + 2, 0);
   for (int h = 0; h <= hmax + 1; ++h) nf.lvl_off[h] = nf.cls_off[size_t(h) * kClasses];
-  if (cudaMemcpyAsync(d_cur, nf.cls_off.data(), sizeof(int64_t) * nbk, cudaMemcpyHostToDevice, s))
-    return fail(set_err(c, LA_ERR_CUDA, "la_load_nets: %s", cudaGetErrorString(cudaGetLastError())));
-  launch_level_sort(nf, nullptr, d_cur, s);
-  launch_weights_eq4(c->grid.li, nf, s);
+  if (cudaMemcpyAsync(d_cur, nf.cls_off.data(), sizeof(int64_t) * nbk, cudaMemcpyHostToDevice, s)) return cuda_fail();
+  launch_level_sort(tf, nullptr, d_cur, s);
+  launch_weights_eq4(c->grid.li, tf, s);
   c->launches += 2;
-  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
-    return fail(set_err(c, LA_ERR_CUDA, "la_load_nets: %s", cudaGetErrorString(cudaGetLastError())));
+  // internal order
+  GETK(nf.root_of_net, N); GETK(nf.parent_g, V); GETK(nf.net_of, V); GETK(nf.pin, V); GETK(nf.sink_cap, V);
+  GETK(nf.kappa, V); GETK(nf.gk, V); GETK(nf.geo, V); GETK(nf.child_start, V); GETK(nf.nch, V);
+  GETK(nf.child_list, V); GETK(nf.W_eq4, V); GETK(nf.rho_eq4, V);
+  GETK(nf.A, V * LD); GETK(nf.Cc, V * LD); GETK(nf.M, V * LD); GETK(nf.B, V * LD); GETK(nf.sb, V * LD);
+  GETK(nf.st, V * LD); GETK(nf.ent, V * LD); GETK(nf.Jroot, V); GETK(nf.layer, V); GETK(nf.b, V); GETK(nf.t, V);
+  GETK(nf.s0, V); GETK(nf.s1, V); GETK(nf.s2, V); GETK(nf.s3, V); GETK(nf.s4, V); GETK(nf.W_adj, V);
+  GETK(nf.rho_adj, V);
+  const int nred = std::max(scan_blocks(c->grid.li), int((N + 255) / 256)) + 8;
+  GETK(nf.red, size_t(nred) * 2);
+#undef GETK
+#undef GETT
+  if (st) return fail(st);
+  nf.red_cap = nred;
+  launch_renumber(tf, nf, s);
+  c->launches += 2;
+  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) return cuda_fail();
+  ta.release();
   // success: replace the forest
   la_ctx_allocs* a = allocs_of(c);
   a->forest.release();
@@ -515,10 +526,11 @@ la_status la_get_assignment(la_ctx* c, int8_t* layer, int8_t* b, int8_t* t) {
   TRY(check_loaded(c));
   if (!c->forest.have_assign) return set_err(c, LA_ERR_STATE, "no assignment yet");
   DeviceGuard g(c->device);
-  const size_t V = size_t(c->forest.V);
-  if (layer) CK(cudaMemcpyAsync(layer, c->forest.layer, V, cudaMemcpyDeviceToDevice, c->stream));
-  if (b) CK(cudaMemcpyAsync(b, c->forest.b, V, cudaMemcpyDeviceToDevice, c->stream));
-  if (t) CK(cudaMemcpyAsync(t, c->forest.t, V, cudaMemcpyDeviceToDevice, c->stream));
+  Forest& f = c->forest;
+  if (layer) { launch_permute8(f.V, f.lvl_nodes, f.layer, layer, false, c->stream); ++c->launches; }
+  if (b) { launch_permute8(f.V, f.lvl_nodes, f.b, b, false, c->stream); ++c->launches; }
+  if (t) { launch_permute8(f.V, f.lvl_nodes, f.t, t, false, c->stream); ++c->launches; }
+  CK(cudaGetLastError());
   return LA_OK;
 }
 
@@ -526,19 +538,32 @@ la_status la_set_assignment(la_ctx* c, const int8_t* layer, const int8_t* b, con
   TRY(check_loaded(c));
   if (!layer || !b || !t) return set_err(c, LA_ERR_INVALID, "la_set_assignment: null pointer");
   DeviceGuard g(c->device);
-  const size_t V = size_t(c->forest.V);
+  Forest& f = c->forest;
+  // gather into internal order in scratch (s0 holds 8 bytes per node), check, then commit
+  int8_t* gl = reinterpret_cast<int8_t*>(f.s0);
+  int8_t* gb = gl + f.V;
+  int8_t* gt = gb + f.V;
+  launch_permute8(f.V, f.lvl_nodes, layer, gl, true, c->stream);
+  launch_permute8(f.V, f.lvl_nodes, b, gb, true, c->stream);
+  launch_permute8(f.V, f.lvl_nodes, t, gt, true, c->stream);
+  c->launches += 3;
   TRY(reset_dev_err(c));
-  launch_check_assignment(c, layer, b, t, c->stream);
+  launch_check_assignment(c, gl, gb, gt, c->stream);
   CK(cudaGetLastError());
   int code;
   long long idx;
   TRY(read_dev_err(c, &code, &idx));
-  if (code) return set_err(c, LA_ERR_INVALID, "la_set_assignment: %s (node %lld)", dev_err_name(code), idx);
-  CK(cudaMemcpyAsync(c->forest.layer, layer, V, cudaMemcpyDeviceToDevice, c->stream));
-  CK(cudaMemcpyAsync(c->forest.b, b, V, cudaMemcpyDeviceToDevice, c->stream));
-  CK(cudaMemcpyAsync(c->forest.t, t, V, cudaMemcpyDeviceToDevice, c->stream));
+  if (code) {
+    int32_t in_id = -1;
+    CK(cudaMemcpy(&in_id, f.lvl_nodes + idx, sizeof in_id, cudaMemcpyDeviceToHost));
+    return set_err(c, LA_ERR_INVALID, "la_set_assignment: %s (node %d)", dev_err_name(code), in_id);
+  }
+  const size_t V = size_t(f.V);
+  CK(cudaMemcpyAsync(f.layer, gl, V, cudaMemcpyDeviceToDevice, c->stream));
+  CK(cudaMemcpyAsync(f.b, gb, V, cudaMemcpyDeviceToDevice, c->stream));
+  CK(cudaMemcpyAsync(f.t, gt, V, cudaMemcpyDeviceToDevice, c->stream));
   CK(cudaStreamSynchronize(c->stream));
-  c->forest.have_assign = true;
+  f.have_assign = true;
   return LA_OK;
 }
 
@@ -606,7 +631,7 @@ la_status la_rc_from_assignment(la_ctx* c, double* R, double* C) {
   TRY(check_assigned(c));
   if (!R || !C) return set_err(c, LA_ERR_INVALID, "la_rc_from_assignment: null pointer");
   DeviceGuard g(c->device);
-  launch_rc_from_assignment(c, R, C, c->stream);
+  launch_rc_from_assignment(c, R, C, c->forest.lvl_nodes, c->stream);
   CK(cudaGetLastError());
   return LA_OK;
 }
@@ -615,7 +640,13 @@ la_status la_elmore(la_ctx* c, const double* R, const double* C, double* delay) 
   TRY(check_assigned(c));
   if (!R || !C || !delay) return set_err(c, LA_ERR_INVALID, "la_elmore: null pointer");
   DeviceGuard g(c->device);
-  launch_elmore_fwd(c, R, C, delay, c->stream);
+  Forest& f = c->forest;
+  // input order -> internal (s3, s4), the level passes, internal -> input
+  launch_permute64(f.V, f.lvl_nodes, R, f.s3, true, c->stream);
+  launch_permute64(f.V, f.lvl_nodes, C, f.s4, true, c->stream);
+  launch_elmore_fwd(c, f.s3, f.s4, f.s2, c->stream);
+  launch_permute64(f.V, f.lvl_nodes, f.s2, delay, false, c->stream);
+  c->launches += 3;
   CK(cudaGetLastError());
   return LA_OK;
 }
@@ -624,7 +655,19 @@ la_status la_elmore_backward(la_ctx* c, const double* R, const double* C, const 
   TRY(check_assigned(c));
   if (!R || !C || !gd || !dR || !dC) return set_err(c, LA_ERR_INVALID, "la_elmore_backward: null pointer");
   DeviceGuard g(c->device);
-  launch_elmore_bwd(c, R, C, gd, dR, dC, nullptr, nullptr, c->stream);
+  Forest& f = c->forest;
+  // gather R, C, g into internal order; dR, dC come back through the same
+  // scratch (each input is consumed by the pass that precedes its reuse)
+  double* gi = reinterpret_cast<double*>(f.A);  // V doubles of the DP table are free between rounds
+  launch_permute64(f.V, f.lvl_nodes, R, f.s3, true, c->stream);
+  launch_permute64(f.V, f.lvl_nodes, C, f.s4, true, c->stream);
+  launch_permute64(f.V, f.lvl_nodes, gd, gi, true, c->stream);
+  double* dRi = reinterpret_cast<double*>(f.Cc);
+  double* dCi = reinterpret_cast<double*>(f.M);
+  launch_elmore_bwd(c, f.s3, f.s4, gi, dRi, dCi, nullptr, nullptr, c->stream);
+  launch_permute64(f.V, f.lvl_nodes, dRi, dR, false, c->stream);
+  launch_permute64(f.V, f.lvl_nodes, dCi, dC, false, c->stream);
+  c->launches += 5;
   CK(cudaGetLastError());
   return LA_OK;
 }
@@ -633,9 +676,9 @@ la_status la_reweight_adjoint(la_ctx* c) {
   TRY(check_assigned(c));
   DeviceGuard g(c->device);
   Forest& f = c->forest;
-  // R and C of the assignment in scratch s1/s2; the adjoint with g = kappa at pins
-  launch_rc_from_assignment(c, f.s1, f.s2, c->stream);
-  launch_elmore_bwd(c, f.s1, f.s2, f.gk, nullptr, nullptr, f.W_adj, f.rho_adj, c->stream);
+  // R and C of the assignment in scratch s3/s4; the adjoint with g = kappa at pins
+  launch_rc_from_assignment(c, f.s3, f.s4, nullptr, c->stream);
+  launch_elmore_bwd(c, f.s3, f.s4, f.gk, nullptr, nullptr, f.W_adj, f.rho_adj, c->stream);
   CK(cudaGetLastError());
   f.have_adj = true;
   return LA_OK;
@@ -648,9 +691,9 @@ la_status la_get_weights(la_ctx* c, int32_t source, double* W, double* rho) {
     return set_err(c, LA_ERR_INVALID, "la_get_weights: unknown source %d", source);
   if (source == LA_WEIGHTS_ADJOINT && !f.have_adj) return set_err(c, LA_ERR_STATE, "no adjoint weights yet");
   DeviceGuard g(c->device);
-  const size_t bytes = sizeof(double) * size_t(f.V);
-  if (W) CK(cudaMemcpyAsync(W, source ? f.W_adj : f.W_eq4, bytes, cudaMemcpyDeviceToDevice, c->stream));
-  if (rho) CK(cudaMemcpyAsync(rho, source ? f.rho_adj : f.rho_eq4, bytes, cudaMemcpyDeviceToDevice, c->stream));
+  if (W) { launch_permute64(f.V, f.lvl_nodes, source ? f.W_adj : f.W_eq4, W, false, c->stream); ++c->launches; }
+  if (rho) { launch_permute64(f.V, f.lvl_nodes, source ? f.rho_adj : f.rho_eq4, rho, false, c->stream); ++c->launches; }
+  CK(cudaGetLastError());
   return LA_OK;
 }
 

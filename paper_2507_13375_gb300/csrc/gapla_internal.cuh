@@ -90,9 +90,14 @@ struct Forest {
   int Hmax = 0;                         // max height (levels 0..Hmax)
   std::vector<int64_t> lvl_off;         // host copy: level h is [lvl_off[h], lvl_off[h+1])
   std::vector<int64_t> cls_off;         // host copy, 4 (Hmax+1) + 1 entries: (level, node class) buckets
-  // device arrays (node ids are int32: V < 2^31)
-  int64_t* net_ptr = nullptr;           // N + 1
-  int32_t* parent_g = nullptr;          // global parent id, -1 at roots
+  // Device arrays.  Node ids are int32 (V < 2^31).  After la_load_nets every
+  // per-node array is in INTERNAL order: nodes sorted by (level, class), so a
+  // level's nodes, their table rows and their sons' rows are contiguous
+  // ranges.  lvl_nodes maps internal -> input id (outputs are scattered back
+  // through it at the API boundary).
+  int64_t* net_ptr = nullptr;           // N + 1 (input ids)
+  int32_t* root_of_net = nullptr;       // N: internal id of each net's root
+  int32_t* parent_g = nullptr;          // parent id, -1 at roots
   int32_t* net_of = nullptr;            // net of each node
   int8_t* pin = nullptr;
   double* sink_cap = nullptr;
@@ -104,7 +109,7 @@ struct Forest {
   int32_t* nch = nullptr;               // number of sons
   int32_t* child_list = nullptr;        // son ids, increasing within a parent
   int32_t* height = nullptr;
-  int32_t* lvl_nodes = nullptr;         // nodes sorted by level
+  int32_t* lvl_nodes = nullptr;         // internal -> input node id
   double* W_eq4 = nullptr;
   double* rho_eq4 = nullptr;
   double* W_adj = nullptr;
@@ -123,10 +128,12 @@ struct Forest {
   int8_t* b = nullptr;
   int8_t* t = nullptr;
   bool have_assign = false;
-  // Elmore scratch
+  // Elmore scratch (internal order)
   double* s0 = nullptr;                 // [V]
   double* s1 = nullptr;
   double* s2 = nullptr;
+  double* s3 = nullptr;
+  double* s4 = nullptr;
   double* red = nullptr;                // reduction partials: [red_cap] tof, [red_cap] J
   int red_cap = 0;
 };
@@ -192,6 +199,11 @@ void launch_level_sort(Forest& f, int32_t* lvl_cnt, int64_t* lvl_cursor, cudaStr
 void launch_weights_eq4(const LayerInfo& li, Forest& f, cudaStream_t s);
 void launch_check_assignment(la_ctx* c, const int8_t* layer, const int8_t* b, const int8_t* t,
                              cudaStream_t s);
+// input-order forest `in` (after prepare, level sort and weights) -> internal order `out`
+void launch_renumber(const Forest& in, Forest& out, cudaStream_t s);
+// dst[i] = src[perm[i]] (gather into internal order) or dst[perm[i]] = src[i] (scatter)
+void launch_permute8(int64_t V, const int32_t* perm, const int8_t* src, int8_t* dst, bool gather, cudaStream_t s);
+void launch_permute64(int64_t V, const int32_t* perm, const double* src, double* dst, bool gather, cudaStream_t s);
 // k_round.cu
 struct RoundW {
   double w_cong, w_via, w_cap, w_d, hist_w;
@@ -204,7 +216,8 @@ void launch_demand(la_ctx* c, cudaStream_t s);
 void launch_sum_roots(la_ctx* c, double* part, double* J_out, cudaStream_t s);
 int scan_blocks(const LayerInfo& li);
 // k_elmore.cu
-void launch_rc_from_assignment(la_ctx* c, double* R, double* C, cudaStream_t s);
+// R, C in internal order, or scattered to input order when perm != nullptr
+void launch_rc_from_assignment(la_ctx* c, double* R, double* C, const int32_t* perm, cudaStream_t s);
 void launch_elmore_fwd(la_ctx* c, const double* R, const double* C, double* delay, cudaStream_t s);
 void launch_elmore_bwd(la_ctx* c, const double* R, const double* C, const double* g, double* dR,
                        double* dC, double* Wsum_out, double* UJ_out, cudaStream_t s);

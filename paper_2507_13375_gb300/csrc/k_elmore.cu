@@ -13,30 +13,31 @@
 namespace gapla {
 
 __global__ void k_rc(int64_t V, const DevTables* __restrict__ tab, const int32_t* __restrict__ parent_g,
-                     const uint64_t* __restrict__ geo, const int8_t* __restrict__ layer, double* __restrict__ R,
-                     double* __restrict__ C) {
+                     const uint64_t* __restrict__ geo, const int8_t* __restrict__ layer, const int32_t* perm,
+                     double* __restrict__ R, double* __restrict__ C) {
   const int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (v >= V) return;
+  const int64_t o = perm ? perm[v] : v;
   if (parent_g[v] < 0) {
-    R[v] = 0.0;
-    C[v] = 0.0;
+    R[o] = 0.0;
+    C[o] = 0.0;
     return;
   }
   const int l = layer[v];
   const double len = double(geo_len(geo[v]));
-  R[v] = len * tab->unit_r[l];
-  C[v] = len * tab->unit_c[l];
+  R[o] = len * tab->unit_r[l];
+  C[o] = len * tab->unit_c[l];
 }
 
-void launch_rc_from_assignment(la_ctx* c, double* R, double* C, cudaStream_t s) {
+void launch_rc_from_assignment(la_ctx* c, double* R, double* C, const int32_t* perm, cudaStream_t s) {
   Forest& f = c->forest;
-  k_rc<<<(unsigned)((f.V + 255) / 256), 256, 0, s>>>(f.V, c->grid.tab_dev, f.parent_g, f.geo, f.layer, R, C);
+  k_rc<<<(unsigned)((f.V + 255) / 256), 256, 0, s>>>(f.V, c->grid.tab_dev, f.parent_g, f.geo, f.layer, perm, R, C);
   ++c->launches;
 }
 
 struct ElmArgs {
-  const int32_t *nodes, *parent_g, *child_start, *nch, *child_list, *net_of;
-  int64_t count;
+  const int32_t *parent_g, *child_start, *nch, *child_list, *net_of;
+  int64_t base, count;
   const int8_t *layer, *b, *t, *pin;
   const double *sink_cap, *r_drv, *R, *C, *g;
   const DevTables* tab;
@@ -48,7 +49,7 @@ struct ElmArgs {
 __global__ void k_elm_up(ElmArgs a) {
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= a.count) return;
-  const int v = a.nodes[i];
+  const int v = int(a.base + i);
   double s = a.parent_g[v] < 0 ? 0.0 : 0.5 * a.C[v];
   s = s + a.tab->via_c * double(a.t[v] - a.b[v]);
   s = s + a.sink_cap[v];
@@ -69,7 +70,7 @@ __global__ void k_elm_up(ElmArgs a) {
 __global__ void k_elm_delay(ElmArgs a) {
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= a.count) return;
-  const int v = a.nodes[i];
+  const int v = int(a.base + i);
   const int p = a.parent_g[v];
   const int lv = a.layer[v];
   double dj;
@@ -89,7 +90,7 @@ __global__ void k_elm_delay(ElmArgs a) {
 __global__ void k_elm_adj(ElmArgs a) {
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= a.count) return;
-  const int v = a.nodes[i];
+  const int v = int(a.base + i);
   const int p = a.parent_g[v];
   if (p < 0) {
     a.UJ[v] = a.r_drv[a.net_of[v]] * a.Ws[v];
@@ -120,7 +121,7 @@ static void per_level(la_ctx* c, ElmArgs a, K kernel, bool ascending, cudaStream
   Forest& f = c->forest;
   for (int q = 0; q <= f.Hmax; ++q) {
     const int h = ascending ? q : f.Hmax - q;
-    a.nodes = f.lvl_nodes + f.lvl_off[h];
+    a.base = f.lvl_off[h];
     a.count = f.lvl_off[h + 1] - f.lvl_off[h];
     if (a.count == 0) continue;
     kernel<<<(unsigned)((a.count + 255) / 256), 256, 0, s>>>(a);

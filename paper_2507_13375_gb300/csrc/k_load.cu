@@ -242,4 +242,78 @@ void launch_check_assignment(la_ctx* c, const int8_t* layer, const int8_t* b, co
   ++c->launches;
 }
 
+// Internal order: thread i is the node at position i of the (level, class)
+// sort; in = its input id.
+__global__ void k_inverse_perm(int64_t V, const int32_t* __restrict__ int2in, int32_t* __restrict__ in2int) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < V) in2int[int2in[i]] = int32_t(i);
+}
+
+struct RenumArgs {
+  int64_t V;
+  const int32_t *int2in, *in2int;
+  const int32_t *parent_in, *net_of_in, *child_start_in, *nch_in, *child_list_in;
+  const int8_t* pin_in;
+  const double *cap_in, *kap_in, *gk_in, *W_in, *rho_in;
+  const uint64_t* geo_in;
+  int32_t *parent, *net_of, *child_start, *nch, *child_list, *root_of_net;
+  int8_t* pin;
+  double *cap, *kap, *gk, *W, *rho;
+  uint64_t* geo;
+};
+
+__global__ void k_renumber(RenumArgs a) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= a.V) return;
+  const int in = a.int2in[i];
+  const int p = a.parent_in[in];
+  a.parent[i] = p < 0 ? -1 : a.in2int[p];
+  if (p < 0) a.root_of_net[a.net_of_in[in]] = int32_t(i);
+  a.net_of[i] = a.net_of_in[in];
+  a.pin[i] = a.pin_in[in];
+  a.cap[i] = a.cap_in[in];
+  a.kap[i] = a.kap_in[in];
+  a.gk[i] = a.gk_in[in];
+  a.W[i] = a.W_in[in];
+  a.rho[i] = a.rho_in[in];
+  a.geo[i] = a.geo_in[in];
+  // the son slots of a node keep their place; their contents become internal ids
+  const int cs = a.child_start_in[in], nc = a.nch_in[in];
+  a.child_start[i] = cs;
+  a.nch[i] = nc;
+  for (int k = 0; k < nc; ++k) a.child_list[cs + k] = a.in2int[a.child_list_in[cs + k]];
+}
+
+void launch_renumber(const Forest& in, Forest& out, cudaStream_t s) {
+  const int T = 256;
+  const unsigned B = (unsigned)((in.V + T - 1) / T);
+  // the parent's height array is free now: reuse it for input -> internal ids
+  int32_t* in2int = in.height;
+  k_inverse_perm<<<B, T, 0, s>>>(in.V, out.lvl_nodes, in2int);
+  RenumArgs a;
+  a.V = in.V; a.int2in = out.lvl_nodes; a.in2int = in2int;
+  a.parent_in = in.parent_g; a.net_of_in = in.net_of; a.child_start_in = in.child_start; a.nch_in = in.nch;
+  a.child_list_in = in.child_list; a.pin_in = in.pin; a.cap_in = in.sink_cap; a.kap_in = in.kappa; a.gk_in = in.gk;
+  a.W_in = in.W_eq4; a.rho_in = in.rho_eq4; a.geo_in = in.geo;
+  a.parent = out.parent_g; a.net_of = out.net_of; a.child_start = out.child_start; a.nch = out.nch;
+  a.child_list = out.child_list; a.root_of_net = out.root_of_net; a.pin = out.pin; a.cap = out.sink_cap;
+  a.kap = out.kappa; a.gk = out.gk; a.W = out.W_eq4; a.rho = out.rho_eq4; a.geo = out.geo;
+  k_renumber<<<B, T, 0, s>>>(a);
+}
+
+template <typename T>
+__global__ void k_permute(int64_t V, const int32_t* __restrict__ perm, const T* __restrict__ src, T* __restrict__ dst,
+                          bool gather) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= V) return;
+  if (gather) dst[i] = src[perm[i]];
+  else dst[perm[i]] = src[i];
+}
+void launch_permute8(int64_t V, const int32_t* perm, const int8_t* src, int8_t* dst, bool gather, cudaStream_t s) {
+  k_permute<int8_t><<<(unsigned)((V + 255) / 256), 256, 0, s>>>(V, perm, src, dst, gather);
+}
+void launch_permute64(int64_t V, const int32_t* perm, const double* src, double* dst, bool gather, cudaStream_t s) {
+  k_permute<double><<<(unsigned)((V + 255) / 256), 256, 0, s>>>(V, perm, src, dst, gather);
+}
+
 }  // namespace gapla

@@ -153,7 +153,7 @@ void launch_scan_lines(la_ctx* c, bool from_diff, double hist_w, double* tof_par
 // ---------------------------------------------------------------------------
 struct DPArgs {
   int LD;
-  const int32_t* nodes;
+  int64_t base;          // first node of the (level, class) bucket
   int64_t count;
   const int32_t *parent_g, *child_start, *nch, *child_list;
   const int8_t* pin;
@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(256) k_dp_level(LayerInfo li, DPArgs a) {
   const int64_t node_i = ROOT ? k : k / a.LD;
   const int ldi = ROOT ? 0 : int(k - node_i * a.LD);
   if (node_i >= a.count) return;
-  const int v = a.nodes[node_i];
+  const int v = int(a.base + node_i);
   const int L = li.L, LD = a.LD;
   const int pin = a.pin[v];
   const uint64_t gv = a.geo[v];
@@ -386,7 +386,7 @@ void launch_dp_level(la_ctx* c, const RoundW& w, const double* W, const double* 
     const size_t bk = size_t(level) * kClasses + cls;
     const int64_t n = f.cls_off[bk + 1] - f.cls_off[bk];
     if (n == 0) continue;
-    a.nodes = f.lvl_nodes + f.cls_off[bk];
+    a.base = f.cls_off[bk];
     a.count = n;
     if (L <= 6) dp_launch_class<6>(c, a, cls, s);
     else if (L <= 12) dp_launch_class<12>(c, a, cls, s);
@@ -397,14 +397,14 @@ void launch_dp_level(la_ctx* c, const RoundW& w, const double* W, const double* 
 // ---------------------------------------------------------------------------
 // Backtrack (Alg. 4): top-down, one thread per node of the level.
 // ---------------------------------------------------------------------------
-__global__ void k_backtrack_level(const int32_t* __restrict__ nodes, int64_t count, int LD,
+__global__ void k_backtrack_level(int64_t base, int64_t count, int LD,
                                   const DevTables* __restrict__ tab, const int32_t* __restrict__ parent_g,
                                   const int8_t* __restrict__ pin, const int8_t* __restrict__ ent,
                                   const int8_t* __restrict__ sb, const int8_t* __restrict__ st,
                                   int8_t* __restrict__ layer, int8_t* __restrict__ b, int8_t* __restrict__ t) {
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= count) return;
-  const int v = nodes[i];
+  const int v = int(base + i);
   const int gp = parent_g[v];
   int l, idx;
   if (gp < 0) {
@@ -426,7 +426,7 @@ void launch_backtrack_level(la_ctx* c, int level, cudaStream_t s) {
   const int64_t n = f.lvl_off[level + 1] - f.lvl_off[level];
   if (n == 0) return;
   const int T = 256;
-  k_backtrack_level<<<(unsigned)((n + T - 1) / T), T, 0, s>>>(f.lvl_nodes + f.lvl_off[level], n, c->LD,
+  k_backtrack_level<<<(unsigned)((n + T - 1) / T), T, 0, s>>>(f.lvl_off[level], n, c->LD,
                                                             c->grid.tab_dev, f.parent_g, f.pin, f.ent, f.sb,
                                                             f.st, f.layer, f.b, f.t);
   ++c->launches;
@@ -484,14 +484,14 @@ void launch_demand(la_ctx* c, cudaStream_t s) {
 }
 
 // Per-block partial sums of the root costs J_n, in net order (deterministic).
-__global__ void __launch_bounds__(256) k_sum_roots(int64_t N, const int64_t* __restrict__ net_ptr,
+__global__ void __launch_bounds__(256) k_sum_roots(int64_t N, const int32_t* __restrict__ root_of_net,
                                                    const double* __restrict__ Jroot, double* __restrict__ part,
                                                    double* __restrict__ J_out) {
   __shared__ double s_p[8];
   const int64_t n = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   double x = 0.0;
   if (n < N) {
-    x = Jroot[net_ptr[n]];
+    x = Jroot[root_of_net[n]];
     if (J_out) J_out[n] = x;
   }
   x = warp_sum(x);
@@ -506,7 +506,7 @@ __global__ void __launch_bounds__(256) k_sum_roots(int64_t N, const int64_t* __r
 
 void launch_sum_roots(la_ctx* c, double* part, double* J_out, cudaStream_t s) {
   Forest& f = c->forest;
-  k_sum_roots<<<(unsigned)((f.N + 255) / 256), 256, 0, s>>>(f.N, f.net_ptr, f.Jroot, part, J_out);
+  k_sum_roots<<<(unsigned)((f.N + 255) / 256), 256, 0, s>>>(f.N, f.root_of_net, f.Jroot, part, J_out);
   ++c->launches;
 }
 
