@@ -207,6 +207,39 @@ la_status la_reweight_adjoint(la_ctx* ctx);
  * source (LA_WEIGHTS_EQ4 or LA_WEIGHTS_ADJOINT). */
 la_status la_get_weights(la_ctx* ctx, int32_t source, double* W, double* rho);
 
+/* ---------------------------------------------------------------------------
+ * Allocation-free Elmore forward pass.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory at all,
+ * for example code whose device memory is entirely owned by another
+ * allocator, or code on a latency-critical path that must not call
+ * cudaMalloc (which may synchronise the device and takes unbounded time).
+ *
+ * It computes exactly what la_elmore computes (delay[v] at v's pin point for
+ * pin nodes, at its junction otherwise) for a forest and an assignment given
+ * directly, without a context, and makes no allocation of any kind.  Its
+ * scratch (2 doubles per node) is a fixed device array compiled into the
+ * library, LA_STATIC_MAX_NODES nodes large (32 MiB), which every GPU that
+ * loads the library holds until the process exits.
+ *   nets:           device pointers; net_ptr, parent, pin_layer, sink_cap and
+ *                   r_drv are read (x, y, kappa are not)
+ *   layer, b, t:    device, V: junction layers and via stacks (input order,
+ *                   as la_get_assignment returns them)
+ *   L, via_r, via_c: the layer count, host via_r[L-1] and the via cap
+ *   R_seg, C_seg:   device, V (root entries ignored); delay: device, V output
+ *   stream:         cudaStream_t to enqueue on (NULL = legacy default stream)
+ * Runs on the calling thread's current CUDA device; all pointers must be on
+ * it.  The first call on a device looks up the device address of the scratch
+ * array (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  Every call uses the same scratch, which keeps the last call's
+ * contents, so calls that overlap on the GPU (other streams, other host
+ * threads) race.  Returns LA_ERR_INVALID for more than LA_STATIC_MAX_NODES
+ * nodes or bad arguments (la_last_error(NULL) says which); a net whose parent
+ * ids are out of order or whose layers are out of range gets NaN delays. */
+#define LA_STATIC_MAX_NODES (1 << 21)
+la_status la_elmore_static(const la_net_desc* nets, const int8_t* layer, const int8_t* b, const int8_t* t,
+                           int32_t L, const double* via_r, double via_c, const double* R_seg,
+                           const double* C_seg, double* delay, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -35,7 +35,8 @@ EXPORTS = ("la_create", "la_destroy", "la_last_error", "la_set_stream", "la_devi
            "la_launch_count",
            "la_load_grid", "la_load_nets", "la_assign_round", "la_get_assignment", "la_set_assignment",
            "la_get_net_cost", "la_get_state", "la_set_state", "la_rc_from_assignment", "la_elmore",
-           "la_elmore_backward", "la_reweight_adjoint", "la_get_weights")
+           "la_elmore_backward", "la_reweight_adjoint", "la_get_weights", "la_elmore_static")
+LA_STATIC_MAX_NODES = 1 << 21
 
 
 class LaError(RuntimeError):
@@ -95,6 +96,7 @@ def library() -> ctypes.CDLL:
         "la_rc_from_assignment": [vp, vp, vp], "la_elmore": [vp, vp, vp, vp],
         "la_elmore_backward": [vp, vp, vp, vp, vp, vp], "la_reweight_adjoint": [vp],
         "la_get_weights": [vp, i32, vp, vp],
+        "la_elmore_static": [P(NetDesc), vp, vp, vp, i32, vp, ctypes.c_double, vp, vp, vp, vp],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -238,6 +240,26 @@ def la_reweight_adjoint(ctx):
 
 def la_get_weights(ctx, source, W, rho):
     _check(ctx, library().la_get_weights(ctx, int(source), _ptr(W), _ptr(rho)))
+
+
+def la_elmore_static(nets: dict, layer, b, t, L: int, via_r, via_c: float, R, C, delay, stream=None,
+                     num_nodes: int | None = None):
+    """The allocation-free Elmore forward pass (see include/gapla.h).
+
+    nets: CUDA tensors net_ptr, parent, pin_layer, sink_cap, r_drv (x, y,
+    kappa optional); layer, b, t, R, C, delay: CUDA tensors in input order.
+    Nothing is allocated on the device by the library for this call."""
+    lib = library()
+    keep = np.ascontiguousarray(via_r, np.float64)
+    z = lambda k: nets[k].data_ptr() if k in nets and nets[k] is not None else None
+    d = NetDesc(int(nets["r_drv"].numel()), int(num_nodes if num_nodes is not None else nets["parent"].numel()),
+                z("net_ptr"), z("x"), z("y"), z("parent"), z("pin_layer"), z("sink_cap"), z("kappa"), z("r_drv"))
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    st = lib.la_elmore_static(ctypes.byref(d), _ptr(layer), _ptr(b), _ptr(t), int(L), keep.ctypes.data,
+                              float(via_c), _ptr(R), _ptr(C), _ptr(delay), ctypes.c_void_p(stream))
+    if st != LA_OK:
+        raise LaError(st, lib.la_last_error(None).decode())
 
 
 # ------------------------------ convenience ------------------------------

@@ -82,6 +82,8 @@ struct Allocs {
 
 }  // namespace
 
+void gapla::set_noctx_error(const std::string& msg) { g_create_err = msg; }
+
 // Allocation groups live beside the context (kept out of the shared header).
 struct la_ctx_allocs {
   Allocs grid, forest;

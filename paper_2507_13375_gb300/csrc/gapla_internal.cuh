@@ -222,6 +222,9 @@ void launch_elmore_fwd(la_ctx* c, const double* R, const double* C, double* dela
 void launch_elmore_bwd(la_ctx* c, const double* R, const double* C, const double* g, double* dR,
                        double* dC, double* Wsum_out, double* UJ_out, cudaStream_t s);
 
+// error message of calls that have no context (read by la_last_error(NULL))
+void set_noctx_error(const std::string& msg);
+
 // small device helpers
 __device__ __forceinline__ void dev_error(unsigned long long* err, int code, int64_t index) {
   unsigned long long key = (static_cast<unsigned long long>(index) << 8) | static_cast<unsigned long long>(code);
