@@ -154,6 +154,13 @@ typedef struct {
   double ms_backtrack;     /*   the top-down backtrack, all levels (Alg. 4)          */
   double ms_demand;        /*   demand + line scan (D, H and the next penalty prefix) */
   int64_t launches;        /* kernels this round launched                            */
+  /* batched form only: the autotuner's choice (nets with at most 2^split nodes
+   * run as level waves, larger ones in the persistent block-per-net kernels) */
+  int32_t batch_split, batch_block;
+  int64_t batch_big_nets;
+  int32_t batch_cached;    /* 1: round-invariant constants cached per weight set  */
+  int32_t reserved2;
+  double batch_tune_ms;    /* its DP + backtrack time when it was chosen         */
 } la_round_stats;
 
 /* Run one round against the current snapshot (D, H): every net sees the same

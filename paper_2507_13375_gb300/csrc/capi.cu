@@ -155,6 +155,10 @@ la_status la_create(la_ctx** out, int device, void* stream) {
   bool ok = cudaMalloc(&c->d_err, sizeof(unsigned long long)) == cudaSuccess &&
             cudaMalloc(&c->d_stats, sizeof(Stats)) == cudaSuccess;
   for (auto& e2 : c->ev) ok = ok && cudaEventCreate(&e2) == cudaSuccess;
+  ok = ok && cudaStreamCreateWithFlags(&c->s2, cudaStreamNonBlocking) == cudaSuccess &&
+       cudaStreamCreateWithFlags(&c->s_cap, cudaStreamNonBlocking) == cudaSuccess &&
+       cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
+       cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) == cudaSuccess;
   if (!ok) {
     g_create_err = std::string("context set-up failed: ") + cudaGetErrorString(cudaGetLastError());
     la_destroy(c);
@@ -177,6 +181,12 @@ la_status la_destroy(la_ctx* c) {
   if (c->d_stats) cudaFree(c->d_stats);
   for (auto& e2 : c->ev)
     if (e2) cudaEventDestroy(e2);
+  for (auto& e2 : c->plan.exec)
+    if (e2) cudaGraphExecDestroy(e2);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->s2) cudaStreamDestroy(c->s2);
+  if (c->s_cap) cudaStreamDestroy(c->s_cap);
   delete c;
   return LA_OK;
 }
@@ -330,7 +340,10 @@ la_status la_load_grid(la_ctx* c, const la_grid_desc* gd) {
   if (cudaGetLastError() != cudaSuccess || read_dev_err(c, &code, &idx) != LA_OK)
     return fail(set_err(c, LA_ERR_CUDA, "la_load_grid: kernel launch failed"));
   if (code) return fail(set_err(c, LA_ERR_INVALID, "la_load_grid: capacity %lld is negative", idx));
-  // success: replace the grid, drop the forest
+  // success: replace the grid, drop the forest and the batched plan
+  for (auto& e2 : c->plan.exec)
+    if (e2) cudaGraphExecDestroy(e2);
+  c->plan = BatchPlan();
   la_ctx_allocs* a = allocs_of(c);
   a->forest.release();
   a->grid.release();
@@ -387,10 +400,10 @@ la_status la_load_nets(la_ctx* c, const la_net_desc* nd) {
   int hmax = 0;
   if (cudaMemcpy(&hmax, d_hmax, sizeof hmax, cudaMemcpyDeviceToHost)) return cuda_fail();
   nf.Hmax = tf.Hmax = hmax;
-  // levels: (level, class) buckets
+  // levels: (level, class, size class) buckets
   int32_t* d_cnt = nullptr;
   int64_t* d_cur = nullptr;
-  const size_t nbk = size_t(hmax + 1) * kClasses;
+  const size_t nbk = size_t(bucket_key(hmax + 1, 0, 0));
   GETT(d_cnt, nbk); GETT(d_cur, nbk);
   GETK(nf.lvl_nodes, V);
   if (st) return fail(st);
@@ -402,14 +415,46 @@ la_status la_load_nets(la_ctx* c, const la_net_desc* nd) {
   if (cudaMemcpyAsync(cnt.data(), d_cnt, sizeof(int32_t) * nbk, cudaMemcpyDeviceToHost, s) ||
       cudaStreamSynchronize(s))
     return cuda_fail();
-  nf.cls_off.assign(nbk + 1, 0);
-  for (size_t k = 0; k < nbk; ++k) nf.cls_off[k + 1] = nf.cls_off[k] + cnt[k];
+  nf.key_off.assign(nbk + 1, 0);
+  for (size_t k = 0; k < nbk; ++k) nf.key_off[k + 1] = nf.key_off[k] + cnt[k];
   nf.lvl_off.assign(hmax + 2, 0);
-  for (int h = 0; h <= hmax + 1; ++h) nf.lvl_off[h] = nf.cls_off[size_t(h) * kClasses];
-  if (cudaMemcpyAsync(d_cur, nf.cls_off.data(), sizeof(int64_t) * nbk, cudaMemcpyHostToDevice, s)) return cuda_fail();
+  for (int h = 0; h <= hmax + 1; ++h) nf.lvl_off[h] = nf.key_off[size_t(bucket_key(h, 0, 0))];
+  if (cudaMemcpyAsync(d_cur, nf.key_off.data(), sizeof(int64_t) * nbk, cudaMemcpyHostToDevice, s)) return cuda_fail();
   launch_level_sort(tf, nullptr, d_cur, s);
   launch_weights_eq4(c->grid.li, tf, s);
   c->launches += 2;
+  // per-net level lists and the big-net queue, then the internal order
+  int32_t* in2int = nullptr;
+  int32_t* d_sc = nullptr;
+  int64_t* d_sccur = nullptr;
+  GETT(in2int, V); GETT(d_sc, kSizeClasses); GETT(d_sccur, kSizeClasses);
+  GETK(nf.bl_nodes, V); GETK(nf.bl_hoff, V + N); GETK(nf.net_H, N); GETK(nf.queue_ctr, 4);
+  if (st) return fail(st);
+  if (cudaMemsetAsync(d_sc, 0, sizeof(int32_t) * kSizeClasses, s)) return cuda_fail();
+  launch_inverse_perm(tf.V, nf.lvl_nodes, in2int, s);
+  launch_net_levels(tf, in2int, nf, d_sc, nullptr, s);
+  c->launches += 2;
+  std::vector<int32_t> sc_cnt(kSizeClasses);
+  if (cudaMemcpyAsync(sc_cnt.data(), d_sc, sizeof(int32_t) * kSizeClasses, cudaMemcpyDeviceToHost, s) ||
+      cudaStreamSynchronize(s))
+    return cuda_fail();
+  {
+    // queue order: size class descending (largest nets first)
+    std::vector<int64_t> cur(kSizeClasses, 0);
+    int64_t acc = 0;
+    nf.big_sc_cnt.assign(kSizeClasses, 0);
+    for (int sc = kSizeClasses - 1; sc >= kMinBigSc; --sc) {
+      cur[sc] = acc;
+      acc += sc_cnt[sc];
+      nf.big_sc_cnt[sc] = sc_cnt[sc];
+    }
+    GETK(nf.big_queue, size_t(std::max<int64_t>(acc, 1)));
+    if (st) return fail(st);
+    if (cudaMemcpyAsync(d_sccur, cur.data(), sizeof(int64_t) * kSizeClasses, cudaMemcpyHostToDevice, s))
+      return cuda_fail();
+    launch_net_levels(tf, in2int, nf, nullptr, d_sccur, s);
+    ++c->launches;
+  }
   // internal order
   GETK(nf.root_of_net, N); GETK(nf.parent_g, V); GETK(nf.net_of, V); GETK(nf.pin, V); GETK(nf.sink_cap, V);
   GETK(nf.kappa, V); GETK(nf.gk, V); GETK(nf.geo, V); GETK(nf.child_start, V); GETK(nf.nch, V);
@@ -424,11 +469,24 @@ la_status la_load_nets(la_ctx* c, const la_net_desc* nd) {
 #undef GETT
   if (st) return fail(st);
   nf.red_cap = nred;
-  launch_renumber(tf, nf, s);
-  c->launches += 2;
+  {
+    // every array the kernels below and the rounds use must exist
+    const void* need[] = {nf.net_ptr, nf.r_drv, nf.lvl_nodes, nf.bl_nodes, nf.bl_hoff, nf.net_H, nf.queue_ctr,
+                          nf.big_queue, nf.root_of_net, nf.parent_g, nf.net_of, nf.pin, nf.sink_cap, nf.kappa,
+                          nf.gk, nf.geo, nf.child_start, nf.nch, nf.child_list, nf.W_eq4, nf.rho_eq4, nf.A, nf.Cc,
+                          nf.M, nf.B, nf.sb, nf.st, nf.ent, nf.Jroot, nf.layer, nf.b, nf.t, nf.s0, nf.s1, nf.s2,
+                          nf.s3, nf.s4, nf.W_adj, nf.rho_adj, nf.red, in2int};
+    for (const void* q : need)
+      if (!q) return fail(set_err(c, LA_ERR_STATE, "la_load_nets: internal allocation missing"));
+  }
+  launch_renumber(tf, in2int, nf, s);
+  ++c->launches;
   if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) return cuda_fail();
   ta.release();
-  // success: replace the forest
+  // success: replace the forest (and forget the batched plan of the old one)
+  for (auto& e2 : c->plan.exec)
+    if (e2) cudaGraphExecDestroy(e2);
+  c->plan = BatchPlan();
   la_ctx_allocs* a = allocs_of(c);
   a->forest.release();
   a->forest = na;
@@ -440,6 +498,172 @@ la_status la_load_nets(la_ctx* c, const la_net_desc* nd) {
 static la_status check_loaded(la_ctx* c) {
   TRY(check_ctx(c));
   if (!c->grid.loaded || c->forest.V == 0) return set_err(c, LA_ERR_STATE, "load a grid and a forest first");
+  return LA_OK;
+}
+
+// ---- batched form ----
+static BatchPlan make_plan(la_ctx* c, int k, int block, bool one_per_sm) {
+  Forest& f = c->forest;
+  BatchPlan bp;
+  bp.k = k;
+  bp.block = block;
+  for (int sc = std::max(k + 1, kMinBigSc); sc < kSizeClasses; ++sc) bp.n_big += f.big_sc_cnt[sc];
+  bp.Hs = 0;
+  for (int h = f.Hmax; h >= 0; --h) {
+    int64_t n = 0;
+    for (int cls = 0; cls < kClasses; ++cls)
+      n += f.key_off[size_t(bucket_key(h, cls, k + 1))] - f.key_off[size_t(bucket_key(h, cls, 0))];
+    if (n > 0) { bp.Hs = h; break; }
+  }
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+  const int per_sm = one_per_sm ? 1 : bignet_blocks_per_sm(c->grid.li.L, block);
+  bp.grid = int(std::min<int64_t>(bp.n_big, int64_t(sms) * per_sm));
+  if (bp.grid < 1) bp.grid = 1;
+  return bp;
+}
+
+// DP and backtrack of the batched form: small nets on `s`, big nets on s2.
+// fuse: the backtrack also updates the demand (not during tuning trials).
+static la_status enqueue_batched(la_ctx* c, const BatchPlan& bp, const RoundW& w, const double* W, const double* rho,
+                                 int si, bool fuse, cudaStream_t s) {
+  const int cache = bp.cached ? si : -1;
+  Forest& f = c->forest;
+  if (bp.n_big > 0) {
+    CK(cudaEventRecord(c->ev_fork, s));
+    CK(cudaStreamWaitEvent(c->s2, c->ev_fork, 0));
+    CK(cudaMemsetAsync(f.queue_ctr, 0, 2 * sizeof(int), c->s2));
+    launch_dp_bignets(c, w, W, rho, bp.n_big, bp.grid, bp.block, cache, c->s2);
+    launch_backtrack_bignets(c, bp.n_big, bp.grid, bp.block, fuse, c->s2);
+    CK(cudaEventRecord(c->ev_join, c->s2));
+  }
+  for (int h = 0; h <= bp.Hs; ++h) launch_dp_level(c, w, W, rho, h, bp.k, cache, s);
+  for (int h = bp.Hs; h >= 0; --h) launch_backtrack_level(c, h, bp.k, fuse, s);
+  if (bp.n_big > 0) CK(cudaStreamWaitEvent(s, c->ev_join, 0));
+  CK(cudaGetLastError());
+  return LA_OK;
+}
+
+// The batched form's constant caches: allocated on first use, refreshed when
+// the weight set (W, w_d, w_cap) changes; w_d r_est per round.
+static la_status batched_caches(la_ctx* c, const RoundW& w, const double* W, int si, cudaStream_t s) {
+  Forest& f = c->forest;
+  if (!f.ncache[si]) {
+    la_ctx_allocs* a = allocs_of(c);
+    TRY(a->forest.get(c, &f.ncache[si], size_t(f.V) * 4));
+    TRY(a->forest.get(c, &f.scache[si], size_t(f.V) * c->LD * 3));
+  }
+  BatchPlan& bp = c->plan;
+  if (bp.cache_wd[si] != w.w_d || bp.cache_wcap[si] != w.w_cap) {
+    launch_seg_consts(c, w, W, si, s);
+    CK(cudaGetLastError());
+    bp.cache_wd[si] = w.w_d;
+    bp.cache_wcap[si] = w.w_cap;
+  }
+  return LA_OK;
+}
+
+// Autotuner: time the DP + backtrack of every distinct split (size-class
+// threshold) and block shape on the loaded forest, keep the fastest.  The
+// trials compute the same tables the round computes next.
+static la_status autotune(la_ctx* c, const RoundW& w, const double* W, const double* rho, int si, cudaStream_t s) {
+  Forest& f = c->forest;
+  TRY(batched_caches(c, w, W, si, s));
+  launch_node_round(c, w, rho, si, s);
+  std::vector<BatchPlan> cand;
+  int64_t last_big = -1;
+  for (int k = kSizeClasses - 1; k >= kMinBigSc - 1; --k) {
+    BatchPlan b = make_plan(c, k, 256, false);
+    if (b.n_big == last_big) continue;
+    last_big = b.n_big;
+    cand.push_back(b);
+    if (b.n_big > 0) {
+      cand.push_back(make_plan(c, k, 128, false));
+      cand.push_back(make_plan(c, k, 256, true));
+    }
+  }
+  // each shape with the constant caches and without
+  const size_t nshape = cand.size();
+  for (size_t i = 0; i < nshape; ++i) {
+    BatchPlan b = cand[i];
+    b.cached = false;
+    cand.push_back(b);
+  }
+  double best = 1e30;
+  BatchPlan chosen = cand.front();
+  for (auto& b : cand) {
+    double t = 1e30;
+    for (int rep = 0; rep < 2; ++rep) {
+      CK(cudaEventRecord(c->ev[1], s));
+      TRY(enqueue_batched(c, b, w, W, rho, si, false, s));
+      CK(cudaEventRecord(c->ev[2], s));
+      CK(cudaEventSynchronize(c->ev[2]));
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, c->ev[1], c->ev[2]));
+      t = std::min(t, double(ms));
+    }
+    if (t < best) { best = t; chosen = b; }
+  }
+  (void)f;
+  chosen.tuned = true;
+  chosen.best_ms = best;
+  chosen.trials = int(cand.size());
+  for (int i = 0; i < 2; ++i) {
+    chosen.cache_wd[i] = c->plan.cache_wd[i];
+    chosen.cache_wcap[i] = c->plan.cache_wcap[i];
+  }
+  c->plan = chosen;
+  return LA_OK;
+}
+
+// The round after the penalty prefix, as one CUDA graph (captured once per
+// weights and parameter set on the context's own capture stream, replayed on
+// the caller's stream every round; the caller's stream may be the legacy
+// default stream, which cannot be captured).
+static la_status batched_graph(la_ctx* c, const RoundW& w, const double* W, const double* rho, int si,
+                               cudaStream_t s_run) {
+  BatchPlan& bp = c->plan;
+  cudaStream_t s = c->s_cap;
+  const double wv[5] = {w.w_cong, w.w_via, w.w_cap, w.w_d, w.hist_w};
+  bool same = bp.exec[si] != nullptr;
+  for (int i = 0; i < 5 && same; ++i) same = bp.w[si][i] == wv[i];
+  if (!same) {
+    if (bp.exec[si]) {
+      cudaGraphExecDestroy(bp.exec[si]);
+      bp.exec[si] = nullptr;
+    }
+    const long long l0 = c->launches;
+    CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    la_status st = LA_OK;
+    // phase events as external record nodes of the graph (timed on replay)
+    auto mark = [&](cudaEvent_t e) {
+      if (st == LA_OK && cudaEventRecordWithFlags(e, s, cudaEventRecordExternal) != cudaSuccess) st = LA_ERR_CUDA;
+    };
+    launch_node_round(c, w, rho, si, s);
+    mark(c->ev[1]);
+    if (st == LA_OK) st = enqueue_batched(c, bp, w, W, rho, si, true, s);
+    mark(c->ev[3]);
+    Forest& f = c->forest;
+    if (st == LA_OK) {
+      launch_scan_lines(c, true, w.hist_w, f.red, s);
+      launch_sum_roots(c, f.red + f.red_cap, nullptr, s);
+    }
+    mark(c->ev[4]);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(s, &g);
+    if (st != LA_OK || e != cudaSuccess || !g) {
+      if (g) cudaGraphDestroy(g);
+      return set_err(c, LA_ERR_CUDA, "la_assign_round: graph capture failed: %s", cudaGetErrorString(e));
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&bp.exec[si], g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) return set_err(c, LA_ERR_CUDA, "la_assign_round: graph instantiate: %s", cudaGetErrorString(ei));
+    bp.graph_launches[si] = c->launches - l0;
+    c->launches = l0;
+    for (int i = 0; i < 5; ++i) bp.w[si][i] = wv[i];
+  }
+  CK(cudaGraphLaunch(bp.exec[si], s_run));
+  c->launches += bp.graph_launches[si];
   return LA_OK;
 }
 
@@ -457,8 +681,6 @@ la_status la_assign_round(la_ctx* c, const la_round_params* p, la_round_stats* s
   Grid& gr = c->grid;
   if (p->weights == LA_WEIGHTS_ADJOINT && !f.have_adj)
     return set_err(c, LA_ERR_STATE, "la_assign_round: no adjoint weights yet (call la_reweight_adjoint)");
-  if (p->mode == LA_MODE_BATCHED)
-    return set_err(c, LA_ERR_INVALID, "la_assign_round: batched mode is not available in this build");
   const double* W = p->weights == LA_WEIGHTS_ADJOINT ? f.W_adj : f.W_eq4;
   const double* rho = p->weights == LA_WEIGHTS_ADJOINT ? f.rho_adj : f.rho_eq4;
   DeviceGuard g(c->device);
@@ -473,19 +695,29 @@ la_status la_assign_round(la_ctx* c, const la_round_params* p, la_round_stats* s
   CK(cudaMemsetAsync(c->d_stats, 0, sizeof(Stats), s));
   TRY(reset_dev_err(c));
   const long long launches0 = c->launches;
-  CK(cudaEventRecord(c->ev[0], s));
   double* tof_part = f.red;
   double* J_part = f.red + f.red_cap;
   if (!gr.P_valid || gr.P_hist_w != p->hist_w) launch_scan_lines(c, false, p->hist_w, tof_part, s);
-  CK(cudaEventRecord(c->ev[1], s));
-  for (int h = 0; h <= f.Hmax; ++h) launch_dp_level(c, w, W, rho, h, s);
-  CK(cudaEventRecord(c->ev[2], s));
-  for (int h = f.Hmax; h >= 0; --h) launch_backtrack_level(c, h, s);
-  CK(cudaEventRecord(c->ev[3], s));
-  launch_demand(c, s);
-  launch_scan_lines(c, true, p->hist_w, tof_part, s);
-  launch_sum_roots(c, J_part, nullptr, s);
-  CK(cudaEventRecord(c->ev[4], s));
+  const bool batched = p->mode == LA_MODE_BATCHED;
+  const int si = p->weights == LA_WEIGHTS_ADJOINT ? 1 : 0;
+  if (batched) {
+    TRY(batched_caches(c, w, W, si, s));
+    if (!c->plan.tuned) TRY(autotune(c, w, W, rho, si, s));
+  }
+  CK(cudaEventRecord(c->ev[0], s));
+  if (batched) {
+    TRY(batched_graph(c, w, W, rho, si, s));
+  } else {
+    CK(cudaEventRecord(c->ev[1], s));
+    for (int h = 0; h <= f.Hmax; ++h) launch_dp_level(c, w, W, rho, h, kSizeClasses - 1, false, s);
+    CK(cudaEventRecord(c->ev[2], s));
+    for (int h = f.Hmax; h >= 0; --h) launch_backtrack_level(c, h, kSizeClasses - 1, false, s);
+    CK(cudaEventRecord(c->ev[3], s));
+    launch_demand(c, s);
+    launch_scan_lines(c, true, p->hist_w, tof_part, s);
+    launch_sum_roots(c, J_part, nullptr, s);
+    CK(cudaEventRecord(c->ev[4], s));
+  }
   CK(cudaGetLastError());
   gr.P_valid = true;
   gr.P_hist_w = p->hist_w;
@@ -505,10 +737,22 @@ la_status la_assign_round(la_ctx* c, const la_round_params* p, la_round_stats* s
   for (int i = 0; i < nsb; ++i) tof += part[i];
   for (int i = 0; i < njb; ++i) J += part[f.red_cap + i];
   float ms = 0.f, ms_dp = 0.f, ms_bt = 0.f, ms_dem = 0.f;
-  CK(cudaEventElapsedTime(&ms, c->ev[0], c->ev[4]));
-  CK(cudaEventElapsedTime(&ms_dp, c->ev[1], c->ev[2]));
-  CK(cudaEventElapsedTime(&ms_bt, c->ev[2], c->ev[3]));
-  CK(cudaEventElapsedTime(&ms_dem, c->ev[3], c->ev[4]));
+  // phase times from events (inside the graph for the batched form); a
+  // phase whose events cannot be timed is reported as -1
+  auto elapsed = [&](float* out, cudaEvent_t a, cudaEvent_t b) {
+    if (cudaEventElapsedTime(out, a, b) != cudaSuccess) {
+      cudaGetLastError();
+      *out = -1.f;
+    }
+  };
+  elapsed(&ms, c->ev[0], c->ev[4]);
+  if (batched) {  // DP and backtrack overlap across the two buckets: reported together
+    elapsed(&ms_dp, c->ev[1], c->ev[3]);
+  } else {
+    elapsed(&ms_dp, c->ev[1], c->ev[2]);
+    elapsed(&ms_bt, c->ev[2], c->ev[3]);
+  }
+  elapsed(&ms_dem, c->ev[3], c->ev[4]);
   memset(stats, 0, sizeof *stats);
   stats->total_cost = J;
   stats->tof = tof;
@@ -521,6 +765,13 @@ la_status la_assign_round(la_ctx* c, const la_round_params* p, la_round_stats* s
   stats->ms_backtrack = ms_bt;
   stats->ms_demand = ms_dem;
   stats->launches = c->launches - launches0;
+  if (batched) {
+    stats->batch_split = c->plan.k;
+    stats->batch_block = c->plan.block;
+    stats->batch_big_nets = c->plan.n_big;
+    stats->batch_tune_ms = c->plan.best_ms;
+    stats->batch_cached = c->plan.cached ? 1 : 0;
+  }
   return LA_OK;
 }
 

@@ -26,6 +26,23 @@ namespace gapla {
 constexpr int kMaxL = LA_MAX_LAYERS;
 constexpr int64_t kPenMax = int64_t(1) << 48;
 
+// Nodes are bucketed by (level, class, size class): class = 3 * is_root +
+// min(sons, 2); size class = ceil(log2(nodes of the node's net)), capped at 15.
+// Inside every (level, class) range the nodes of nets with at most 2^k nodes
+// form a prefix, for every k: the batched form splits small and large nets at
+// any power of two without re-sorting.
+constexpr int kClasses = 6;
+constexpr int kSizeClasses = 16;
+constexpr int kMinBigSc = 5;  // nets of 17+ nodes get per-net level lists
+__host__ __device__ inline int size_class(int64_t m) {
+  int s = 0;
+  while ((int64_t(1) << s) < m && s < kSizeClasses - 1) ++s;
+  return s;
+}
+__host__ __device__ inline int64_t bucket_key(int64_t h, int cls, int sc) {
+  return (h * kClasses + cls) * kSizeClasses + sc;
+}
+
 // Device error word: (index << 8) | code, smallest wins (atomicMin).
 enum DevErr : int {
   DE_NONE = 0,
@@ -89,7 +106,16 @@ struct Forest {
   int64_t N = 0, V = 0;
   int Hmax = 0;                         // max height (levels 0..Hmax)
   std::vector<int64_t> lvl_off;         // host copy: level h is [lvl_off[h], lvl_off[h+1])
-  std::vector<int64_t> cls_off;         // host copy, 4 (Hmax+1) + 1 entries: (level, node class) buckets
+  std::vector<int64_t> key_off;         // host copy: offsets of the (level, class, size class) buckets
+  // Per-net level lists of the nets with size class >= kMinBigSc (input-order
+  // slots of the net: bl_nodes[base + j] is the internal id of its j-th node
+  // by height; bl_hoff[base + n + h] the start of height h, relative to base).
+  int32_t* bl_nodes = nullptr;
+  int32_t* bl_hoff = nullptr;
+  int32_t* net_H = nullptr;             // [N] height of each net
+  int32_t* big_queue = nullptr;         // those nets, size class descending (largest first)
+  std::vector<int64_t> big_sc_cnt;      // host: how many of them per size class
+  int* queue_ctr = nullptr;             // device work-queue counter
   // Device arrays.  Node ids are int32 (V < 2^31).  After la_load_nets every
   // per-node array is in INTERNAL order: nodes sorted by (level, class), so a
   // level's nodes, their table rows and their sons' rows are contiguous
@@ -120,6 +146,8 @@ struct Forest {
   double* Cc = nullptr;
   double* M = nullptr;
   double* B = nullptr;                  // look-ahead base fma(w_d r_est(parent), Cc, A)
+  double* ncache[2] = {nullptr, nullptr};  // batched form, per weight source: [V][4] per-node constants
+  double* scache[2] = {nullptr, nullptr};  // and [V][LD][3] per (node, layer) constants
   int8_t* sb = nullptr;                 // [V][LD] chosen stack bottom
   int8_t* st = nullptr;                 // [V][LD] chosen stack top
   int8_t* ent = nullptr;                // [V][LD] layer of this son per parent candidate
@@ -161,6 +189,25 @@ struct Grid {
   double P_hist_w = -1.0;
 };
 
+// Batched form: small nets (size class <= k) by level waves of class kernels,
+// the rest by the persistent block-per-net kernels on a second stream; chosen
+// by the autotuner, and the round replayed as a CUDA graph.
+struct BatchPlan {
+  bool tuned = false;
+  int k = kSizeClasses - 1;
+  int block = 256, grid = 0;
+  bool cached = true;         // read the constant caches (else recompute in the DP)
+  int64_t n_big = 0;
+  int Hs = 0;                 // highest level with a small-net node
+  double best_ms = 0.0;       // tuning time of the chosen plan
+  int trials = 0;
+  // one graph and one constant cache per weight source (0 Eq. 4, 1 adjoint)
+  cudaGraphExec_t exec[2] = {nullptr, nullptr};
+  double w[2][5] = {{0, 0, 0, 0, 0}, {0, 0, 0, 0, 0}};  // what each graph was captured with
+  long long graph_launches[2] = {0, 0};
+  double cache_wd[2] = {-1.0, -1.0}, cache_wcap[2] = {-1.0, -1.0};
+};
+
 struct Stats {  // device accumulators of one round
   unsigned long long vias, wl, relu;
   unsigned long long wl_layer[kMaxL];
@@ -181,6 +228,10 @@ struct la_ctx {
   cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   int LD = 0;
   long long launches = 0;               // kernels launched (host-side count)
+  cudaStream_t s2 = nullptr;            // second stream (big-net bucket)
+  cudaStream_t s_cap = nullptr;         // stream the batched round is captured on
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  gapla::BatchPlan plan;
   void* alloc_groups = nullptr;         // device allocations, grouped per load
 };
 
@@ -193,14 +244,17 @@ namespace gapla {
 void launch_grid_to_internal(const LayerInfo& li, int X, int Y, const int32_t* pub, int32_t* inter,
                              bool to_internal, unsigned long long* err, cudaStream_t s);
 void launch_forest_prepare(la_ctx* c, Forest& f, const la_net_desc* d, int* d_hmax, cudaStream_t s);
-// Nodes bucketed by (level, class): class = 3 * is_root + min(sons, 2).
-constexpr int kClasses = 6;
 void launch_level_sort(Forest& f, int32_t* lvl_cnt, int64_t* lvl_cursor, cudaStream_t s);
+// in2int[input id] = internal id
+void launch_inverse_perm(int64_t V, const int32_t* int2in, int32_t* in2int, cudaStream_t s);
+// per-net level lists and the big-net queue (input-order forest `in`, internal ids via in2int)
+void launch_net_levels(const Forest& in, const int32_t* in2int, Forest& out, int32_t* sc_cnt, int64_t* sc_cur,
+                       cudaStream_t s);
 void launch_weights_eq4(const LayerInfo& li, Forest& f, cudaStream_t s);
 void launch_check_assignment(la_ctx* c, const int8_t* layer, const int8_t* b, const int8_t* t,
                              cudaStream_t s);
 // input-order forest `in` (after prepare, level sort and weights) -> internal order `out`
-void launch_renumber(const Forest& in, Forest& out, cudaStream_t s);
+void launch_renumber(const Forest& in, const int32_t* in2int, Forest& out, cudaStream_t s);
 // dst[i] = src[perm[i]] (gather into internal order) or dst[perm[i]] = src[i] (scatter)
 void launch_permute8(int64_t V, const int32_t* perm, const int8_t* src, int8_t* dst, bool gather, cudaStream_t s);
 void launch_permute64(int64_t V, const int32_t* perm, const double* src, double* dst, bool gather, cudaStream_t s);
@@ -209,9 +263,20 @@ struct RoundW {
   double w_cong, w_via, w_cap, w_d, hist_w;
 };
 void launch_scan_lines(la_ctx* c, bool from_diff, double hist_w, double* red_tof, cudaStream_t s);
-void launch_dp_level(la_ctx* c, const RoundW& w, const double* W, const double* rho, int level,
-                     cudaStream_t s);
-void launch_backtrack_level(la_ctx* c, int level, cudaStream_t s);
+// kmax: nodes of nets up to size class kmax (kSizeClasses - 1 = every node)
+// cached: read the batched form's constant caches (ncache/scache)
+// cache: the constant-cache set to read (0/1), or -1 to recompute
+void launch_dp_level(la_ctx* c, const RoundW& w, const double* W, const double* rho, int level, int kmax,
+                     int cache, cudaStream_t s);
+// fuse_demand: the batched form's backtrack also does the demand update
+void launch_backtrack_level(la_ctx* c, int level, int kmax, bool fuse_demand, cudaStream_t s);
+// the first n_big nets of the big-net queue, persistent grid
+void launch_dp_bignets(la_ctx* c, const RoundW& w, const double* W, const double* rho, int64_t n_big, int grid,
+                       int block, int cache, cudaStream_t s);
+void launch_backtrack_bignets(la_ctx* c, int64_t n_big, int grid, int block, bool fuse_demand, cudaStream_t s);
+void launch_seg_consts(la_ctx* c, const RoundW& w, const double* W, int cache, cudaStream_t s);
+void launch_node_round(la_ctx* c, const RoundW& w, const double* rho, int cache, cudaStream_t s);
+int bignet_blocks_per_sm(int L, int block);
 void launch_demand(la_ctx* c, cudaStream_t s);
 void launch_sum_roots(la_ctx* c, double* part, double* J_out, cudaStream_t s);
 int scan_blocks(const LayerInfo& li);

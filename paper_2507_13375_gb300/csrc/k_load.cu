@@ -143,28 +143,30 @@ void launch_forest_prepare(la_ctx* c, Forest& f, const la_net_desc* d, int* d_hm
   ++c->launches;
 }
 
-__device__ __forceinline__ int node_bucket(int64_t v, const int32_t* height, const int32_t* nch,
-                                           const int32_t* parent_g) {
-  const int cls = (parent_g[v] < 0 ? 3 : 0) + min(nch[v], 2);
-  return height[v] * kClasses + cls;
+struct BucketIn {
+  const int32_t *height, *nch, *parent_g, *net_of;
+  const int64_t* net_ptr;
+};
+__device__ __forceinline__ long long node_bucket(int64_t v, const BucketIn& b) {
+  const int cls = (b.parent_g[v] < 0 ? 3 : 0) + min(b.nch[v], 2);
+  const int n = b.net_of[v];
+  return bucket_key(b.height[v], cls, size_class(b.net_ptr[n + 1] - b.net_ptr[n]));
 }
 
 // Warp-aggregated counting: lanes with the same bucket add once.
-__global__ void k_level_count(int64_t V, const int32_t* __restrict__ height, const int32_t* __restrict__ nch,
-                              const int32_t* __restrict__ parent_g, int32_t* __restrict__ cnt) {
+__global__ void k_level_count(int64_t V, BucketIn b, int32_t* __restrict__ cnt) {
   const int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   const bool act = v < V;
-  const int key = act ? node_bucket(v, height, nch, parent_g) : -1;
+  const long long key = act ? node_bucket(v, b) : -1;
   const unsigned peers = __match_any_sync(0xffffffffu, key);
   const int lane = threadIdx.x & 31;
   if (act && lane == __ffs(peers) - 1) atomicAdd(&cnt[key], __popc(peers));
 }
-__global__ void k_level_place(int64_t V, const int32_t* __restrict__ height, const int32_t* __restrict__ nch,
-                              const int32_t* __restrict__ parent_g, unsigned long long* __restrict__ cursor,
+__global__ void k_level_place(int64_t V, BucketIn b, unsigned long long* __restrict__ cursor,
                               int32_t* __restrict__ out) {
   const int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   const bool act = v < V;
-  const int key = act ? node_bucket(v, height, nch, parent_g) : -1;
+  const long long key = act ? node_bucket(v, b) : -1;
   const unsigned peers = __match_any_sync(0xffffffffu, key);
   const int lane = threadIdx.x & 31;
   const int leader = __ffs(peers) - 1;
@@ -174,16 +176,15 @@ __global__ void k_level_place(int64_t V, const int32_t* __restrict__ height, con
   if (act) out[base + __popc(peers & ((1u << lane) - 1u))] = int32_t(v);
 }
 
-// lvl_cnt: kClasses (Hmax+1) zeroed ints; lvl_cursor: as many int64 holding
+// lvl_cnt: one zeroed int per bucket key; lvl_cursor: as many int64 holding
 // the bucket offsets on entry.  Within a bucket the order is whatever the
 // atomics give: nodes of one level never read each other's results.
 void launch_level_sort(Forest& f, int32_t* lvl_cnt, int64_t* lvl_cursor, cudaStream_t s) {
   const int T = 256;
   const unsigned B = (unsigned)((f.V + T - 1) / T);
-  if (lvl_cnt) k_level_count<<<B, T, 0, s>>>(f.V, f.height, f.nch, f.parent_g, lvl_cnt);
-  if (lvl_cursor)
-    k_level_place<<<B, T, 0, s>>>(f.V, f.height, f.nch, f.parent_g,
-                                  reinterpret_cast<unsigned long long*>(lvl_cursor), f.lvl_nodes);
+  BucketIn b{f.height, f.nch, f.parent_g, f.net_of, f.net_ptr};
+  if (lvl_cnt) k_level_count<<<B, T, 0, s>>>(f.V, b, lvl_cnt);
+  if (lvl_cursor) k_level_place<<<B, T, 0, s>>>(f.V, b, reinterpret_cast<unsigned long long*>(lvl_cursor), f.lvl_nodes);
 }
 
 // Eq. 4 edge weights (max sink criticality below) and the distance-based
@@ -284,12 +285,13 @@ __global__ void k_renumber(RenumArgs a) {
   for (int k = 0; k < nc; ++k) a.child_list[cs + k] = a.in2int[a.child_list_in[cs + k]];
 }
 
-void launch_renumber(const Forest& in, Forest& out, cudaStream_t s) {
+void launch_inverse_perm(int64_t V, const int32_t* int2in, int32_t* in2int, cudaStream_t s) {
+  k_inverse_perm<<<(unsigned)((V + 255) / 256), 256, 0, s>>>(V, int2in, in2int);
+}
+
+void launch_renumber(const Forest& in, const int32_t* in2int, Forest& out, cudaStream_t s) {
   const int T = 256;
   const unsigned B = (unsigned)((in.V + T - 1) / T);
-  // the parent's height array is free now: reuse it for input -> internal ids
-  int32_t* in2int = in.height;
-  k_inverse_perm<<<B, T, 0, s>>>(in.V, out.lvl_nodes, in2int);
   RenumArgs a;
   a.V = in.V; a.int2in = out.lvl_nodes; a.in2int = in2int;
   a.parent_in = in.parent_g; a.net_of_in = in.net_of; a.child_start_in = in.child_start; a.nch_in = in.nch;
@@ -299,6 +301,51 @@ void launch_renumber(const Forest& in, Forest& out, cudaStream_t s) {
   a.child_list = out.child_list; a.root_of_net = out.root_of_net; a.pin = out.pin; a.cap = out.sink_cap;
   a.kap = out.kappa; a.gk = out.gk; a.W = out.W_eq4; a.rho = out.rho_eq4; a.geo = out.geo;
   k_renumber<<<B, T, 0, s>>>(a);
+}
+
+// One thread per net of size class >= kMinBigSc: a stable counting sort of
+// its nodes by height (internal ids), and the net's height.
+__global__ void k_net_levels(int64_t N, const int64_t* __restrict__ net_ptr, const int32_t* __restrict__ height,
+                             const int32_t* __restrict__ in2int, int32_t* __restrict__ nodes,
+                             int32_t* __restrict__ hoff, int32_t* __restrict__ net_H, int32_t* __restrict__ sc_cnt) {
+  const int64_t n = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const int64_t base = net_ptr[n], m = net_ptr[n + 1] - base;
+  const int H = height[base];
+  net_H[n] = H;
+  const int sc = size_class(m);
+  if (sc < kMinBigSc) return;
+  atomicAdd(&sc_cnt[sc], 1);
+  int32_t* ho = hoff + base + n;  // H + 2 <= m + 1 slots
+  for (int h = 0; h <= H + 1; ++h) ho[h] = 0;
+  for (int64_t i = 0; i < m; ++i) ho[height[base + i] + 1] += 1;
+  for (int h = 0; h <= H; ++h) ho[h + 1] += ho[h];
+  // place (ho[h] advances to the end of height h; shift back afterwards)
+  for (int64_t i = 0; i < m; ++i) {
+    const int h = height[base + i];
+    nodes[base + ho[h]] = in2int[base + i];
+    ho[h] += 1;
+  }
+  for (int h = H; h >= 1; --h) ho[h] = ho[h - 1];
+  ho[0] = 0;
+}
+
+__global__ void k_big_queue(int64_t N, const int64_t* __restrict__ net_ptr, unsigned long long* __restrict__ cursor,
+                            int32_t* __restrict__ queue) {
+  const int64_t n = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const int sc = size_class(net_ptr[n + 1] - net_ptr[n]);
+  if (sc < kMinBigSc) return;
+  queue[atomicAdd(&cursor[sc], 1ull)] = int32_t(n);
+}
+
+void launch_net_levels(const Forest& in, const int32_t* in2int, Forest& out, int32_t* sc_cnt, int64_t* sc_cur,
+                       cudaStream_t s) {
+  const unsigned B = (unsigned)((in.N + 127) / 128);
+  if (sc_cnt) k_net_levels<<<B, 128, 0, s>>>(in.N, in.net_ptr, in.height, in2int, out.bl_nodes, out.bl_hoff,
+                                             out.net_H, sc_cnt);
+  if (sc_cur) k_big_queue<<<B, 128, 0, s>>>(in.N, in.net_ptr, reinterpret_cast<unsigned long long*>(sc_cur),
+                                            out.big_queue);
 }
 
 template <typename T>

@@ -165,6 +165,10 @@ struct DPArgs {
   int8_t *sb, *st, *ent;
   double w_cong_s, w_cap, w_d, sigma0;
   unsigned long long* err;
+  // batched form only (else null): per node {w_d W, w_d kappa, w_d r_est, sigma}
+  // and per (node, layer) {alpha = w_d W R, gamma = fma(alpha, C/2, w_cap C), C}
+  const double* ncache;
+  const double* scache;
 };
 
 // (fp, k, b) lexicographic order of Kernel 2 (least f', fewest vias, lowest b).
@@ -172,16 +176,11 @@ __device__ __forceinline__ bool stack_better(long long f, int k, int b, long lon
   return f < bf || (f == bf && (k < bk || (k == bk && b < bb)));
 }
 
-template <int LMAX, int DEG, bool ROOT>
-__global__ void __launch_bounds__(256) k_dp_level(LayerInfo li, DPArgs a) {
-  __shared__ DevTables s;
-  load_tables(s, a.tab);
-  const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  const int64_t node_i = ROOT ? k : k / a.LD;
-  const int ldi = ROOT ? 0 : int(k - node_i * a.LD);
-  if (node_i >= a.count) return;
-  const int v = int(a.base + node_i);
-  const int L = li.L, LD = a.LD;
+// The work of one thread: node v, candidate index ldi (0 at a root).
+// CACHED: read the batched form's constant caches instead of recomputing.
+template <int LMAX, int DEG, bool ROOT, bool CACHED>
+__device__ __forceinline__ void dp_node(const DPArgs& a, const DevTables& s, int L, int v, int ldi) {
+  const int LD = a.LD;
   const int pin = a.pin[v];
   const uint64_t gv = a.geo[v];
   const int d = geo_dir(gv);
@@ -193,12 +192,13 @@ __global__ void __launch_bounds__(256) k_dp_level(LayerInfo li, DPArgs a) {
     l = s.lay[d][ldi];
   }
   const double* rvl = &s.rv[l * kMaxL];
-  const double wd_rho = a.w_d * a.rho[v];
-  const double sigma_v = fma(wd_rho, s.via_c, a.sigma0);
+  const double* nc = CACHED ? a.ncache + 4 * int64_t(v) : nullptr;
+  const double wd_rho = CACHED ? nc[2] : a.w_d * a.rho[v];
+  const double sigma_v = CACHED ? nc[3] : fma(wd_rho, s.via_c, a.sigma0);
   double Cs = 0.0, sinkf = 0.0, z = 0.0;  // a node without a pin: all exactly 0
   if (pin >= 0) {
     Cs = a.sink_cap[v];
-    sinkf = ((a.w_d * a.kappa[v]) * rvl[pin]) * Cs;
+    sinkf = ((CACHED ? nc[1] : a.w_d * a.kappa[v]) * rvl[pin]) * Cs;
     z = fma(wd_rho, Cs, sinkf);
   }
   const int lo_req = pin >= 0 ? min(l, pin) : l;
@@ -329,12 +329,21 @@ __global__ void __launch_bounds__(256) k_dp_level(LayerInfo li, DPArgs a) {
     a.Jroot[v] = __longlong_as_double(bfp);
   } else {
     const int len = geo_len(gv), line = geo_line(gv), lo = geo_lo(gv);
-    const double R = double(len) * s.unit_r[l];
-    const double C = double(len) * s.unit_c[l];
-    const double Ch = double(len) * s.half_c[l];
-    const double wdW = a.w_d * a.W[v];
-    const double alpha = wdW * R;
-    const double gamma = fma(alpha, Ch, a.w_cap * C);
+    double C, wdW, alpha, gamma;
+    if constexpr (CACHED) {
+      const double* sc3 = a.scache + 3 * o;
+      alpha = sc3[0];
+      gamma = sc3[1];
+      C = sc3[2];
+      wdW = nc[0];
+    } else {
+      const double R = double(len) * s.unit_r[l];
+      C = double(len) * s.unit_c[l];
+      const double Ch = double(len) * s.half_c[l];
+      wdW = a.w_d * a.W[v];
+      alpha = wdW * R;
+      gamma = fma(alpha, Ch, a.w_cap * C);
+    }
     const int nldd = s.nld[d];
     const int64_t pb = s.grid_off[d] + int64_t(line) * s.npos[d] * nldd + ldi;
     const int64_t K = a.P[pb + int64_t(lo + len) * nldd] - a.P[pb + int64_t(lo) * nldd];
@@ -344,7 +353,161 @@ __global__ void __launch_bounds__(256) k_dp_level(LayerInfo li, DPArgs a) {
     a.A[o] = Av;
     a.Cc[o] = ccv;
     a.M[o] = wdW * ccv;
-    a.B[o] = fma(a.w_d * a.rho[a.parent_g[v]], ccv, Av);
+    const int p = a.parent_g[v];
+    a.B[o] = fma(CACHED ? a.ncache[4 * int64_t(p) + 2] : a.w_d * a.rho[p], ccv, Av);
+  }
+}
+
+template <int LMAX, int DEG, bool ROOT, bool CACHED>
+__global__ void __launch_bounds__(256) k_dp_level(LayerInfo li, DPArgs a) {
+  __shared__ DevTables s;
+  load_tables(s, a.tab);
+  const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t node_i = ROOT ? k : k / a.LD;
+  const int ldi = ROOT ? 0 : int(k - node_i * a.LD);
+  if (node_i >= a.count) return;
+  dp_node<LMAX, DEG, ROOT, CACHED>(a, s, li.L, int(a.base + node_i), ldi);
+}
+
+// Any node: pick its class at run time (used where classes mix).
+template <int LMAX, bool CACHED>
+__device__ void dp_node_any(const DPArgs& a, const DevTables& s, int L, int v, int ldi) {
+  const int nc = a.nch[v];
+  if (a.parent_g[v] < 0) {
+    if (ldi != 0) return;
+    if (nc == 0) dp_node<LMAX, 0, true, CACHED>(a, s, L, v, 0);
+    else if (nc == 1) dp_node<LMAX, 1, true, CACHED>(a, s, L, v, 0);
+    else dp_node<LMAX, 2, true, CACHED>(a, s, L, v, 0);
+  } else {
+    if (nc == 0) dp_node<LMAX, 0, false, CACHED>(a, s, L, v, ldi);
+    else if (nc == 1) dp_node<LMAX, 1, false, CACHED>(a, s, L, v, ldi);
+    else dp_node<LMAX, 2, false, CACHED>(a, s, L, v, ldi);
+  }
+}
+
+__device__ __forceinline__ void backtrack_node(int v, int LD, const int8_t* ld_of, const int32_t* parent_g,
+                                               const int8_t* pin, const int8_t* ent, const int8_t* sb,
+                                               const int8_t* st, int8_t* layer, int8_t* b, int8_t* t) {
+  const int gp = parent_g[v];
+  int l, idx;
+  if (gp < 0) {
+    l = pin[v];
+    idx = 0;
+  } else {
+    const int lp = layer[gp];
+    const int pidx = parent_g[gp] < 0 ? 0 : ld_of[lp];
+    l = ent[int64_t(v) * LD + pidx];
+    idx = ld_of[l];
+  }
+  layer[v] = int8_t(l);
+  b[v] = sb[int64_t(v) * LD + idx];
+  t[v] = st[int64_t(v) * LD + idx];
+}
+
+// Large nets (batched form): a persistent grid takes nets from a work queue
+// (largest first); a block walks its net's levels, the (node, layer) tasks of
+// a level spread over its threads, __syncthreads between levels.  No wait
+// crosses blocks.
+struct BigArgs {
+  const int32_t* queue;
+  int64_t n_big;
+  const int64_t* net_ptr;
+  const int32_t *bl_nodes, *bl_hoff, *net_H;
+  int* ctr;
+};
+
+template <int LMAX, bool CACHED>
+__global__ void __launch_bounds__(256) k_dp_bignets(LayerInfo li, DPArgs a, BigArgs g) {
+  __shared__ DevTables s;
+  __shared__ int s_q;
+  load_tables(s, a.tab);
+  const int LD = a.LD;
+  for (;;) {
+    if (threadIdx.x == 0) s_q = atomicAdd(g.ctr, 1);
+    __syncthreads();
+    const int q = s_q;
+    __syncthreads();
+    if (q >= g.n_big) return;
+    const int n = g.queue[q];
+    const int64_t base = g.net_ptr[n];
+    const int32_t* ho = g.bl_hoff + base + n;
+    const int H = g.net_H[n];
+    for (int h = 0; h <= H; ++h) {
+      const int lo = ho[h], cnt = ho[h + 1] - lo;
+      for (int t = threadIdx.x; t < cnt * LD; t += blockDim.x)
+        dp_node_any<LMAX, CACHED>(a, s, li.L, g.bl_nodes[base + lo + t / LD], t % LD);
+      __syncthreads();
+    }
+  }
+}
+
+struct BtArgs {
+  int LD;
+  const DevTables* tab;
+  const int32_t* parent_g;
+  const int8_t *pin, *ent, *sb, *st;
+  int8_t *layer, *b, *t;
+  // batched form: the demand update fused in (null: separate k_demand)
+  int32_t* diff;
+  const uint64_t* geo;
+  Stats* stats;
+};
+
+// Demand of node v's segment on its new layer (+1 at the first edge, -1 past
+// the last, in the difference array of its line); returns the segment length.
+__device__ __forceinline__ int demand_node(const BtArgs& a, int v, int l) {
+  if (a.parent_g[v] < 0) return 0;
+  const uint64_t g = a.geo[v];
+  const int d = geo_dir(g), len = geo_len(g);
+  const int nld = a.tab->nld[d];
+  const int64_t base = a.tab->grid_off[d] + (int64_t(geo_line(g)) * a.tab->npos[d] + geo_lo(g)) * nld + a.tab->ld_of[l];
+  atomicAdd(a.diff + base, 1);
+  atomicAdd(a.diff + base + int64_t(len) * nld, -1);
+  return len;
+}
+
+__global__ void __launch_bounds__(256) k_backtrack_bignets(BtArgs a, BigArgs g) {
+  __shared__ int s_q;
+  __shared__ int8_t s_ld[kMaxL];
+  __shared__ unsigned long long s_wl[kMaxL], s_vias;
+  if (threadIdx.x < kMaxL) {
+    s_ld[threadIdx.x] = a.tab->ld_of[threadIdx.x];
+    s_wl[threadIdx.x] = 0;
+  }
+  if (threadIdx.x == 0) s_vias = 0;
+  unsigned my_vias = 0;
+  for (;;) {
+    if (threadIdx.x == 0) s_q = atomicAdd(g.ctr, 1);
+    __syncthreads();
+    const int q = s_q;
+    __syncthreads();
+    if (q >= g.n_big) break;
+    const int n = g.queue[q];
+    const int64_t base = g.net_ptr[n];
+    const int32_t* ho = g.bl_hoff + base + n;
+    for (int h = g.net_H[n]; h >= 0; --h) {
+      const int lo = ho[h], cnt = ho[h + 1] - lo;
+      for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+        const int v = g.bl_nodes[base + lo + t];
+        backtrack_node(v, a.LD, s_ld, a.parent_g, a.pin, a.ent, a.sb, a.st, a.layer, a.b, a.t);
+        if (a.diff) {
+          const int l = a.layer[v];
+          const int len = demand_node(a, v, l);
+          if (len) atomicAdd(&s_wl[l], (unsigned long long)len);
+          my_vias += unsigned(a.t[v] - a.b[v]);
+        }
+      }
+      __syncthreads();
+    }
+  }
+  if (a.diff) {
+    if (my_vias) atomicAdd(&s_vias, (unsigned long long)my_vias);
+    __syncthreads();
+    if (threadIdx.x < kMaxL && s_wl[threadIdx.x]) {
+      atomicAdd(&a.stats->wl_layer[threadIdx.x], s_wl[threadIdx.x]);
+      atomicAdd(&a.stats->wl, s_wl[threadIdx.x]);
+    }
+    if (threadIdx.x == 0 && s_vias) atomicAdd(&a.stats->vias, s_vias);
   }
 }
 
@@ -352,7 +515,9 @@ template <int LMAX, int DEG, bool ROOT>
 static void dp_launch(la_ctx* c, const DPArgs& a, cudaStream_t s) {
   const int T = 256;
   const int64_t threads = ROOT ? a.count : a.count * a.LD;
-  k_dp_level<LMAX, DEG, ROOT><<<(unsigned)((threads + T - 1) / T), T, 0, s>>>(c->grid.li, a);
+  const unsigned B = (unsigned)((threads + T - 1) / T);
+  if (a.scache) k_dp_level<LMAX, DEG, ROOT, true><<<B, T, 0, s>>>(c->grid.li, a);
+  else k_dp_level<LMAX, DEG, ROOT, false><<<B, T, 0, s>>>(c->grid.li, a);
   ++c->launches;
 }
 
@@ -368,7 +533,7 @@ static void dp_launch_class(la_ctx* c, const DPArgs& a, int cls, cudaStream_t s)
   }
 }
 
-void launch_dp_level(la_ctx* c, const RoundW& w, const double* W, const double* rho, int level, cudaStream_t s) {
+static DPArgs dp_args(la_ctx* c, const RoundW& w, const double* W, const double* rho) {
   Forest& f = c->forest;
   DPArgs a;
   a.LD = c->LD;
@@ -381,12 +546,28 @@ void launch_dp_level(la_ctx* c, const RoundW& w, const double* W, const double* 
   a.w_d = w.w_d;
   a.sigma0 = w.w_via + w.w_cap * c->grid.li.via_c;
   a.err = c->d_err;
+  a.base = 0;
+  a.count = 0;
+  a.ncache = nullptr;
+  a.scache = nullptr;
+  return a;
+}
+
+void launch_dp_level(la_ctx* c, const RoundW& w, const double* W, const double* rho, int level, int kmax,
+                     int cache, cudaStream_t s) {
+  Forest& f = c->forest;
+  DPArgs a = dp_args(c, w, W, rho);
+  if (cache >= 0) {
+    a.ncache = f.ncache[cache];
+    a.scache = f.scache[cache];
+  }
   const int L = c->grid.li.L;
   for (int cls = 0; cls < kClasses; ++cls) {
-    const size_t bk = size_t(level) * kClasses + cls;
-    const int64_t n = f.cls_off[bk + 1] - f.cls_off[bk];
+    const int64_t lo = f.key_off[size_t(bucket_key(level, cls, 0))];
+    const int64_t hi = f.key_off[size_t(bucket_key(level, cls, kmax + 1))];
+    const int64_t n = hi - lo;
     if (n == 0) continue;
-    a.base = f.cls_off[bk];
+    a.base = lo;
     a.count = n;
     if (L <= 6) dp_launch_class<6>(c, a, cls, s);
     else if (L <= 12) dp_launch_class<12>(c, a, cls, s);
@@ -397,39 +578,171 @@ void launch_dp_level(la_ctx* c, const RoundW& w, const double* W, const double* 
 // ---------------------------------------------------------------------------
 // Backtrack (Alg. 4): top-down, one thread per node of the level.
 // ---------------------------------------------------------------------------
-__global__ void k_backtrack_level(int64_t base, int64_t count, int LD,
-                                  const DevTables* __restrict__ tab, const int32_t* __restrict__ parent_g,
-                                  const int8_t* __restrict__ pin, const int8_t* __restrict__ ent,
-                                  const int8_t* __restrict__ sb, const int8_t* __restrict__ st,
-                                  int8_t* __restrict__ layer, int8_t* __restrict__ b, int8_t* __restrict__ t) {
-  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= count) return;
-  const int v = int(base + i);
-  const int gp = parent_g[v];
-  int l, idx;
-  if (gp < 0) {
-    l = pin[v];
-    idx = 0;
-  } else {
-    const int lp = layer[gp];
-    const int pidx = parent_g[gp] < 0 ? 0 : tab->ld_of[lp];
-    l = ent[int64_t(v) * LD + pidx];
-    idx = tab->ld_of[l];
+// Up to kClasses node ranges of one level (the small-net prefixes of its
+// class buckets), one thread per node.
+struct Ranges {
+  int64_t lo[kClasses], cnt[kClasses];
+  int64_t total;
+};
+
+__global__ void __launch_bounds__(256) k_backtrack_level(Ranges r, BtArgs a) {
+  __shared__ int8_t s_ld[kMaxL];
+  __shared__ unsigned long long s_wl[kMaxL], s_vias;
+  if (threadIdx.x < kMaxL) {
+    s_ld[threadIdx.x] = a.tab->ld_of[threadIdx.x];
+    s_wl[threadIdx.x] = 0;
   }
-  layer[v] = int8_t(l);
-  b[v] = sb[int64_t(v) * LD + idx];
-  t[v] = st[int64_t(v) * LD + idx];
+  if (threadIdx.x == 0) s_vias = 0;
+  __syncthreads();
+  int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  unsigned vias = 0, len = 0;
+  int l = -1;
+  if (j < r.total) {
+    int k = 0;
+    while (k < kClasses - 1 && j >= r.cnt[k]) j -= r.cnt[k++];
+    const int v = int(r.lo[k] + j);
+    backtrack_node(v, a.LD, s_ld, a.parent_g, a.pin, a.ent, a.sb, a.st, a.layer, a.b, a.t);
+    if (a.diff) {
+      l = a.layer[v];
+      len = unsigned(demand_node(a, v, l));
+      vias = unsigned(a.t[v] - a.b[v]);
+      if (len == 0) l = -1;
+    }
+  }
+  if (a.diff) {
+    // warp-level sums first: one shared atomic per warp (vias) and per layer
+    const unsigned wv = __reduce_add_sync(0xffffffffu, vias);
+    if ((threadIdx.x & 31) == 0 && wv) atomicAdd(&s_vias, (unsigned long long)wv);
+    const unsigned peers = __match_any_sync(0xffffffffu, l);
+    const unsigned wl = __reduce_add_sync(peers, len);
+    if (l >= 0 && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&s_wl[l], (unsigned long long)wl);
+    __syncthreads();
+    if (threadIdx.x < kMaxL && s_wl[threadIdx.x]) {
+      atomicAdd(&a.stats->wl_layer[threadIdx.x], s_wl[threadIdx.x]);
+      atomicAdd(&a.stats->wl, s_wl[threadIdx.x]);
+    }
+    if (threadIdx.x == 0 && s_vias) atomicAdd(&a.stats->vias, s_vias);
+  }
 }
 
-void launch_backtrack_level(la_ctx* c, int level, cudaStream_t s) {
+static BtArgs bt_args(la_ctx* c, bool fuse_demand) {
   Forest& f = c->forest;
-  const int64_t n = f.lvl_off[level + 1] - f.lvl_off[level];
-  if (n == 0) return;
-  const int T = 256;
-  k_backtrack_level<<<(unsigned)((n + T - 1) / T), T, 0, s>>>(f.lvl_off[level], n, c->LD,
-                                                            c->grid.tab_dev, f.parent_g, f.pin, f.ent, f.sb,
-                                                            f.st, f.layer, f.b, f.t);
+  return BtArgs{c->LD,  c->grid.tab_dev, f.parent_g, f.pin, f.ent, f.sb, f.st, f.layer, f.b, f.t,
+                fuse_demand ? c->grid.diff : nullptr, f.geo, c->d_stats};
+}
+
+void launch_backtrack_level(la_ctx* c, int level, int kmax, bool fuse_demand, cudaStream_t s) {
+  Forest& f = c->forest;
+  Ranges r{};
+  for (int cls = 0; cls < kClasses; ++cls) {
+    r.lo[cls] = f.key_off[size_t(bucket_key(level, cls, 0))];
+    r.cnt[cls] = f.key_off[size_t(bucket_key(level, cls, kmax + 1))] - r.lo[cls];
+    r.total += r.cnt[cls];
+  }
+  if (r.total == 0) return;
+  k_backtrack_level<<<(unsigned)((r.total + 255) / 256), 256, 0, s>>>(r, bt_args(c, fuse_demand));
   ++c->launches;
+}
+
+static BigArgs big_args(la_ctx* c, int64_t n_big, int slot) {
+  Forest& f = c->forest;
+  return BigArgs{f.big_queue, n_big, f.net_ptr, f.bl_nodes, f.bl_hoff, f.net_H, f.queue_ctr + slot};
+}
+
+void launch_backtrack_bignets(la_ctx* c, int64_t n_big, int grid, int block, bool fuse_demand, cudaStream_t s) {
+  if (n_big == 0) return;
+  k_backtrack_bignets<<<grid, block, 0, s>>>(bt_args(c, fuse_demand), big_args(c, n_big, 1));
+  ++c->launches;
+}
+
+void launch_dp_bignets(la_ctx* c, const RoundW& w, const double* W, const double* rho, int64_t n_big, int grid,
+                       int block, int cache, cudaStream_t s) {
+  if (n_big == 0) return;
+  DPArgs a = dp_args(c, w, W, rho);
+  const bool cached = cache >= 0;
+  if (cached) {
+    a.ncache = c->forest.ncache[cache];
+    a.scache = c->forest.scache[cache];
+  }
+  const int L = c->grid.li.L;
+  BigArgs g = big_args(c, n_big, 0);
+  if (cached) {
+    if (L <= 6) k_dp_bignets<6, true><<<grid, block, 0, s>>>(c->grid.li, a, g);
+    else if (L <= 12) k_dp_bignets<12, true><<<grid, block, 0, s>>>(c->grid.li, a, g);
+    else k_dp_bignets<16, true><<<grid, block, 0, s>>>(c->grid.li, a, g);
+  } else {
+    if (L <= 6) k_dp_bignets<6, false><<<grid, block, 0, s>>>(c->grid.li, a, g);
+    else if (L <= 12) k_dp_bignets<12, false><<<grid, block, 0, s>>>(c->grid.li, a, g);
+    else k_dp_bignets<16, false><<<grid, block, 0, s>>>(c->grid.li, a, g);
+  }
+  ++c->launches;
+}
+
+// Batched form: values that do not change between rounds of one weight set,
+// computed once (the same expressions the DP evaluates otherwise).  W of the
+// adjoint mode is the criticality below each node, which depends only on the
+// forest, so it is the same after every la_reweight_adjoint.
+__global__ void k_seg_consts(int64_t V, int LD, const DevTables* __restrict__ tab, const uint64_t* __restrict__ geo,
+                             const int32_t* __restrict__ parent_g, const int8_t* __restrict__ pin,
+                             const double* __restrict__ W, const double* __restrict__ kappa, double w_d, double w_cap,
+                             double* __restrict__ ncache, double* __restrict__ scache) {
+  const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t v = k / LD;
+  const int ldi = int(k - v * LD);
+  if (v >= V) return;
+  const double wdW = w_d * W[v];
+  if (ldi == 0) {
+    ncache[4 * v] = wdW;
+    ncache[4 * v + 1] = pin[v] >= 0 ? w_d * kappa[v] : 0.0;
+  }
+  const uint64_t g = geo[v];
+  const int d = geo_dir(g);
+  if (parent_g[v] < 0 || ldi >= tab->nld[d]) return;
+  const int l = tab->lay[d][ldi];
+  const double len = double(geo_len(g));
+  const double R = len * tab->unit_r[l];
+  const double C = len * tab->unit_c[l];
+  const double Ch = len * tab->half_c[l];
+  const double alpha = wdW * R;
+  double* o = scache + 3 * (v * LD + ldi);
+  o[0] = alpha;
+  o[1] = fma(alpha, Ch, w_cap * C);
+  o[2] = C;
+}
+
+// Batched form, every round: w_d r_est and sigma = fma(w_d r_est, vc, w_via + w_cap vc) per node.
+__global__ void k_node_round(int64_t V, const double* __restrict__ rho, double w_d, double via_c, double sigma0,
+                             double* __restrict__ ncache) {
+  const int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (v >= V) return;
+  const double wd_rho = w_d * rho[v];
+  ncache[4 * v + 2] = wd_rho;
+  ncache[4 * v + 3] = fma(wd_rho, via_c, sigma0);
+}
+
+void launch_seg_consts(la_ctx* c, const RoundW& w, const double* W, int cache, cudaStream_t s) {
+  Forest& f = c->forest;
+  const int64_t threads = f.V * c->LD;
+  k_seg_consts<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(f.V, c->LD, c->grid.tab_dev, f.geo, f.parent_g, f.pin,
+                                                                W, f.kappa, w.w_d, w.w_cap, f.ncache[cache],
+                                                                f.scache[cache]);
+  ++c->launches;
+}
+
+void launch_node_round(la_ctx* c, const RoundW& w, const double* rho, int cache, cudaStream_t s) {
+  Forest& f = c->forest;
+  k_node_round<<<(unsigned)((f.V + 255) / 256), 256, 0, s>>>(f.V, rho, w.w_d, c->grid.li.via_c,
+                                                             w.w_via + w.w_cap * c->grid.li.via_c, f.ncache[cache]);
+  ++c->launches;
+}
+
+// Resident blocks per SM of the big-net kernels (for a persistent grid).
+int bignet_blocks_per_sm(int L, int block) {
+  int n = 0;
+  if (L <= 6) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_dp_bignets<6, true>, block, 0);
+  else if (L <= 12) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_dp_bignets<12, true>, block, 0);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_dp_bignets<16, true>, block, 0);
+  return n > 0 ? n : 1;
 }
 
 // ---------------------------------------------------------------------------
