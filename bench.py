@@ -89,6 +89,43 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def dp_algorithmic_flops(forest, dirs):
+    """FP64 flops of one DP pass (Alg. 3) counted from the oracle's expressions,
+    each distinct value evaluated once (FMA = 2 flops), for the winning stack
+    plus every son-layer key:
+      per (node, candidate layer): fv, cv (2 FMA); with sons one add each per
+        son; a pin's sink term (2 MUL + 1 FMA); per son one key FMA per legal
+        son layer and the winner's g (1 FMA); the winner's f' (sons - 1 adds +
+        1 FMA + 1 add); a non-root entry A, Cc, M, B (3 FMA, 2 ADD, 1 MUL);
+      per node: w_d r_est (MUL), sigma (FMA), w_d kappa at pins (MUL), w_d W
+        at non-roots (MUL).
+    Round-invariant constants (len r, len c, alpha, gamma) are not counted."""
+    import numpy as np
+
+    par, ptr = forest["parent"], forest["net_ptr"]
+    V, N = int(forest["num_nodes"]), int(forest["num_nets"])
+    net_of = np.repeat(np.arange(N), np.diff(ptr))
+    root = par < 0
+    gp = np.where(root, -1, ptr[net_of] + par)
+    # direction of each segment (0 H, 1 V) and the layer count of it
+    x, y = forest["x"], forest["y"]
+    d = np.zeros(V, np.int8)
+    nr = ~root
+    d[nr] = (y[nr] != y[gp[nr]]).astype(np.int8)
+    nld = np.array([sum(1 for q in dirs if q == 0), sum(1 for q in dirs if q == 1)])
+    LDv = np.where(root, 1, nld[d])
+    deg = np.bincount(gp[nr], minlength=V)
+    son_layers = np.bincount(gp[nr], weights=nld[d[nr]], minlength=V)
+    pin = forest["pin_layer"] >= 0
+    per_layer = (4 + 2 * (deg >= 1) + 2 * np.maximum(deg - 1, 0)  # fv, cv and their son sums
+                 + 4 * pin                                       # sink term
+                 + 2 * son_layers + 2 * deg                      # keys and winners' g
+                 + np.where(deg >= 1, deg + 2, 2)                # the winner's f'
+                 + 9 * nr)                                       # A, Cc, M, B
+    per_node = 3 + pin + nr
+    return float(np.sum(LDv * per_layer + per_node))
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -225,21 +262,45 @@ def bench_gpu(args):
         e2e_ms = float(tt.item())
 
     # ---- roofline of the dominant kernel (the DP) ----
-    peak, peak_src = measured_peaks()
+    # GB300 issues FP64 at 2 FMA/clk/SM: 152 SMs x 2 x 2070 MHz x 2 flops
+    fp64_peak_tflops = 152 * 2 * 2070e6 * 2 / 1e12
+    flops = dp_algorithmic_flops(forest, wl.dirs)
+    achieved = flops / (dp_ms * 1e-3) / 1e12
+    hbm_peak, peak_src = measured_peaks()
     LD = max(sum(1 for d in wl.dirs if d == 0), sum(1 for d in wl.dirs if d == 1))
-    nch = S  # every non-root node is some node's son
-    # algorithmic bytes of one DP pass (all levels): per node its own segment
-    # (geometry 8 B, W and r_est 16 B, pin/caps 17 B, CSR 8 B), per candidate
-    # layer the two congestion prefixes (16 B) and its table entry written
-    # (A, Cc, M: 24 B; stack 2 B), per son and son layer its table read
-    # (A, Cc, M: 24 B) and its entry byte written.
-    dp_bytes = V * (8 + 16 + 17 + 8) + S * LD * (16 + 24 + 2) + N * (24 + 2) + nch * LD * (24 + 1)
-    achieved = dp_bytes / (dp_ms * 1e-3) / 1e9
-    roofline = {"kernel": "k_dp_level (all levels of one round)", "bound": "hbm", "achieved": round(achieved, 1),
-                "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
-                "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)" if peak_src == "measured" else
-                "fallback 6.8 TB/s", "algorithmic_bytes_per_launch_set": int(dp_bytes),
-                "dp_ms_per_round": round(dp_ms, 4)}
+    # algorithmic bytes of one DP pass: per node its own data (geometry 8 B, W
+    # and r_est 16 B, pin/caps 17 B, CSR 8 B); per candidate layer the two
+    # congestion prefixes (16 B) and its entry (A, Cc, M, B 32 B, stack 2 B);
+    # per son and son layer its entry read (M, B 16 B) and its choice byte.
+    dp_bytes = V * (8 + 16 + 17 + 8) + S * LD * (16 + 32 + 2) + N * 2 + S * LD * (16 + 1)
+    hbm_achieved = dp_bytes / (dp_ms * 1e-3) / 1e9
+    roofline = {"kernel": "k_dp_level / k_dp_bignets (all levels of one round; in the batched form the phase "
+                          "also holds the backtrack and the fused demand update)",
+                "bound": "alu", "achieved": round(achieved, 4), "peak": round(fp64_peak_tflops, 4),
+                "unit": "TFLOP/s", "frac": round(achieved / fp64_peak_tflops, 4), "traffic": None,
+                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk/SM x 2070 MHz x 2 flops (FP64 pipe)",
+                "algorithmic_flops_per_round": flops, "dp_ms_per_round": round(dp_ms, 4),
+                "hbm": {"achieved": round(hbm_achieved, 1), "peak": hbm_peak, "unit": "GB/s",
+                        "frac": round(hbm_achieved / hbm_peak, 4), "algorithmic_bytes_per_round": int(dp_bytes),
+                        "peak_source": f"{peak_src} hbm_gbs"}}
+
+    # ---- the plain form on the same forest, for comparison ----
+    plain = None
+    if args.mode == "batched" and not args.no_plain:
+        for _ in range(1):
+            run_step(a, la, wl.rounds, la.LA_MODE_PLAIN, weights, False, torch)
+        torch.cuda.synchronize()
+        e_start.record()
+        pst = []
+        for _ in range(max(1, min(args.steps, 3))):
+            st_, _, _ = run_step(a, la, wl.rounds, la.LA_MODE_PLAIN, weights, True, torch)
+            pst += st_
+        e_end.record()
+        torch.cuda.synchronize()
+        p_ms = e_start.elapsed_time(e_end) / max(1, min(args.steps, 3))
+        plain = {"value": world * N * wl.rounds / (p_ms * 1e-3), "unit": "nets/s", "ms_per_step": round(p_ms, 3),
+                 "dp_ms_per_round": round(statistics.mean(x["ms_dp"] for x in pst), 4),
+                 "round_ms": round(statistics.mean(x["ms"] for x in pst), 4)}
 
     res = {
         "metric": METRIC, "value": value, "unit": "nets/s", "n_gpus": world, "steps": args.steps,
@@ -247,7 +308,7 @@ def bench_gpu(args):
         "vs_baseline": None, "dtype": "f64",
         "data": "synthetic: seeded grid + MST/L-split net forest generator (forestgen), seed = rank",
         "config": {"workload": wl.name, "nets": N, "nodes": V, "segments": S, "rounds_per_step": wl.rounds,
-                   "grid": f"{wl.X}x{wl.Y}x{wl.L}", "mode": args.mode,
+                   "grid": f"{wl.X}x{wl.Y}x{wl.L}", "mode": args.mode + ("+adjoint" if wl.rounds > 1 else ""),
                    "weights": "Eq. 4 in round 0, adjoint sensitivities in later rounds",
                    "l2": "inputs larger than L2 (working set %.1f GB)" % (a.device_bytes() / 1e9),
                    "parallelism": f"replicas x{world}"},
@@ -264,6 +325,7 @@ def bench_gpu(args):
                 "d2h_bytes_per_step": int(d2h), "ms_per_step": round(e2e_ms, 3),
                 "wall_ms_per_step": round(e2e_wall_ms, 3)},
         "gpu_launches": int(launches),
+        "plain_form": plain,
         "clocks": clk.summary(),
         "quality_last_round": {k: _finite(stats[-1][k]) for k in ("total_cost", "tof", "relu_overflow", "vias", "wl")},
     }
@@ -378,7 +440,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", type=int, default=5, choices=[1, 2, 4, 5])
-    ap.add_argument("--mode", default="plain", choices=["plain", "batched"])
+    ap.add_argument("--mode", default="batched", choices=["plain", "batched"])
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain-form comparison")
     ap.add_argument("--impl", default="gapla", choices=["gapla", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--ref-nets", type=int, default=400000)

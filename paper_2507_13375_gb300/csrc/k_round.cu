@@ -358,8 +358,10 @@ __device__ __forceinline__ void dp_node(const DPArgs& a, const DevTables& s, int
   }
 }
 
+// Leaves and one-son nodes fit 64 registers (4 blocks of 256 per SM); the
+// several-sons case keeps 2 blocks.
 template <int LMAX, int DEG, bool ROOT, bool CACHED>
-__global__ void __launch_bounds__(256) k_dp_level(LayerInfo li, DPArgs a) {
+__global__ void __launch_bounds__(256, (DEG <= 1 ? 4 : 2)) k_dp_level(LayerInfo li, DPArgs a) {
   __shared__ DevTables s;
   load_tables(s, a.tab);
   const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
