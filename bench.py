@@ -318,7 +318,7 @@ def bench_gpu(args):
                                 "demand_scan": round(statistics.mean(s["ms_demand"] for s in stats), 4),
                                 "adjoint": round(adj_ms, 4)},
         "load_ms": round(load_ms, 3), "generate_s": round(gen_s, 2),
-        "batched_plan": ({k: stats[-1][k] for k in ("batch_split", "batch_block", "batch_big_nets", "batch_cached", "batch_tune_ms")}
+        "batched_plan": ({k: stats[-1][k] for k in ("batch_split", "batch_block", "batch_big_nets", "batch_cached", "batch_trials", "batch_tune_ms")}
                          if args.mode == "batched" else None),
         "roofline": roofline,
         "e2e": {"value": world * N * wl.rounds / (e2e_ms * 1e-3), "unit": "nets/s", "h2d_bytes_per_step": int(h2d),
@@ -420,6 +420,8 @@ def profile_case(args):
 
     __graft_entry__.build()
     wl = fg.WORKLOADS[args.workload]
+    if args.nets:
+        wl = wl.scaled(args.nets)
     grid, forest = fg.make_grid(wl, 0), fg.make_forest(wl, 0)
     a = la.LayerAssigner(0)
     a.load_grid(grid)
@@ -431,7 +433,8 @@ def profile_case(args):
     R, C = a.rc_from_assignment()
     a.elmore(R, C)
     torch.cuda.synchronize()
-    print(json.dumps({"profile_case": wl.name, "rounds": args.rounds, "last_round_ms": st["ms"]}))
+    print(json.dumps({"profile_case": wl.name, "nets": wl.num_nets, "nodes": int(forest["num_nodes"]),
+                      "rounds": args.rounds, "last_round_ms": st["ms"], "device_bytes": a.device_bytes()}))
 
 
 def main():
@@ -448,6 +451,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", action="store_true", help="short untimed run for ncu captures")
     ap.add_argument("--rounds", type=int, default=1, help="rounds of the --profile run")
+    ap.add_argument("--nets", type=int, default=0, help="--profile: the workload's shape scaled to this many nets")
     args = ap.parse_args()
     if args.profile:
         profile_case(args)

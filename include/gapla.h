@@ -159,7 +159,9 @@ typedef struct {
   int32_t batch_split, batch_block;
   int64_t batch_big_nets;
   int32_t batch_cached;    /* 1: round-invariant constants cached per weight set  */
-  int32_t reserved2;
+  int32_t batch_trials;    /* plans timed to choose it; 0: taken untimed from the
+                            * tuning memo (an earlier forest with the same level,
+                            * class and size-class bucket offsets)                */
   double batch_tune_ms;    /* its DP + backtrack time when it was chosen         */
 } la_round_stats;
 

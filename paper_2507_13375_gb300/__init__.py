@@ -71,7 +71,7 @@ class RoundStats(ctypes.Structure):
                 ("wl_per_layer", ctypes.c_int64 * LA_MAX_LAYERS), ("ms", ctypes.c_double),
                 ("ms_dp", ctypes.c_double), ("ms_backtrack", ctypes.c_double), ("ms_demand", ctypes.c_double),
                 ("launches", ctypes.c_int64), ("batch_split", ctypes.c_int32), ("batch_block", ctypes.c_int32),
-                ("batch_big_nets", ctypes.c_int64), ("batch_cached", ctypes.c_int32), ("reserved2", ctypes.c_int32),
+                ("batch_big_nets", ctypes.c_int64), ("batch_cached", ctypes.c_int32), ("batch_trials", ctypes.c_int32),
                 ("batch_tune_ms", ctypes.c_double)]
 
 
@@ -202,7 +202,8 @@ def la_assign_round(ctx, mode: int = LA_MODE_PLAIN, weights: int = LA_WEIGHTS_EQ
     return dict(total_cost=s.total_cost, tof=s.tof, relu_overflow=s.relu_overflow, vias=s.vias, wl=s.wl,
                 wl_per_layer=list(s.wl_per_layer), ms=s.ms, ms_dp=s.ms_dp, ms_backtrack=s.ms_backtrack,
                 ms_demand=s.ms_demand, launches=s.launches, batch_split=s.batch_split, batch_block=s.batch_block,
-                batch_big_nets=s.batch_big_nets, batch_cached=s.batch_cached, batch_tune_ms=s.batch_tune_ms)
+                batch_big_nets=s.batch_big_nets, batch_cached=s.batch_cached, batch_trials=s.batch_trials,
+                batch_tune_ms=s.batch_tune_ms)
 
 
 def la_get_assignment(ctx, layer, b, t):

@@ -356,6 +356,8 @@ la_status la_load_grid(la_ctx* c, const la_grid_desc* gd) {
   return LA_OK;
 }
 
+static void plan_from_memo(la_ctx* c);
+
 // ------------------------------------------------------------------------
 la_status la_load_nets(la_ctx* c, const la_net_desc* nd) {
   TRY(check_ctx(c));
@@ -491,6 +493,7 @@ la_status la_load_nets(la_ctx* c, const la_net_desc* nd) {
   a->forest.release();
   a->forest = na;
   c->forest = nf;
+  plan_from_memo(c);
   return LA_OK;
 }
 
@@ -517,7 +520,7 @@ static BatchPlan make_plan(la_ctx* c, int k, int block, bool one_per_sm) {
   }
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
-  const int per_sm = one_per_sm ? 1 : bignet_blocks_per_sm(c->grid.li.L, block);
+  const int per_sm = one_per_sm ? 1 : bignet_blocks_per_sm(c->grid.li.L, c->LD, block);
   bp.grid = int(std::min<int64_t>(bp.n_big, int64_t(sms) * per_sm));
   if (bp.grid < 1) bp.grid = 1;
   return bp;
@@ -527,7 +530,7 @@ static BatchPlan make_plan(la_ctx* c, int k, int block, bool one_per_sm) {
 // fuse: the backtrack also updates the demand (not during tuning trials).
 static la_status enqueue_batched(la_ctx* c, const BatchPlan& bp, const RoundW& w, const double* W, const double* rho,
                                  int si, bool fuse, cudaStream_t s) {
-  const int cache = bp.cached ? si : -1;
+  const int cache = bp.cached ? si : kNoCache;
   Forest& f = c->forest;
   if (bp.n_big > 0) {
     CK(cudaEventRecord(c->ev_fork, s));
@@ -613,7 +616,32 @@ static la_status autotune(la_ctx* c, const RoundW& w, const double* W, const dou
     chosen.cache_wcap[i] = c->plan.cache_wcap[i];
   }
   c->plan = chosen;
+  TuneMemo& m = c->memo;
+  m.valid = true;
+  m.L = c->grid.li.L;
+  m.LD = c->LD;
+  m.key_off = f.key_off;
+  m.k = chosen.k;
+  m.block = chosen.block;
+  m.grid = chosen.grid;
+  m.cached = chosen.cached;
+  m.best_ms = chosen.best_ms;
+  m.trials = chosen.trials;
   return LA_OK;
+}
+
+// A forest with the same bucket offsets as the one the memo was tuned on
+// takes the memo's plan without new trials.
+static void plan_from_memo(la_ctx* c) {
+  const TuneMemo& m = c->memo;
+  if (!m.valid || m.L != c->grid.li.L || m.LD != c->LD || m.key_off != c->forest.key_off) return;
+  BatchPlan b = make_plan(c, m.k, m.block, false);
+  b.grid = m.grid;
+  b.cached = m.cached;
+  b.tuned = true;
+  b.best_ms = m.best_ms;
+  b.trials = 0;
+  c->plan = b;
 }
 
 // The round after the penalty prefix, as one CUDA graph (captured once per
@@ -641,10 +669,11 @@ static la_status batched_graph(la_ctx* c, const RoundW& w, const double* W, cons
     };
     launch_node_round(c, w, rho, si, s);
     mark(c->ev[1]);
-    if (st == LA_OK) st = enqueue_batched(c, bp, w, W, rho, si, true, s);
+    if (st == LA_OK) st = enqueue_batched(c, bp, w, W, rho, si, false, s);
     mark(c->ev[3]);
     Forest& f = c->forest;
     if (st == LA_OK) {
+      launch_demand(c, s);
       launch_scan_lines(c, true, w.hist_w, f.red, s);
       launch_sum_roots(c, f.red + f.red_cap, nullptr, s);
     }
@@ -709,7 +738,7 @@ la_status la_assign_round(la_ctx* c, const la_round_params* p, la_round_stats* s
     TRY(batched_graph(c, w, W, rho, si, s));
   } else {
     CK(cudaEventRecord(c->ev[1], s));
-    for (int h = 0; h <= f.Hmax; ++h) launch_dp_level(c, w, W, rho, h, kSizeClasses - 1, false, s);
+    for (int h = 0; h <= f.Hmax; ++h) launch_dp_level(c, w, W, rho, h, kSizeClasses - 1, kNoCache, s);
     CK(cudaEventRecord(c->ev[2], s));
     for (int h = f.Hmax; h >= 0; --h) launch_backtrack_level(c, h, kSizeClasses - 1, false, s);
     CK(cudaEventRecord(c->ev[3], s));
@@ -771,6 +800,7 @@ la_status la_assign_round(la_ctx* c, const la_round_params* p, la_round_stats* s
     stats->batch_big_nets = c->plan.n_big;
     stats->batch_tune_ms = c->plan.best_ms;
     stats->batch_cached = c->plan.cached ? 1 : 0;
+    stats->batch_trials = c->plan.trials;
   }
   return LA_OK;
 }

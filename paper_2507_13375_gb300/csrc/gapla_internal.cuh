@@ -208,6 +208,18 @@ struct BatchPlan {
   double cache_wd[2] = {-1.0, -1.0}, cache_wcap[2] = {-1.0, -1.0};
 };
 
+// The tuner's choice for one forest shape: a forest loaded later whose
+// (level, class, size class) bucket offsets are the same reuses it untimed.
+struct TuneMemo {
+  bool valid = false;
+  int L = 0, LD = 0;
+  std::vector<int64_t> key_off;
+  int k = 0, block = 0, grid = 0;
+  bool cached = true;
+  double best_ms = 0.0;
+  int trials = 0;
+};
+
 struct Stats {  // device accumulators of one round
   unsigned long long vias, wl, relu;
   unsigned long long wl_layer[kMaxL];
@@ -232,6 +244,7 @@ struct la_ctx {
   cudaStream_t s_cap = nullptr;         // stream the batched round is captured on
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   gapla::BatchPlan plan;
+  gapla::TuneMemo memo;
   void* alloc_groups = nullptr;         // device allocations, grouped per load
 };
 
@@ -264,8 +277,9 @@ struct RoundW {
 };
 void launch_scan_lines(la_ctx* c, bool from_diff, double hist_w, double* red_tof, cudaStream_t s);
 // kmax: nodes of nets up to size class kmax (kSizeClasses - 1 = every node)
-// cached: read the batched form's constant caches (ncache/scache)
-// cache: the constant-cache set to read (0/1), or -1 to recompute
+// cache: the batched form's constant-cache set to read (0 Eq. 4, 1 adjoint), or
+// kNoCache to recompute the constants in the DP (the plain form)
+constexpr int kNoCache = -1;
 void launch_dp_level(la_ctx* c, const RoundW& w, const double* W, const double* rho, int level, int kmax,
                      int cache, cudaStream_t s);
 // fuse_demand: the batched form's backtrack also does the demand update
@@ -276,7 +290,7 @@ void launch_dp_bignets(la_ctx* c, const RoundW& w, const double* W, const double
 void launch_backtrack_bignets(la_ctx* c, int64_t n_big, int grid, int block, bool fuse_demand, cudaStream_t s);
 void launch_seg_consts(la_ctx* c, const RoundW& w, const double* W, int cache, cudaStream_t s);
 void launch_node_round(la_ctx* c, const RoundW& w, const double* rho, int cache, cudaStream_t s);
-int bignet_blocks_per_sm(int L, int block);
+int bignet_blocks_per_sm(int L, int LD, int block);
 void launch_demand(la_ctx* c, cudaStream_t s);
 void launch_sum_roots(la_ctx* c, double* part, double* J_out, cudaStream_t s);
 int scan_blocks(const LayerInfo& li);

@@ -9,6 +9,7 @@
 // fma() exactly where the oracle calls fma().  Minima over non-negative
 // doubles compare their bit patterns as int64 (exact, and it keeps the
 // comparisons off the FP64 pipe, which GB300 runs at 1/64 of FP32).
+#include <algorithm>
 #include <climits>
 
 #include "gapla_internal.cuh"
@@ -16,11 +17,14 @@
 namespace gapla {
 
 // ---------------------------------------------------------------------------
-// Penalty + prefix per line.  One warp per (direction, line); lane j handles
-// edge position chunk*32 + j for every layer of the direction, so each step
-// reads 32 * nld contiguous elements.  from_diff = 1 also folds the demand
-// difference array into D (and clears it), updates H += max(0, D - C) and
-// accumulates the overflow statistics of the new demand.
+// Penalty + prefix per line.  One block per (direction, line).  The block
+// walks the line in rows of kScanT edge positions, thread j on position
+// row*kScanT + j for every layer of the direction (so a warp reads 32 * nld
+// contiguous elements).  Per row and layer: a warp shuffle scan, the warp
+// totals through shared memory (double-buffered by row parity, so one
+// barrier per scan), and the carry of the rows before.  from_diff = 1 also
+// folds the demand difference array into D (and clears it), updates
+// H += max(0, D - C) and accumulates the overflow statistics of the new demand.
 // ---------------------------------------------------------------------------
 struct ScanArgs {
   int32_t *cap, *D, *H, *diff;
@@ -33,6 +37,8 @@ struct ScanArgs {
   unsigned long long* relu;
 };
 
+constexpr int kScanT = 256, kScanW = kScanT / 32;
+
 template <typename Tv>
 __device__ __forceinline__ Tv warp_incl_scan(Tv x, int lane) {
 #pragma unroll
@@ -43,88 +49,139 @@ __device__ __forceinline__ Tv warp_incl_scan(Tv x, int lane) {
   return x;
 }
 
-__global__ void __launch_bounds__(256) k_scan_lines(const DevTables* __restrict__ tab, ScanArgs a) {
-  __shared__ double s_tof[8];
-  __shared__ unsigned long long s_relu[8];
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int64_t gl = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+// NLD bounds the layers of one direction (4, 6, 8 or 16 variants).
+// The direction's penalty table sits in shared memory (it is on the path from
+// D to the second scan); every global load of a row is issued before the
+// row's first barrier.
+template <int NLD>
+__global__ void __launch_bounds__(kScanT, (NLD <= 8 ? 3 : 1)) k_scan_lines(const DevTables* __restrict__ tab, ScanArgs a) {
+  __shared__ int32_t s_wd[2][kScanW][NLD];
+  __shared__ int64_t s_wp[2][kScanW][NLD];
+  __shared__ int64_t s_T[NLD][2][129];
+  __shared__ int s_lay[NLD];
+  __shared__ int32_t s_cD[2][NLD];  // carries into the row: D and P per layer
+  __shared__ int64_t s_cP[2][NLD];
+  __shared__ double s_tof[kScanW];
+  __shared__ unsigned long long s_relu[kScanW];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t gl = blockIdx.x;
   const int nl0 = tab->nlines[0];
-  const int64_t nl_total = int64_t(nl0) + tab->nlines[1];
+  const int d = gl < nl0 ? 0 : 1;
+  const int64_t line = gl - (d ? nl0 : 0);
+  const int nld = tab->nld[d], npos = tab->npos[d];
+  const int64_t base = tab->grid_off[d] + line * npos * nld;
+  for (int i = threadIdx.x; i < nld * 2 * 129; i += kScanT) {
+    const int q = i / 258, r = i - q * 258;
+    (&s_T[q][0][0])[r] = a.T[int(tab->lay[d][q]) * 258 + r];
+  }
+  if (threadIdx.x < NLD) {
+    s_lay[threadIdx.x] = tab->lay[d][threadIdx.x];
+    s_cD[0][threadIdx.x] = 0;
+    s_cP[0][threadIdx.x] = 0;
+  }
+  __syncthreads();
   double tof = 0.0;
   unsigned long long relu = 0;
-  if (gl < nl_total) {
-    const int d = gl < nl0 ? 0 : 1;
-    const int64_t line = gl - (d ? nl0 : 0);
-    const int nld = tab->nld[d], npos = tab->npos[d];
-    const int64_t base = tab->grid_off[d] + line * npos * nld;
-    int lays[kMaxL];
+  int buf = 0;
+  for (int r0 = 0; r0 < npos; r0 += kScanT, buf ^= 1) {
+    const int pos = r0 + int(threadIdx.x);
+    const bool valid = pos < npos;
+    const bool edge = pos < npos - 1;
+    const int64_t row = base + int64_t(pos) * nld;
+    int32_t Dv[NLD], cv[NLD], hv[NLD];
 #pragma unroll
-    for (int q = 0; q < kMaxL; ++q) lays[q] = tab->lay[d][q];
-    int32_t carryD[kMaxL];
-    int64_t carryP[kMaxL];
+    for (int q = 0; q < NLD; ++q) {
+      if (q < nld) {
+        Dv[q] = a.from_diff ? (valid ? a.diff[row + q] : 0) : (edge ? a.D[row + q] : 0);
+        cv[q] = edge ? a.cap[row + q] : 0;
+        hv[q] = edge ? a.H[row + q] : 0;
+      }
+    }
+    if (a.from_diff) {
 #pragma unroll
-    for (int q = 0; q < kMaxL; ++q) { carryD[q] = 0; carryP[q] = 0; }
-    for (int c0 = 0; c0 < npos; c0 += 32) {
-      const int pos = c0 + lane;
-      const bool valid = pos < npos;
-      const bool edge = pos < npos - 1;
-#pragma unroll
-      for (int q = 0; q < kMaxL; ++q) {
-        if (q >= nld) break;
-        const int64_t idx = base + int64_t(pos) * nld + q;
-        const int l = lays[q];
-        int32_t Dv;
-        if (a.from_diff) {
-          int32_t dv = 0;
-          if (valid) { dv = a.diff[idx]; a.diff[idx] = 0; }
-          Dv = warp_incl_scan<int32_t>(dv, lane) + carryD[q];
-          carryD[q] = __shfl_sync(0xffffffffu, Dv, 31);
-          if (edge) a.D[idx] = Dv;
-        } else {
-          Dv = edge ? a.D[idx] : 0;
+      for (int q = 0; q < NLD; ++q) {
+        if (q < nld) {
+          if (valid) a.diff[row + q] = 0;
+          Dv[q] = warp_incl_scan<int32_t>(Dv[q], lane);
+          if (lane == 31) s_wd[buf][w][q] = Dv[q];
         }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < NLD; ++q) {
+        if (q < nld) {
+          int32_t off = s_cD[buf][q], tot = off;
+#pragma unroll
+          for (int w2 = 0; w2 < kScanW; ++w2) {
+            const int32_t x = s_wd[buf][w2][q];
+            if (w2 < w) off += x;
+            tot += x;
+          }
+          Dv[q] += off;
+          if (threadIdx.x == 0) s_cD[buf ^ 1][q] = tot;
+          if (edge) a.D[row + q] = Dv[q];
+        }
+      }
+    }
+    int64_t pex[NLD];
+#pragma unroll
+    for (int q = 0; q < NLD; ++q) {
+      if (q < nld) {
         int64_t pen = 0;
         if (edge) {
-          const int32_t c = a.cap[idx];
-          int32_t h = a.H[idx];
+          const int32_t c = cv[q];
+          int32_t h = hv[q];
           const int si = c > 0 ? 0 : 1;
           if (a.from_diff) {
-            const int32_t over = Dv - c;
-            if (over > 0) { h += over; a.H[idx] = h; relu += (unsigned long long)over; }
+            const int32_t over = Dv[q] - c;
+            const int l = s_lay[q];
+            if (over > 0) { h += over; a.H[row + q] = h; relu += (unsigned long long)over; }
             if (over >= -128 && over <= 128) tof += a.tofT[(l * 2 + si) * 257 + (over + 128)];
             else tof += a.tofT[(l * 2 + si) * 257 + 128] * exp((si ? 1.5 : 0.5) * double(over));
           }
-          int kk = Dv + 1 - c;
+          int kk = Dv[q] + 1 - c;
           kk = kk < -64 ? -64 : (kk > 64 ? 64 : kk);
-          const int64_t tv = a.T[(l * 2 + si) * 129 + (kk + 64)];
+          const int64_t tv = s_T[q][si][kk + 64];
           if (h > 0 && a.HW > 0 && int64_t(h) > (kPenMax - tv) / a.HW) pen = kPenMax;
           else pen = tv + a.HW * int64_t(h);
           if (pen > kPenMax) pen = kPenMax;
         }
         const int64_t incl = warp_incl_scan<int64_t>(pen, lane);
-        if (valid) a.P[idx] = carryP[q] + (incl - pen);
-        carryP[q] += __shfl_sync(0xffffffffu, incl, 31);
+        pex[q] = incl - pen;
+        if (lane == 31) s_wp[buf][w][q] = incl;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < NLD; ++q) {
+      if (q < nld) {
+        int64_t off = s_cP[buf][q], tot = off;
+#pragma unroll
+        for (int w2 = 0; w2 < kScanW; ++w2) {
+          const int64_t x = s_wp[buf][w2][q];
+          if (w2 < w) off += x;
+          tot += x;
+        }
+        if (valid) a.P[row + q] = off + pex[q];
+        if (threadIdx.x == 0) s_cP[buf ^ 1][q] = tot;
       }
     }
   }
   // deterministic block reduction of the statistics
   tof = warp_sum(tof);
   relu = warp_sum(relu);
-  if (lane == 0) { s_tof[wib] = tof; s_relu[wib] = relu; }
+  if (lane == 0) { s_tof[w] = tof; s_relu[w] = relu; }
   __syncthreads();
   if (threadIdx.x == 0) {
     double t = 0.0;
     unsigned long long r = 0;
-    for (int w = 0; w < int(blockDim.x >> 5); ++w) { t += s_tof[w]; r += s_relu[w]; }
+    for (int w2 = 0; w2 < kScanW; ++w2) { t += s_tof[w2]; r += s_relu[w2]; }
     a.tof_part[blockIdx.x] = t;
     if (r) atomicAdd(a.relu, r);
   }
 }
 
-int scan_blocks(const LayerInfo& li) {
-  const int64_t lines = int64_t(li.nlines[0]) + li.nlines[1];
-  return int((lines * 32 + 255) / 256);
-}
+int scan_blocks(const LayerInfo& li) { return li.nlines[0] + li.nlines[1]; }
 
 void launch_scan_lines(la_ctx* c, bool from_diff, double hist_w, double* tof_part, cudaStream_t s) {
   Grid& g = c->grid;
@@ -134,7 +191,11 @@ void launch_scan_lines(la_ctx* c, bool from_diff, double hist_w, double* tof_par
   a.from_diff = from_diff ? 1 : 0;
   a.tof_part = tof_part;
   a.relu = &c->d_stats->relu;
-  k_scan_lines<<<scan_blocks(g.li), 256, 0, s>>>(g.tab_dev, a);
+  const int nb = scan_blocks(g.li), nmax = std::max(g.li.nld[0], g.li.nld[1]);
+  if (nmax <= 4) k_scan_lines<4><<<nb, kScanT, 0, s>>>(g.tab_dev, a);
+  else if (nmax <= 6) k_scan_lines<6><<<nb, kScanT, 0, s>>>(g.tab_dev, a);
+  else if (nmax <= 8) k_scan_lines<8><<<nb, kScanT, 0, s>>>(g.tab_dev, a);
+  else k_scan_lines<kMaxL><<<nb, kScanT, 0, s>>>(g.tab_dev, a);
   ++c->launches;
 }
 
@@ -178,7 +239,7 @@ __device__ __forceinline__ bool stack_better(long long f, int k, int b, long lon
 
 // The work of one thread: node v, candidate index ldi (0 at a root).
 // CACHED: read the batched form's constant caches instead of recomputing.
-template <int LMAX, int DEG, bool ROOT, bool CACHED>
+template <int LMAX, int LDM, int DEG, bool ROOT, bool CACHED>
 __device__ __forceinline__ void dp_node(const DPArgs& a, const DevTables& s, int L, int v, int ldi) {
   const int LD = a.LD;
   const int pin = a.pin[v];
@@ -215,33 +276,51 @@ __device__ __forceinline__ void dp_node(const DPArgs& a, const DevTables& s, int
     // One son: only a stack that is the hull of (junction, pin, son layer
     // lc), with lc the son's own least key inside it, can win (a larger stack
     // with the same choice costs more and loses ties on t - b): evaluate those.
+    // The son's layers ascend with j, so the hull of candidate j covers a run
+    // of indices: [p, q) (the layers in [lo_req, hi_req]) widened down to j or
+    // up to j.  j is its own least key there (ties to the lower index) iff
+    //   j in [p, q): j is the first least key of [p, q);
+    //   j < p:       key[j] <= every key of (j, q);
+    //   j >= q:      key[j] <  every key of [p, j).
     const int c = a.child_list[cs];
     const int dc = geo_dir(a.geo[c]);
     const int nldc = s.nld[dc];
     const double* Bc = a.B + int64_t(c) * LD;
     const double* Mc = a.M + int64_t(c) * LD;
-    long long key[LMAX];
+    long long key[LDM];
+    int lcs[LDM];
 #pragma unroll
-    for (int j = 0; j < LMAX; ++j)
-      if (j < nldc) key[j] = dbits(fma(Mc[j], rvl[s.lay[dc][j]], Bc[j]));
+    for (int j = 0; j < LDM; ++j) {
+      lcs[j] = s.lay[dc][j];
+      if (j < nldc) key[j] = dbits(fma(Mc[j], rvl[lcs[j]], Bc[j]));
+    }
+    long long inmin = LLONG_MAX;
+    int m = -1;
+#pragma unroll
+    for (int j = 0; j < LDM; ++j)
+      if (j < nldc && lcs[j] >= lo_req && lcs[j] <= hi_req && key[j] < inmin) { inmin = key[j]; m = j; }
+    unsigned cons = m >= 0 ? 1u << m : 0u;
+    long long run = inmin;
+#pragma unroll
+    for (int j = LDM - 1; j >= 0; --j)
+      if (j < nldc && lcs[j] < lo_req) {
+        if (key[j] <= run) cons |= 1u << j;
+        run = min(run, key[j]);
+      }
+    run = inmin;
+#pragma unroll
+    for (int j = 0; j < LDM; ++j)
+      if (j < nldc && lcs[j] > hi_req) {
+        if (key[j] < run) cons |= 1u << j;
+        run = min(run, key[j]);
+      }
     int bj = 0, bk = INT_MAX;
 #pragma unroll
-    for (int j = 0; j < LMAX; ++j) {
-      if (j < nldc) {
-        const int lc = s.lay[dc][j];
-        const int b0 = min(lo_req, lc), t0 = max(hi_req, lc);
-        bool consistent = true;
-#pragma unroll
-        for (int j2 = 0; j2 < LMAX; ++j2) {
-          if (j2 < nldc && j2 != j) {
-            const int l2 = s.lay[dc][j2];
-            if (l2 >= b0 && l2 <= t0 && (key[j2] < key[j] || (key[j2] == key[j] && j2 < j))) consistent = false;
-          }
-        }
-        if (consistent) {
-          const long long f = dbits(__longlong_as_double(key[j]) + fma(s.kd[t0 - b0], sigma_v, z));
-          if (stack_better(f, t0 - b0, b0, bfp, bk, bb)) { bfp = f; bk = t0 - b0; bb = b0; bt = t0; bj = j; }
-        }
+    for (int j = 0; j < LDM; ++j) {
+      if ((cons >> j) & 1u) {
+        const int b0 = min(lo_req, lcs[j]), t0 = max(hi_req, lcs[j]);
+        const long long f = dbits(__longlong_as_double(key[j]) + fma(s.kd[t0 - b0], sigma_v, z));
+        if (stack_better(f, t0 - b0, b0, bfp, bk, bb)) { bfp = f; bk = t0 - b0; bb = b0; bt = t0; bj = j; }
       }
     }
     if (bfp == LLONG_MAX) {  // cannot happen (the least key overall is consistent); report it
@@ -360,7 +439,7 @@ __device__ __forceinline__ void dp_node(const DPArgs& a, const DevTables& s, int
 
 // Leaves and one-son nodes fit 64 registers (4 blocks of 256 per SM); the
 // several-sons case keeps 2 blocks.
-template <int LMAX, int DEG, bool ROOT, bool CACHED>
+template <int LMAX, int LDM, int DEG, bool ROOT, bool CACHED>
 __global__ void __launch_bounds__(256, (DEG <= 1 ? 4 : 2)) k_dp_level(LayerInfo li, DPArgs a) {
   __shared__ DevTables s;
   load_tables(s, a.tab);
@@ -368,22 +447,22 @@ __global__ void __launch_bounds__(256, (DEG <= 1 ? 4 : 2)) k_dp_level(LayerInfo 
   const int64_t node_i = ROOT ? k : k / a.LD;
   const int ldi = ROOT ? 0 : int(k - node_i * a.LD);
   if (node_i >= a.count) return;
-  dp_node<LMAX, DEG, ROOT, CACHED>(a, s, li.L, int(a.base + node_i), ldi);
+  dp_node<LMAX, LDM, DEG, ROOT, CACHED>(a, s, li.L, int(a.base + node_i), ldi);
 }
 
 // Any node: pick its class at run time (used where classes mix).
-template <int LMAX, bool CACHED>
+template <int LMAX, int LDM, bool CACHED>
 __device__ void dp_node_any(const DPArgs& a, const DevTables& s, int L, int v, int ldi) {
   const int nc = a.nch[v];
   if (a.parent_g[v] < 0) {
     if (ldi != 0) return;
-    if (nc == 0) dp_node<LMAX, 0, true, CACHED>(a, s, L, v, 0);
-    else if (nc == 1) dp_node<LMAX, 1, true, CACHED>(a, s, L, v, 0);
-    else dp_node<LMAX, 2, true, CACHED>(a, s, L, v, 0);
+    if (nc == 0) dp_node<LMAX, LDM, 0, true, CACHED>(a, s, L, v, 0);
+    else if (nc == 1) dp_node<LMAX, LDM, 1, true, CACHED>(a, s, L, v, 0);
+    else dp_node<LMAX, LDM, 2, true, CACHED>(a, s, L, v, 0);
   } else {
-    if (nc == 0) dp_node<LMAX, 0, false, CACHED>(a, s, L, v, ldi);
-    else if (nc == 1) dp_node<LMAX, 1, false, CACHED>(a, s, L, v, ldi);
-    else dp_node<LMAX, 2, false, CACHED>(a, s, L, v, ldi);
+    if (nc == 0) dp_node<LMAX, LDM, 0, false, CACHED>(a, s, L, v, ldi);
+    else if (nc == 1) dp_node<LMAX, LDM, 1, false, CACHED>(a, s, L, v, ldi);
+    else dp_node<LMAX, LDM, 2, false, CACHED>(a, s, L, v, ldi);
   }
 }
 
@@ -418,7 +497,7 @@ struct BigArgs {
   int* ctr;
 };
 
-template <int LMAX, bool CACHED>
+template <int LMAX, int LDM, bool CACHED>
 __global__ void __launch_bounds__(256) k_dp_bignets(LayerInfo li, DPArgs a, BigArgs g) {
   __shared__ DevTables s;
   __shared__ int s_q;
@@ -437,7 +516,7 @@ __global__ void __launch_bounds__(256) k_dp_bignets(LayerInfo li, DPArgs a, BigA
     for (int h = 0; h <= H; ++h) {
       const int lo = ho[h], cnt = ho[h + 1] - lo;
       for (int t = threadIdx.x; t < cnt * LD; t += blockDim.x)
-        dp_node_any<LMAX, CACHED>(a, s, li.L, g.bl_nodes[base + lo + t / LD], t % LD);
+        dp_node_any<LMAX, LDM, CACHED>(a, s, li.L, g.bl_nodes[base + lo + t / LD], t % LD);
       __syncthreads();
     }
   }
@@ -513,25 +592,41 @@ __global__ void __launch_bounds__(256) k_backtrack_bignets(BtArgs a, BigArgs g) 
   }
 }
 
-template <int LMAX, int DEG, bool ROOT>
+template <int LMAX, int LDM, int DEG, bool ROOT>
 static void dp_launch(la_ctx* c, const DPArgs& a, cudaStream_t s) {
   const int T = 256;
   const int64_t threads = ROOT ? a.count : a.count * a.LD;
   const unsigned B = (unsigned)((threads + T - 1) / T);
-  if (a.scache) k_dp_level<LMAX, DEG, ROOT, true><<<B, T, 0, s>>>(c->grid.li, a);
-  else k_dp_level<LMAX, DEG, ROOT, false><<<B, T, 0, s>>>(c->grid.li, a);
+  if (a.scache) k_dp_level<LMAX, LDM, DEG, ROOT, true><<<B, T, 0, s>>>(c->grid.li, a);
+  else k_dp_level<LMAX, LDM, DEG, ROOT, false><<<B, T, 0, s>>>(c->grid.li, a);
   ++c->launches;
 }
 
-template <int LMAX>
+template <int LMAX, int LDM>
 static void dp_launch_class(la_ctx* c, const DPArgs& a, int cls, cudaStream_t s) {
   switch (cls) {
-    case 0: dp_launch<LMAX, 0, false>(c, a, s); break;
-    case 1: dp_launch<LMAX, 1, false>(c, a, s); break;
-    case 2: dp_launch<LMAX, 2, false>(c, a, s); break;
-    case 3: dp_launch<LMAX, 0, true>(c, a, s); break;
-    case 4: dp_launch<LMAX, 1, true>(c, a, s); break;
-    default: dp_launch<LMAX, 2, true>(c, a, s); break;
+    case 0: dp_launch<LMAX, LDM, 0, false>(c, a, s); break;
+    case 1: dp_launch<LMAX, LDM, 1, false>(c, a, s); break;
+    case 2: dp_launch<LMAX, LDM, 2, false>(c, a, s); break;
+    case 3: dp_launch<LMAX, LDM, 0, true>(c, a, s); break;
+    case 4: dp_launch<LMAX, LDM, 1, true>(c, a, s); break;
+    default: dp_launch<LMAX, LDM, 2, true>(c, a, s); break;
+  }
+}
+
+// Layer-count variants: LMAX bounds L, LDM the layers of one direction (half
+// of LMAX when the directions alternate).
+static void dp_launch_any(la_ctx* c, const DPArgs& a, int cls, cudaStream_t s) {
+  const int L = c->grid.li.L, LD = c->LD;
+  if (L <= 6) {
+    if (LD <= 3) dp_launch_class<6, 3>(c, a, cls, s);
+    else dp_launch_class<6, 6>(c, a, cls, s);
+  } else if (L <= 12) {
+    if (LD <= 6) dp_launch_class<12, 6>(c, a, cls, s);
+    else dp_launch_class<12, 12>(c, a, cls, s);
+  } else {
+    if (LD <= 8) dp_launch_class<16, 8>(c, a, cls, s);
+    else dp_launch_class<16, 16>(c, a, cls, s);
   }
 }
 
@@ -571,9 +666,7 @@ void launch_dp_level(la_ctx* c, const RoundW& w, const double* W, const double* 
     if (n == 0) continue;
     a.base = lo;
     a.count = n;
-    if (L <= 6) dp_launch_class<6>(c, a, cls, s);
-    else if (L <= 12) dp_launch_class<12>(c, a, cls, s);
-    else dp_launch_class<16>(c, a, cls, s);
+    dp_launch_any(c, a, cls, s);
   }
 }
 
@@ -666,17 +759,24 @@ void launch_dp_bignets(la_ctx* c, const RoundW& w, const double* W, const double
     a.ncache = c->forest.ncache[cache];
     a.scache = c->forest.scache[cache];
   }
-  const int L = c->grid.li.L;
+  const int L = c->grid.li.L, LD = c->LD;
   BigArgs g = big_args(c, n_big, 0);
-  if (cached) {
-    if (L <= 6) k_dp_bignets<6, true><<<grid, block, 0, s>>>(c->grid.li, a, g);
-    else if (L <= 12) k_dp_bignets<12, true><<<grid, block, 0, s>>>(c->grid.li, a, g);
-    else k_dp_bignets<16, true><<<grid, block, 0, s>>>(c->grid.li, a, g);
+#define BIG(LM, LDM_)                                                                   \
+  do {                                                                                 \
+    if (cached) k_dp_bignets<LM, LDM_, true><<<grid, block, 0, s>>>(c->grid.li, a, g);  \
+    else k_dp_bignets<LM, LDM_, false><<<grid, block, 0, s>>>(c->grid.li, a, g);        \
+  } while (0)
+  if (L <= 6) {
+    if (LD <= 3) BIG(6, 3);
+    else BIG(6, 6);
+  } else if (L <= 12) {
+    if (LD <= 6) BIG(12, 6);
+    else BIG(12, 12);
   } else {
-    if (L <= 6) k_dp_bignets<6, false><<<grid, block, 0, s>>>(c->grid.li, a, g);
-    else if (L <= 12) k_dp_bignets<12, false><<<grid, block, 0, s>>>(c->grid.li, a, g);
-    else k_dp_bignets<16, false><<<grid, block, 0, s>>>(c->grid.li, a, g);
+    if (LD <= 8) BIG(16, 8);
+    else BIG(16, 16);
   }
+#undef BIG
   ++c->launches;
 }
 
@@ -739,11 +839,12 @@ void launch_node_round(la_ctx* c, const RoundW& w, const double* rho, int cache,
 }
 
 // Resident blocks per SM of the big-net kernels (for a persistent grid).
-int bignet_blocks_per_sm(int L, int block) {
+int bignet_blocks_per_sm(int L, int LD, int block) {
   int n = 0;
-  if (L <= 6) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_dp_bignets<6, true>, block, 0);
-  else if (L <= 12) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_dp_bignets<12, true>, block, 0);
-  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_dp_bignets<16, true>, block, 0);
+  auto occ = [&](const void* k) { cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, block, 0); };
+  if (L <= 6) occ(LD <= 3 ? (const void*)k_dp_bignets<6, 3, true> : (const void*)k_dp_bignets<6, 6, true>);
+  else if (L <= 12) occ(LD <= 6 ? (const void*)k_dp_bignets<12, 6, true> : (const void*)k_dp_bignets<12, 12, true>);
+  else occ(LD <= 8 ? (const void*)k_dp_bignets<16, 8, true> : (const void*)k_dp_bignets<16, 16, true>);
   return n > 0 ? n : 1;
 }
 
@@ -752,7 +853,15 @@ int bignet_blocks_per_sm(int L, int block) {
 // difference array of its line and layer (the line scan folds it into D),
 // plus vias and wirelength per layer.  Integer atomics: exact in any order.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_demand(int64_t V, int L, const DevTables* __restrict__ tab,
+struct DemandDir {
+  int64_t grid_off;   // this direction's first element
+  int32_t npos, nld;
+  uint64_t ld_of4;    // index of layer l within its direction in bits 4l..4l+3
+};
+
+// Every load of a node is issued at once (streaming: the node arrays are read
+// once and must not evict the difference array from L2).
+__global__ void __launch_bounds__(256) k_demand(int64_t V, int L, int dir, DemandDir g,
                                                 const int32_t* __restrict__ parent_g,
                                                 const uint64_t* __restrict__ geo, const int8_t* __restrict__ layer,
                                                 const int8_t* __restrict__ b, const int8_t* __restrict__ t,
@@ -762,22 +871,28 @@ __global__ void __launch_bounds__(256) k_demand(int64_t V, int L, const DevTable
   if (threadIdx.x < kMaxL) s_wl[threadIdx.x] = 0;
   __syncthreads();
   const int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  unsigned long long vias = 0;
+  unsigned vias = 0, len = 0;
+  int l = -1;
   if (v < V) {
-    vias = (unsigned long long)(t[v] - b[v]);
-    if (parent_g[v] >= 0) {
-      const uint64_t g = geo[v];
-      const int d = geo_dir(g), len = geo_len(g);
-      const int l = layer[v];
-      const int nld = tab->nld[d];
-      const int64_t base = tab->grid_off[d] + (int64_t(geo_line(g)) * tab->npos[d] + geo_lo(g)) * nld + tab->ld_of[l];
+    const int32_t pg = __ldcs(parent_g + v);
+    const uint64_t gv = __ldcs(reinterpret_cast<const unsigned long long*>(geo) + v);
+    const int lv = __ldcs(reinterpret_cast<const signed char*>(layer) + v);
+    if (dir == 0) vias = unsigned(__ldcs(reinterpret_cast<const signed char*>(t) + v) -
+                                  __ldcs(reinterpret_cast<const signed char*>(b) + v));
+    if (pg >= 0 && geo_dir(gv) == dir) {
+      len = unsigned(geo_len(gv));
+      l = lv;
+      const int64_t base = g.grid_off + (int64_t(geo_line(gv)) * g.npos + geo_lo(gv)) * g.nld + int((g.ld_of4 >> (4 * lv)) & 15u);
       atomicAdd(diff + base, 1);
-      atomicAdd(diff + base + int64_t(len) * nld, -1);
-      atomicAdd(&s_wl[l], (unsigned long long)len);
+      atomicAdd(diff + base + int64_t(len) * g.nld, -1);
     }
   }
-  vias = warp_sum(vias);
-  if ((threadIdx.x & 31) == 0) s_v[threadIdx.x >> 5] = vias;
+  // warp sums first: one shared atomic per warp and layer
+  const unsigned wv = __reduce_add_sync(0xffffffffu, vias);
+  if ((threadIdx.x & 31) == 0) s_v[threadIdx.x >> 5] = wv;
+  const unsigned peers = __match_any_sync(0xffffffffu, l);
+  const unsigned wl = __reduce_add_sync(peers, len);
+  if (l >= 0 && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&s_wl[l], (unsigned long long)wl);
   __syncthreads();
   if (threadIdx.x == 0) {
     unsigned long long sv = 0;
@@ -790,12 +905,22 @@ __global__ void __launch_bounds__(256) k_demand(int64_t V, int L, const DevTable
   }
 }
 
+// One pass per direction: the atomics of a pass land in that direction's half
+// of the difference array, which stays resident in L2 while they land.
 void launch_demand(la_ctx* c, cudaStream_t s) {
   Forest& f = c->forest;
+  const LayerInfo& li = c->grid.li;
   const int T = 256;
-  k_demand<<<(unsigned)((f.V + T - 1) / T), T, 0, s>>>(f.V, c->grid.li.L, c->grid.tab_dev, f.parent_g, f.geo,
-                                                     f.layer, f.b, f.t, c->grid.diff, c->d_stats);
-  ++c->launches;
+  for (int dir = 0; dir < 2; ++dir) {
+    DemandDir g{};
+    g.grid_off = li.grid_off[dir];
+    g.npos = li.npos[dir];
+    g.nld = li.nld[dir];
+    for (int l = 0; l < li.L; ++l) g.ld_of4 |= uint64_t(li.ld_of[l] & 15) << (4 * l);
+    k_demand<<<(unsigned)((f.V + T - 1) / T), T, 0, s>>>(f.V, li.L, dir, g, f.parent_g, f.geo, f.layer, f.b, f.t,
+                                                         c->grid.diff, c->d_stats);
+    ++c->launches;
+  }
 }
 
 // Per-block partial sums of the root costs J_n, in net order (deterministic).

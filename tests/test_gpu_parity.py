@@ -277,6 +277,20 @@ def test_batched_equals_plain(la, cfg, nets):
         assert p["stats"]["vias"] == q["stats"]["vias"] and p["stats"]["total_cost"] == q["stats"]["total_cost"]
 
 
+def test_plain_after_batched(la):
+    """The plain form recomputes every constant: after batched rounds have
+    filled the constant caches of both weight sources, plain rounds on the
+    same context still equal the batched ones (adjoint weights included)."""
+    wl = fg.WORKLOADS[5].scaled(30000)
+    grid, forest = fg.make_grid(wl, 8), fg.make_forest(wl, 8)
+    a = _assigner(la, grid, forest)
+    batched = _rounds(a, la, la.LA_MODE_BATCHED, 3, adjoint=True)
+    plain = _rounds(a, la, la.LA_MODE_PLAIN, 3, adjoint=True)
+    for r, (p, q) in enumerate(zip(batched, plain)):
+        for k in ("layer", "b", "t", "D", "H", "J"):
+            assert np.array_equal(p[k], q[k]), (r, k)
+
+
 def test_batched_deep_trees_against_oracle(la):
     """Config 4 shape (Zipf pin counts up to 4096: deep trees handled by the
     persistent block-per-net kernels) against the oracle, two rounds."""
@@ -294,3 +308,28 @@ def test_batched_deep_trees_against_oracle(la):
         ref = ref_round(grid, forest, la.DEFAULT_WEIGHTS, D=D, H=H)
         assert_same_round(got, ref, f"round {r}")
         D, H = got["D"], got["H"]
+
+
+def test_batched_reload_reuses_tuning(la):
+    """A reload of a forest with the same bucket layout takes the tuned plan
+    untimed (no trials) and gives the same round; another forest re-tunes."""
+    wl = fg.WORKLOADS[4].scaled(6000)
+    grid, forest = fg.make_grid(wl, 3), fg.make_forest(wl, 3)
+    a = _assigner(la, grid, forest)
+    first = _rounds(a, la, la.LA_MODE_BATCHED, 2)
+    assert first[0]["stats"]["batch_trials"] > 0
+    a.load_nets(forest)
+    again = _rounds(a, la, la.LA_MODE_BATCHED, 2)
+    assert again[0]["stats"]["batch_trials"] == 0
+    assert again[0]["stats"]["batch_split"] == first[0]["stats"]["batch_split"]
+    for p, q in zip(first, again):
+        for k in ("layer", "b", "t", "D", "H", "J"):
+            assert np.array_equal(p[k], q[k]), k
+    other = fg.make_forest(wl, 4)
+    a.load_nets(other)
+    st = a.assign_round(mode=la.LA_MODE_BATCHED, reset=True, **la.DEFAULT_WEIGHTS)
+    assert st["batch_trials"] > 0
+    got = dict(zip(("layer", "b", "t"), (x.cpu().numpy() for x in a.get_assignment())))
+    a.assign_round(mode=la.LA_MODE_PLAIN, reset=True, **la.DEFAULT_WEIGHTS)
+    for k, x in zip(("layer", "b", "t"), a.get_assignment()):
+        assert np.array_equal(got[k], x.cpu().numpy()), k
