@@ -107,7 +107,8 @@ typedef struct {
   const int32_t* parent;   /* device, V: net-local parent id; -1 exactly at local 0  */
   const int8_t* pin_layer; /* device, V: layer of the node's pin, -1 = no pin; the
                               root must have one (the driver pin)                    */
-  const double* sink_cap;  /* device, V: sink pin capacitance (fF) >= 0              */
+  const double* sink_cap;  /* device, V: sink pin capacitance (fF) >= 0; exactly 0 at
+                              a node without a pin                                  */
   const double* kappa;     /* device, V: sink criticality >= 0 (edge weights, Eq. 4) */
   const double* r_drv;     /* device, N: driver resistance (ohm) >= 0                */
 } la_net_desc;

@@ -105,7 +105,7 @@ static const char* dev_err_name(int code) {
     case DE_COORD: return "node coordinate outside the grid";
     case DE_SEGMENT: return "tree edge is not a straight horizontal/vertical run of length >= 1";
     case DE_PIN: return "pin layer out of range, or a root without a driver pin";
-    case DE_VALUE: return "negative or non-finite value";
+    case DE_VALUE: return "negative or non-finite value, or a sink cap at a node without a pin";
     case DE_ASSIGN: return "assignment layer of the wrong direction, or a via stack not covering it";
     case DE_DEGREE: return "too many sons";
     case DE_NOSTACK: return "no valid via stack";

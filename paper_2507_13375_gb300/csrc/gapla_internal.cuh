@@ -26,12 +26,16 @@ namespace gapla {
 constexpr int kMaxL = LA_MAX_LAYERS;
 constexpr int64_t kPenMax = int64_t(1) << 48;
 
-// Nodes are bucketed by (level, class, size class): class = 3 * is_root +
-// min(sons, 2); size class = ceil(log2(nodes of the node's net)), capped at 15.
-// Inside every (level, class) range the nodes of nets with at most 2^k nodes
-// form a prefix, for every k: the batched form splits small and large nets at
-// any power of two without re-sorting.
-constexpr int kClasses = 6;
+// Nodes are bucketed by (level, class, size class): class = min(sons, 2) +
+// 0 for a non-root node with a pin, 3 for a root (roots always hold the driver
+// pin), 6 for a node without a pin; size class = ceil(log2(nodes of the node's
+// net)), capped at 15.  Inside every (level, class) range the nodes of nets
+// with at most 2^k nodes form a prefix, for every k: the batched form splits
+// small and large nets at any power of two without re-sorting.
+constexpr int kClasses = 9;
+__host__ __device__ inline int node_class(bool root, int sons, bool has_pin) {
+  return (sons < 2 ? sons : 2) + (root ? 3 : (has_pin ? 0 : 6));
+}
 constexpr int kSizeClasses = 16;
 constexpr int kMinBigSc = 5;  // nets of 17+ nodes get per-net level lists
 __host__ __device__ inline int size_class(int64_t m) {
@@ -51,7 +55,7 @@ enum DevErr : int {
   DE_COORD = 3,       // x / y outside the grid
   DE_SEGMENT = 4,     // segment not straight or of zero length
   DE_PIN = 5,         // pin layer out of range, or root without a pin
-  DE_VALUE = 6,       // negative or non-finite cap / criticality / driver R
+  DE_VALUE = 6,       // negative or non-finite cap / criticality / driver R; cap without a pin
   DE_ASSIGN = 7,      // assignment layer of the wrong direction / stack not covering
   DE_DEGREE = 8,      // more sons than the kernels support
   DE_NOSTACK = 9,     // DP found no valid stack (internal)

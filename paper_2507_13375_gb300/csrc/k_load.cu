@@ -75,7 +75,11 @@ __global__ void k_forest_prepare(PrepArgs a) {
     if (xv < 0 || xv >= a.X || yv < 0 || yv >= a.Y) { dev_error(a.err, DE_COORD, v); bad = true; break; }
     const int pv = a.pin_in[v];
     if (pv < -1 || pv >= a.L || (i == 0 && pv < 0)) { dev_error(a.err, DE_PIN, v); bad = true; break; }
-    if (!finite_nonneg(a.cap_in[v]) || !finite_nonneg(a.kap_in[v])) { dev_error(a.err, DE_VALUE, v); bad = true; break; }
+    if (!finite_nonneg(a.cap_in[v]) || !finite_nonneg(a.kap_in[v]) || (pv < 0 && a.cap_in[v] != 0.0)) {
+      dev_error(a.err, DE_VALUE, v);
+      bad = true;
+      break;
+    }
   }
   if (bad) return;
   if (!finite_nonneg(a.rdrv_in[n])) { dev_error(a.err, DE_VALUE, base); return; }
@@ -146,9 +150,10 @@ void launch_forest_prepare(la_ctx* c, Forest& f, const la_net_desc* d, int* d_hm
 struct BucketIn {
   const int32_t *height, *nch, *parent_g, *net_of;
   const int64_t* net_ptr;
+  const int8_t* pin;
 };
 __device__ __forceinline__ long long node_bucket(int64_t v, const BucketIn& b) {
-  const int cls = (b.parent_g[v] < 0 ? 3 : 0) + min(b.nch[v], 2);
+  const int cls = node_class(b.parent_g[v] < 0, b.nch[v], b.pin[v] >= 0);
   const int n = b.net_of[v];
   return bucket_key(b.height[v], cls, size_class(b.net_ptr[n + 1] - b.net_ptr[n]));
 }
@@ -182,7 +187,7 @@ __global__ void k_level_place(int64_t V, BucketIn b, unsigned long long* __restr
 void launch_level_sort(Forest& f, int32_t* lvl_cnt, int64_t* lvl_cursor, cudaStream_t s) {
   const int T = 256;
   const unsigned B = (unsigned)((f.V + T - 1) / T);
-  BucketIn b{f.height, f.nch, f.parent_g, f.net_of, f.net_ptr};
+  BucketIn b{f.height, f.nch, f.parent_g, f.net_of, f.net_ptr, f.pin};
   if (lvl_cnt) k_level_count<<<B, T, 0, s>>>(f.V, b, lvl_cnt);
   if (lvl_cursor) k_level_place<<<B, T, 0, s>>>(f.V, b, reinterpret_cast<unsigned long long*>(lvl_cursor), f.lvl_nodes);
 }

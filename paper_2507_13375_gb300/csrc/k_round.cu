@@ -237,12 +237,27 @@ __device__ __forceinline__ bool stack_better(long long f, int k, int b, long lon
   return f < bf || (f == bf && (k < bk || (k == bk && b < bb)));
 }
 
+// Round constants of the tail terms at a node without a pin: fma(k, s, 0.0)
+// is the rounded product k s, the same for every such node.
+struct RoundTabs {
+  double tS[kMaxL];  // (via count) x sigma0, sigma0 = w_via + w_cap vc
+  double tC[kMaxL];  // (via count) x vc
+};
+__device__ __forceinline__ void load_round_tabs(RoundTabs& rt, const DPArgs& a, double via_c) {
+  if (threadIdx.x < kMaxL) {
+    rt.tS[threadIdx.x] = double(threadIdx.x) * a.sigma0;
+    rt.tC[threadIdx.x] = double(threadIdx.x) * via_c;
+  }
+}
+
 // The work of one thread: node v, candidate index ldi (0 at a root).
 // CACHED: read the batched form's constant caches instead of recomputing.
-template <int LMAX, int LDM, int DEG, bool ROOT, bool CACHED>
-__device__ __forceinline__ void dp_node(const DPArgs& a, const DevTables& s, int L, int v, int ldi) {
+// PINK: 1 the node has a pin, 0 it has none, 2 read it (mixed classes).
+template <int LMAX, int LDM, int DEG, bool ROOT, bool CACHED, int PINK>
+__device__ __forceinline__ void dp_node(const DPArgs& a, const DevTables& s, const RoundTabs& rt, int L, int v,
+                                        int ldi) {
   const int LD = a.LD;
-  const int pin = a.pin[v];
+  const int pin = PINK == 0 ? -1 : a.pin[v];
   const uint64_t gv = a.geo[v];
   const int d = geo_dir(gv);
   int l;
@@ -257,7 +272,7 @@ __device__ __forceinline__ void dp_node(const DPArgs& a, const DevTables& s, int
   const double wd_rho = CACHED ? nc[2] : a.w_d * a.rho[v];
   const double sigma_v = CACHED ? nc[3] : fma(wd_rho, s.via_c, a.sigma0);
   double Cs = 0.0, sinkf = 0.0, z = 0.0;  // a node without a pin: all exactly 0
-  if (pin >= 0) {
+  if (PINK == 1 || (PINK == 2 && pin >= 0)) {
     Cs = a.sink_cap[v];
     sinkf = ((CACHED ? nc[1] : a.w_d * a.kappa[v]) * rvl[pin]) * Cs;
     z = fma(wd_rho, Cs, sinkf);
@@ -399,8 +414,14 @@ __device__ __forceinline__ void dp_node(const DPArgs& a, const DevTables& s, int
 
   // the table entry of the winning stack (0.0 + x == x for the x >= 0 here)
   const int kk = bt - bb;
-  const double fv = DEG == 0 ? fma(s.kd[kk], a.sigma0, sinkf) : sg + fma(s.kd[kk], a.sigma0, sinkf);
-  const double cv = DEG == 0 ? fma(s.kd[kk], s.via_c, Cs) : sc + fma(s.kd[kk], s.via_c, Cs);
+  double fv, cv;
+  if constexpr (PINK == 0) {
+    fv = DEG == 0 ? rt.tS[kk] : sg + rt.tS[kk];
+    cv = DEG == 0 ? rt.tC[kk] : sc + rt.tC[kk];
+  } else {
+    fv = DEG == 0 ? fma(s.kd[kk], a.sigma0, sinkf) : sg + fma(s.kd[kk], a.sigma0, sinkf);
+    cv = DEG == 0 ? fma(s.kd[kk], s.via_c, Cs) : sc + fma(s.kd[kk], s.via_c, Cs);
+  }
   const int64_t o = int64_t(v) * LD + ldi;
   a.sb[o] = int8_t(bb);
   a.st[o] = int8_t(bt);
@@ -439,30 +460,32 @@ __device__ __forceinline__ void dp_node(const DPArgs& a, const DevTables& s, int
 
 // Leaves and one-son nodes fit 64 registers (4 blocks of 256 per SM); the
 // several-sons case keeps 2 blocks.
-template <int LMAX, int LDM, int DEG, bool ROOT, bool CACHED>
+template <int LMAX, int LDM, int DEG, bool ROOT, bool CACHED, int PINK>
 __global__ void __launch_bounds__(256, (DEG <= 1 ? 4 : 2)) k_dp_level(LayerInfo li, DPArgs a) {
   __shared__ DevTables s;
+  __shared__ RoundTabs rt;
+  load_round_tabs(rt, a, li.via_c);
   load_tables(s, a.tab);
   const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   const int64_t node_i = ROOT ? k : k / a.LD;
   const int ldi = ROOT ? 0 : int(k - node_i * a.LD);
   if (node_i >= a.count) return;
-  dp_node<LMAX, LDM, DEG, ROOT, CACHED>(a, s, li.L, int(a.base + node_i), ldi);
+  dp_node<LMAX, LDM, DEG, ROOT, CACHED, PINK>(a, s, rt, li.L, int(a.base + node_i), ldi);
 }
 
 // Any node: pick its class at run time (used where classes mix).
 template <int LMAX, int LDM, bool CACHED>
-__device__ void dp_node_any(const DPArgs& a, const DevTables& s, int L, int v, int ldi) {
+__device__ void dp_node_any(const DPArgs& a, const DevTables& s, const RoundTabs& rt, int L, int v, int ldi) {
   const int nc = a.nch[v];
   if (a.parent_g[v] < 0) {
     if (ldi != 0) return;
-    if (nc == 0) dp_node<LMAX, LDM, 0, true, CACHED>(a, s, L, v, 0);
-    else if (nc == 1) dp_node<LMAX, LDM, 1, true, CACHED>(a, s, L, v, 0);
-    else dp_node<LMAX, LDM, 2, true, CACHED>(a, s, L, v, 0);
+    if (nc == 0) dp_node<LMAX, LDM, 0, true, CACHED, 2>(a, s, rt, L, v, 0);
+    else if (nc == 1) dp_node<LMAX, LDM, 1, true, CACHED, 2>(a, s, rt, L, v, 0);
+    else dp_node<LMAX, LDM, 2, true, CACHED, 2>(a, s, rt, L, v, 0);
   } else {
-    if (nc == 0) dp_node<LMAX, LDM, 0, false, CACHED>(a, s, L, v, ldi);
-    else if (nc == 1) dp_node<LMAX, LDM, 1, false, CACHED>(a, s, L, v, ldi);
-    else dp_node<LMAX, LDM, 2, false, CACHED>(a, s, L, v, ldi);
+    if (nc == 0) dp_node<LMAX, LDM, 0, false, CACHED, 2>(a, s, rt, L, v, ldi);
+    else if (nc == 1) dp_node<LMAX, LDM, 1, false, CACHED, 2>(a, s, rt, L, v, ldi);
+    else dp_node<LMAX, LDM, 2, false, CACHED, 2>(a, s, rt, L, v, ldi);
   }
 }
 
@@ -500,7 +523,9 @@ struct BigArgs {
 template <int LMAX, int LDM, bool CACHED>
 __global__ void __launch_bounds__(256) k_dp_bignets(LayerInfo li, DPArgs a, BigArgs g) {
   __shared__ DevTables s;
+  __shared__ RoundTabs rt;
   __shared__ int s_q;
+  load_round_tabs(rt, a, li.via_c);
   load_tables(s, a.tab);
   const int LD = a.LD;
   for (;;) {
@@ -516,7 +541,7 @@ __global__ void __launch_bounds__(256) k_dp_bignets(LayerInfo li, DPArgs a, BigA
     for (int h = 0; h <= H; ++h) {
       const int lo = ho[h], cnt = ho[h + 1] - lo;
       for (int t = threadIdx.x; t < cnt * LD; t += blockDim.x)
-        dp_node_any<LMAX, LDM, CACHED>(a, s, li.L, g.bl_nodes[base + lo + t / LD], t % LD);
+        dp_node_any<LMAX, LDM, CACHED>(a, s, rt, li.L, g.bl_nodes[base + lo + t / LD], t % LD);
       __syncthreads();
     }
   }
@@ -592,25 +617,29 @@ __global__ void __launch_bounds__(256) k_backtrack_bignets(BtArgs a, BigArgs g) 
   }
 }
 
-template <int LMAX, int LDM, int DEG, bool ROOT>
+template <int LMAX, int LDM, int DEG, bool ROOT, int PINK>
 static void dp_launch(la_ctx* c, const DPArgs& a, cudaStream_t s) {
   const int T = 256;
   const int64_t threads = ROOT ? a.count : a.count * a.LD;
   const unsigned B = (unsigned)((threads + T - 1) / T);
-  if (a.scache) k_dp_level<LMAX, LDM, DEG, ROOT, true><<<B, T, 0, s>>>(c->grid.li, a);
-  else k_dp_level<LMAX, LDM, DEG, ROOT, false><<<B, T, 0, s>>>(c->grid.li, a);
+  if (a.scache) k_dp_level<LMAX, LDM, DEG, ROOT, true, PINK><<<B, T, 0, s>>>(c->grid.li, a);
+  else k_dp_level<LMAX, LDM, DEG, ROOT, false, PINK><<<B, T, 0, s>>>(c->grid.li, a);
   ++c->launches;
 }
 
+// class -> kernel (node_class: 0-2 pin, 3-5 root, 6-8 no pin; sons 0, 1, 2+)
 template <int LMAX, int LDM>
 static void dp_launch_class(la_ctx* c, const DPArgs& a, int cls, cudaStream_t s) {
   switch (cls) {
-    case 0: dp_launch<LMAX, LDM, 0, false>(c, a, s); break;
-    case 1: dp_launch<LMAX, LDM, 1, false>(c, a, s); break;
-    case 2: dp_launch<LMAX, LDM, 2, false>(c, a, s); break;
-    case 3: dp_launch<LMAX, LDM, 0, true>(c, a, s); break;
-    case 4: dp_launch<LMAX, LDM, 1, true>(c, a, s); break;
-    default: dp_launch<LMAX, LDM, 2, true>(c, a, s); break;
+    case 0: dp_launch<LMAX, LDM, 0, false, 1>(c, a, s); break;
+    case 1: dp_launch<LMAX, LDM, 1, false, 1>(c, a, s); break;
+    case 2: dp_launch<LMAX, LDM, 2, false, 1>(c, a, s); break;
+    case 3: dp_launch<LMAX, LDM, 0, true, 1>(c, a, s); break;
+    case 4: dp_launch<LMAX, LDM, 1, true, 1>(c, a, s); break;
+    case 5: dp_launch<LMAX, LDM, 2, true, 1>(c, a, s); break;
+    case 6: dp_launch<LMAX, LDM, 0, false, 0>(c, a, s); break;
+    case 7: dp_launch<LMAX, LDM, 1, false, 0>(c, a, s); break;
+    default: dp_launch<LMAX, LDM, 2, false, 0>(c, a, s); break;
   }
 }
 

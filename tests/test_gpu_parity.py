@@ -216,7 +216,7 @@ def test_eq4_weights_match_oracle(la):
 
 
 @pytest.mark.parametrize("case", ["bent_segment", "parent_order", "outside", "root_without_pin", "negative_cap",
-                                  "net_ptr"])
+                                  "cap_without_pin", "net_ptr"])
 def test_malformed_forest_is_rejected(la, case):
     wl = fg.WORKLOADS[1].scaled(50)
     grid, forest = fg.make_grid(wl, 1), fg.make_forest(wl, 1)
@@ -233,6 +233,8 @@ def test_malformed_forest_is_rejected(la, case):
         bad["pin_layer"][int(bad["net_ptr"][5])] = -1
     elif case == "negative_cap":
         bad["sink_cap"][v] = -1.0
+    elif case == "cap_without_pin":
+        bad["sink_cap"][int(np.flatnonzero(bad["pin_layer"] < 0)[0])] = 1.0
     elif case == "net_ptr":
         bad["net_ptr"][4] = bad["net_ptr"][6]
     a = la.LayerAssigner(0)

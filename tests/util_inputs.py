@@ -83,8 +83,8 @@ def merge_forests(parts) -> dict:
 def edge_case_forest(X: int, Y: int, L: int, seed: int = 0) -> dict:
     """Hand-made nets covering the degenerate shapes: a single-node net, a
     2-pin straight net, a long zig-zag chain (deep tree), a star with four
-    sons, a Steiner node with three sons, pins on upper layers, and a sink
-    merged into the driver's GCell."""
+    sons, a Steiner node with three sons, pins on upper layers, a sink merged
+    into the driver's GCell, and a branch that ends without a pin."""
     rng = np.random.default_rng(seed)
     nets = []
     u = lambda: float(rng.uniform(0.1, 1.0))
@@ -116,4 +116,7 @@ def edge_case_forest(X: int, Y: int, L: int, seed: int = 0) -> dict:
                                   (4, 0, 10, 0, 3.0, u())], r_drv=60.0))
     # sink merged into the driver node, and a son
     nets.append(forest_from_rows([(-1, 5, 5, 0, 4.0, 0.9), (0, 5, 1, 0, 1.0, 0.2)], r_drv=400.0))
+    # a dangling branch: a leaf without a pin, and a bend without a pin below it
+    nets.append(forest_from_rows([(-1, 4, 4, 0, 0.0, 0.0), (0, 9, 4, 0, 1.5, u()), (0, 4, 7, -1, 0.0, 0.0),
+                                  (2, 1, 7, -1, 0.0, 0.0)], r_drv=150.0))
     return merge_forests(nets)
