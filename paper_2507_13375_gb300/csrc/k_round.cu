@@ -253,9 +253,17 @@ __device__ __forceinline__ void load_round_tabs(RoundTabs& rt, const DPArgs& a, 
 // The work of one thread: node v, candidate index ldi (0 at a root).
 // CACHED: read the batched form's constant caches instead of recomputing.
 // PINK: 1 the node has a pin, 0 it has none, 2 read it (mixed classes).
-template <int LMAX, int LDM, int DEG, bool ROOT, bool CACHED, int PINK>
+// STAGED (one son, not a root): the son and its table row (B, M, A, Cc) come
+// in `so`, already copied to shared memory by the node's threads.
+struct Son1 {
+  int c, dc;
+  const double *B, *M, *A, *Cc;
+  const double* T;  // no pin: the node's tail costs T(k) = fma(k, sigma_v, 0.0), k < L
+};
+template <int LMAX, int LDM, int DEG, bool ROOT, bool CACHED, int PINK, bool STAGED = false>
 __device__ __forceinline__ void dp_node(const DPArgs& a, const DevTables& s, const RoundTabs& rt, int L, int v,
-                                        int ldi) {
+                                        int ldi, const Son1& so = Son1{}) {
+  static_assert(!STAGED || (DEG == 1 && !ROOT), "staged son rows are for one-son non-root nodes");
   const int LD = a.LD;
   const int pin = PINK == 0 ? -1 : a.pin[v];
   const uint64_t gv = a.geo[v];
@@ -297,11 +305,17 @@ __device__ __forceinline__ void dp_node(const DPArgs& a, const DevTables& s, con
     //   j in [p, q): j is the first least key of [p, q);
     //   j < p:       key[j] <= every key of (j, q);
     //   j >= q:      key[j] <  every key of [p, j).
-    const int c = a.child_list[cs];
-    const int dc = geo_dir(a.geo[c]);
+    int c, dc;
+    const double *Bc, *Mc, *Ac, *Ccc;
+    if constexpr (STAGED) {
+      c = so.c; dc = so.dc; Bc = so.B; Mc = so.M; Ac = so.A; Ccc = so.Cc;
+    } else {
+      c = a.child_list[cs];
+      dc = geo_dir(a.geo[c]);
+      Bc = a.B + int64_t(c) * LD; Mc = a.M + int64_t(c) * LD;
+      Ac = a.A + int64_t(c) * LD; Ccc = a.Cc + int64_t(c) * LD;
+    }
     const int nldc = s.nld[dc];
-    const double* Bc = a.B + int64_t(c) * LD;
-    const double* Mc = a.M + int64_t(c) * LD;
     long long key[LDM];
     int lcs[LDM];
 #pragma unroll
@@ -334,7 +348,8 @@ __device__ __forceinline__ void dp_node(const DPArgs& a, const DevTables& s, con
     for (int j = 0; j < LDM; ++j) {
       if ((cons >> j) & 1u) {
         const int b0 = min(lo_req, lcs[j]), t0 = max(hi_req, lcs[j]);
-        const long long f = dbits(__longlong_as_double(key[j]) + fma(s.kd[t0 - b0], sigma_v, z));
+        const double tail = (STAGED && PINK == 0) ? so.T[t0 - b0] : fma(s.kd[t0 - b0], sigma_v, z);
+        const long long f = dbits(__longlong_as_double(key[j]) + tail);
         if (stack_better(f, t0 - b0, b0, bfp, bk, bb)) { bfp = f; bk = t0 - b0; bb = b0; bt = t0; bj = j; }
       }
     }
@@ -344,8 +359,8 @@ __device__ __forceinline__ void dp_node(const DPArgs& a, const DevTables& s, con
     }
     const int lc = s.lay[dc][bj];
     a.ent[int64_t(c) * LD + ldi] = int8_t(lc);
-    sg = fma(Mc[bj], rvl[lc], a.A[int64_t(c) * LD + bj]);
-    sc = a.Cc[int64_t(c) * LD + bj];
+    sg = fma(Mc[bj], rvl[lc], Ac[bj]);
+    sc = Ccc[bj];
   } else {
     // Two or more sons: every stack [b, t] with b <= lo_req <= hi_req <= t;
     // S[t] accumulates, son by son in order, the son's least key in [b, t].
@@ -466,12 +481,46 @@ __global__ void __launch_bounds__(256, (DEG <= 1 ? 4 : 2)) k_dp_level(LayerInfo 
   __shared__ RoundTabs rt;
   load_round_tabs(rt, a, li.via_c);
   load_tables(s, a.tab);
-  const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  const int64_t node_i = ROOT ? k : k / a.LD;
-  const int ldi = ROOT ? 0 : int(k - node_i * a.LD);
-  if (node_i >= a.count) return;
-  dp_node<LMAX, LDM, DEG, ROOT, CACHED, PINK>(a, s, rt, li.L, int(a.base + node_i), ldi);
+  if constexpr (DEG == 1 && !ROOT) {
+    // whole nodes per block (256 / LD of them): the node's threads copy the
+    // son's table row to shared memory, one entry each per array
+    // (a node without a pin also tabulates its tail costs T(k), k < L, once)
+    __shared__ double s_son[4][256];
+    __shared__ double s_T[PINK == 0 ? 512 : 1];  // (256 / LD) nodes x L <= 512 since LD >= L / 2
+    const int LD = a.LD, npb = 256 / LD;
+    const int gi = int(threadIdx.x) / LD, ldi = int(threadIdx.x) - gi * LD;
+    const int64_t node_i = int64_t(blockIdx.x) * npb + gi;
+    const bool in = gi < npb && node_i < a.count;
+    const int v = int(a.base + (in ? node_i : 0));
+    Son1 so{};
+    if (in) {
+      so.c = a.child_list[a.child_start[v]];
+      so.dc = geo_dir(a.geo[so.c]);
+      const int64_t o = int64_t(so.c) * LD + ldi;
+      s_son[0][threadIdx.x] = a.B[o];
+      s_son[1][threadIdx.x] = a.M[o];
+      s_son[2][threadIdx.x] = a.A[o];
+      s_son[3][threadIdx.x] = a.Cc[o];
+      so.B = &s_son[0][gi * LD]; so.M = &s_son[1][gi * LD]; so.A = &s_son[2][gi * LD]; so.Cc = &s_son[3][gi * LD];
+      if constexpr (PINK == 0) {
+        const double sig = CACHED ? a.ncache[4 * int64_t(v) + 3] : fma(a.w_d * a.rho[v], li.via_c, a.sigma0);
+        double* T = &s_T[gi * li.L];
+        for (int k2 = ldi; k2 < li.L; k2 += LD) T[k2] = fma(double(k2), sig, 0.0);
+        so.T = T;
+      }
+    }
+    __syncthreads();
+    if (!in) return;
+    dp_node<LMAX, LDM, DEG, ROOT, CACHED, PINK, true>(a, s, rt, li.L, v, ldi, so);
+  } else {
+    const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int64_t node_i = ROOT ? k : k / a.LD;
+    const int ldi = ROOT ? 0 : int(k - node_i * a.LD);
+    if (node_i >= a.count) return;
+    dp_node<LMAX, LDM, DEG, ROOT, CACHED, PINK>(a, s, rt, li.L, int(a.base + node_i), ldi);
+  }
 }
+
 
 // Any node: pick its class at run time (used where classes mix).
 template <int LMAX, int LDM, bool CACHED>
@@ -620,8 +669,14 @@ __global__ void __launch_bounds__(256) k_backtrack_bignets(BtArgs a, BigArgs g) 
 template <int LMAX, int LDM, int DEG, bool ROOT, int PINK>
 static void dp_launch(la_ctx* c, const DPArgs& a, cudaStream_t s) {
   const int T = 256;
-  const int64_t threads = ROOT ? a.count : a.count * a.LD;
-  const unsigned B = (unsigned)((threads + T - 1) / T);
+  unsigned B;
+  if (DEG == 1 && !ROOT) {
+    const int64_t npb = T / a.LD;  // whole nodes per block
+    B = (unsigned)((a.count + npb - 1) / npb);
+  } else {
+    const int64_t threads = ROOT ? a.count : a.count * a.LD;
+    B = (unsigned)((threads + T - 1) / T);
+  }
   if (a.scache) k_dp_level<LMAX, LDM, DEG, ROOT, true, PINK><<<B, T, 0, s>>>(c->grid.li, a);
   else k_dp_level<LMAX, LDM, DEG, ROOT, false, PINK><<<B, T, 0, s>>>(c->grid.li, a);
   ++c->launches;
