@@ -126,6 +126,48 @@ def dp_algorithmic_flops(forest, dirs):
     return float(np.sum(LDv * per_layer + per_node))
 
 
+def nvtx_push(torch, name):
+    """Mark the timed region for profilers (ncu --nvtx --nvtx-include name/)."""
+    try:
+        torch.cuda.nvtx.range_push(name)
+    except Exception:
+        pass
+
+
+def nvtx_pop(torch):
+    try:
+        torch.cuda.nvtx.range_pop()
+    except Exception:
+        pass
+
+
+DP_SOURCES = ("paper_2507_13375_gb300/csrc/k_round.cu", "paper_2507_13375_gb300/csrc/gapla_internal.cuh")
+
+
+def dp_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for rel in DP_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def dp_traffic(workload_name):
+    """DRAM bytes of one round's DP phase from the committed ncu record, if it
+    was taken on the current kernel sources for this workload (else None)."""
+    p = os.path.join(ROOT, "profiles", "dp_traffic.json")
+    if not os.path.exists(p):
+        return None, "no capture record"
+    with open(p) as fh:
+        rec = json.load(fh)
+    if rec.get("workload") != workload_name:
+        return None, "capture record is for another workload"
+    if rec.get("source_sha256") != dp_source_hash():
+        return None, "kernels changed since the capture"
+    return float(rec["bytes_per_round"]), rec.get("how", "")
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -210,12 +252,14 @@ def bench_gpu(args):
     with ClockSampler(local) as clk:
         e_start, e_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e_start.record()
+        nvtx_push(torch, "bench_timed")
         stats = []
         adj = []
         for _ in range(args.steps):
             st, ad, _ = run_step(a, la, wl.rounds, mode, weights, True, torch)
             stats += st
             adj += ad
+        nvtx_pop(torch)
         e_end.record()
         torch.cuda.synchronize()
     if dist:
@@ -268,16 +312,20 @@ def bench_gpu(args):
     achieved = flops / (dp_ms * 1e-3) / 1e12
     hbm_peak, peak_src = measured_peaks()
     LD = max(sum(1 for d in wl.dirs if d == 0), sum(1 for d in wl.dirs if d == 1))
-    # algorithmic bytes of one DP pass: per node its own data (geometry 8 B, W
-    # and r_est 16 B, pin/caps 17 B, CSR 8 B); per candidate layer the two
-    # congestion prefixes (16 B) and its entry (A, Cc, M, B 32 B, stack 2 B);
-    # per son and son layer its entry read (M, B 16 B) and its choice byte.
-    dp_bytes = V * (8 + 16 + 17 + 8) + S * LD * (16 + 32 + 2) + N * 2 + S * LD * (16 + 1)
+    # algorithmic bytes of one DP pass of the batched form, each element once:
+    # per node its own data (geometry 8 B, the constant cache w_d W, w_d kappa,
+    # w_d r_est, sigma 32 B, pin and caps 17 B, CSR 8 B); per (segment, layer)
+    # the two congestion prefixes (16 B), the cached alpha, gamma, C (24 B), the
+    # entry written (A, Cc, M, B 32 B, stack 2 B), the parent's read of it
+    # (32 B) and the parent's choice byte; a root's stack (2 B).
+    dp_bytes = V * (8 + 32 + 17 + 8) + S * LD * (16 + 24 + 32 + 2 + 32 + 1) + N * 2
+    traffic, traffic_src = dp_traffic(wl.name)
     hbm_achieved = dp_bytes / (dp_ms * 1e-3) / 1e9
     roofline = {"kernel": "k_dp_level / k_dp_bignets (all levels of one round; in the batched form the phase "
                           "also holds the backtrack and the fused demand update)",
                 "bound": "alu", "achieved": round(achieved, 4), "peak": round(fp64_peak_tflops, 4),
-                "unit": "TFLOP/s", "frac": round(achieved / fp64_peak_tflops, 4), "traffic": None,
+                "unit": "TFLOP/s", "frac": round(achieved / fp64_peak_tflops, 4), "traffic": traffic,
+                "traffic_source": traffic_src,
                 "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk/SM x 2070 MHz x 2 flops (FP64 pipe)",
                 "algorithmic_flops_per_round": flops, "dp_ms_per_round": round(dp_ms, 4),
                 "hbm": {"achieved": round(hbm_achieved, 1), "peak": hbm_peak, "unit": "GB/s",
