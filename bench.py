@@ -126,6 +126,30 @@ def dp_algorithmic_flops(forest, dirs):
     return float(np.sum(LDv * per_layer + per_node))
 
 
+# --------------------------------------------------------------------------
+# multi-rank host logic (one process per GPU, independent replicas)
+# --------------------------------------------------------------------------
+def replica_seed(rank: int) -> int:
+    """Each replica generates its own grid and forest (weak scaling)."""
+    return rank
+
+
+def max_over_ranks(x: float, dist, device: str) -> float:
+    """The job's time is the slowest rank's (all-reduce MAX; no-op alone)."""
+    if dist is None:
+        return x
+    import torch
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world: int, units_per_rank: float, ms: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the max time."""
+    return world * units_per_rank / (ms * 1e-3)
+
+
 def nvtx_push(torch, name):
     """Mark the timed region for profilers (ncu --nvtx --nvtx-include name/)."""
     try:
@@ -215,9 +239,12 @@ def bench_gpu(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     dist = None
+    red_dev = "cuda"
     if world > 1:
         import torch.distributed as dist
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
+        red_dev = "cuda" if backend == "nccl" else "cpu"
     torch.cuda.set_device(local)
     __graft_entry__.build()
 
@@ -225,8 +252,8 @@ def bench_gpu(args):
     mode = la.LA_MODE_BATCHED if args.mode == "batched" else la.LA_MODE_PLAIN
     weights = dict(la.DEFAULT_WEIGHTS)
     t0 = time.time()
-    grid = fg.make_grid(wl, seed=rank)
-    forest = fg.make_forest(wl, seed=rank)
+    grid = fg.make_grid(wl, seed=replica_seed(rank))
+    forest = fg.make_forest(wl, seed=replica_seed(rank))
     gen_s = time.time() - t0
     N, V = wl.num_nets, int(forest["num_nodes"])
     S = V - N
@@ -265,15 +292,11 @@ def bench_gpu(args):
     if dist:
         dist.barrier()
     launches = a.launch_count() - launches0
-    step_ms = e_start.elapsed_time(e_end) / args.steps
-    if dist:
-        tt = torch.tensor([step_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        step_ms = float(tt.item())
+    step_ms = max_over_ranks(e_start.elapsed_time(e_end) / args.steps, dist, red_dev)
     adj_ms = sum(e0.elapsed_time(e1) for e0, e1 in adj) / max(len(adj), 1)
     dp_ms = statistics.mean(s["ms_dp"] for s in stats)
     rnd_ms = statistics.mean(s["ms"] for s in stats)
-    value = world * N * wl.rounds / (step_ms * 1e-3)
+    value = job_rate(world, N * wl.rounds, step_ms)
 
     # ---- end to end through the C ABI, inputs from pinned host memory ----
     keys = ("net_ptr", "x", "y", "parent", "pin_layer", "sink_cap", "kappa", "r_drv")
@@ -298,12 +321,8 @@ def bench_gpu(args):
             dst.copy_(src, non_blocking=True)
     e_end.record()
     torch.cuda.synchronize()
-    e2e_ms = e_start.elapsed_time(e_end) / e2e_steps
-    e2e_wall_ms = (time.perf_counter() - w0) * 1e3 / e2e_steps
-    if dist:
-        tt = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_ms = float(tt.item())
+    e2e_ms = max_over_ranks(e_start.elapsed_time(e_end) / e2e_steps, dist, red_dev)
+    e2e_wall_ms = max_over_ranks((time.perf_counter() - w0) * 1e3 / e2e_steps, dist, red_dev)
 
     # ---- roofline of the dominant kernel (the DP) ----
     # GB300 issues FP64 at 2 FMA/clk/SM: 152 SMs x 2 x 2070 MHz x 2 flops
@@ -345,8 +364,8 @@ def bench_gpu(args):
             pst += st_
         e_end.record()
         torch.cuda.synchronize()
-        p_ms = e_start.elapsed_time(e_end) / max(1, min(args.steps, 3))
-        plain = {"value": world * N * wl.rounds / (p_ms * 1e-3), "unit": "nets/s", "ms_per_step": round(p_ms, 3),
+        p_ms = max_over_ranks(e_start.elapsed_time(e_end) / max(1, min(args.steps, 3)), dist, red_dev)
+        plain = {"value": job_rate(world, N * wl.rounds, p_ms), "unit": "nets/s", "ms_per_step": round(p_ms, 3),
                  "dp_ms_per_round": round(statistics.mean(x["ms_dp"] for x in pst), 4),
                  "round_ms": round(statistics.mean(x["ms"] for x in pst), 4)}
 
@@ -360,7 +379,7 @@ def bench_gpu(args):
                    "weights": "Eq. 4 in round 0, adjoint sensitivities in later rounds",
                    "l2": "inputs larger than L2 (working set %.1f GB)" % (a.device_bytes() / 1e9),
                    "parallelism": f"replicas x{world}"},
-        "segments_per_s": world * S * wl.rounds / (step_ms * 1e-3),
+        "segments_per_s": job_rate(world, S * wl.rounds, step_ms),
         "phases_ms_per_round": {"round": round(rnd_ms, 4), "dp": round(dp_ms, 4),
                                 "backtrack": round(statistics.mean(s["ms_backtrack"] for s in stats), 4),
                                 "demand_scan": round(statistics.mean(s["ms_demand"] for s in stats), 4),
@@ -369,7 +388,7 @@ def bench_gpu(args):
         "batched_plan": ({k: stats[-1][k] for k in ("batch_split", "batch_block", "batch_big_nets", "batch_cached", "batch_trials", "batch_tune_ms")}
                          if args.mode == "batched" else None),
         "roofline": roofline,
-        "e2e": {"value": world * N * wl.rounds / (e2e_ms * 1e-3), "unit": "nets/s", "h2d_bytes_per_step": int(h2d),
+        "e2e": {"value": job_rate(world, N * wl.rounds, e2e_ms), "unit": "nets/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "ms_per_step": round(e2e_ms, 3),
                 "wall_ms_per_step": round(e2e_wall_ms, 3)},
         "gpu_launches": int(launches),

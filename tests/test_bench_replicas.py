@@ -1,0 +1,62 @@
+"""The multi-GPU form of the bench is N independent replicas (one process per
+GPU, seed = rank, no data-path collective): its host logic on 2 gloo ranks on
+the CPU - max-over-ranks timing, whole-job throughput, one forest per rank -
+and the reference arm's ranks other than 0 exiting without work."""
+import json
+import os
+import socket
+import subprocess
+import sys
+
+import numpy as np
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port() -> int:
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+
+    import bench
+    import forestgen as fg
+
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    local_ms = 100.0 + 50.0 * rank
+    m = bench.max_over_ranks(local_ms, dist, "cpu")
+    value = bench.job_rate(world, 1000.0, m)
+    wl = fg.WORKLOADS[1].scaled(40)
+    f = fg.make_forest(wl, bench.replica_seed(rank))
+    sig = [int(f["num_nodes"]), int(np.sum(f["x"].astype(np.int64) * 31 + f["y"]))]
+    sigs = [None] * world
+    dist.all_gather_object(sigs, sig)
+    if rank == 0:
+        with open(out, "w") as fh:
+            json.dump({"max_ms": m, "value": value, "sigs": sigs}, fh)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_replicas_on_two_gloo_ranks(tmp_path):
+    out = str(tmp_path / "r.json")
+    mp.spawn(_worker, args=(2, _free_port(), out), nprocs=2, join=True)
+    with open(out) as fh:
+        r = json.load(fh)
+    assert r["max_ms"] == 150.0                     # the slower rank's time
+    assert r["value"] == 2 * 1000.0 / 0.150         # units of both ranks over it
+    assert r["sigs"][0] != r["sigs"][1]             # each replica its own forest
+
+
+def test_reference_arm_other_ranks_exit_without_work():
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    p = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "3"], env=env, capture_output=True, text=True, timeout=120)
+    assert p.returncode == 0
+    assert p.stdout.strip() == ""
