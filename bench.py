@@ -341,7 +341,7 @@ def bench_gpu(args):
     traffic, traffic_src = dp_traffic(wl.name)
     hbm_achieved = dp_bytes / (dp_ms * 1e-3) / 1e9
     roofline = {"kernel": "k_dp_level / k_dp_bignets (all levels of one round; in the batched form the phase "
-                          "also holds the backtrack and the fused demand update)",
+                          "also holds the backtrack)",
                 "bound": "alu", "achieved": round(achieved, 4), "peak": round(fp64_peak_tflops, 4),
                 "unit": "TFLOP/s", "frac": round(achieved / fp64_peak_tflops, 4), "traffic": traffic,
                 "traffic_source": traffic_src,
