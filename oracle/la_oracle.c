@@ -15,7 +15,7 @@
  *     f' is kept (Kernel 2);
  *   - no blocking, fusion or reordering.  Threads only split the nets.
  *
- * Exact readings (where the paper is silent) - all restated in the design doc:
+ * Exact readings (where the paper is silent):
  *   Tree / RC model.  Non-root v has a straight segment e_v of length len_v
  *   (GCell edges) to its parent.  On layer l: R_v(l) = len_v r_l,
  *   C_v(l) = len_v c_l, pi-model (half the cap at each end, Sec. III-B).
