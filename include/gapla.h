@@ -119,7 +119,10 @@ typedef struct {
  * builds the children lists, segment geometry, and the Eq. 4 edge weights W
  * and the look-ahead upstream resistances r_est (Sec. III-D).  Synchronises
  * the stream.  LA_ERR_INVALID if the forest is malformed (message names the
- * first bad node). */
+ * first bad node); the forest loaded before stays loaded.  After any other
+ * error the context holds no forest.  A forest of the same shape as the one
+ * before reuses its device blocks and, with the batched form, its tuned plan
+ * and captured rounds. */
 la_status la_load_nets(la_ctx* ctx, const la_net_desc* nets);
 
 /* ---------------------------------------------------------------------------

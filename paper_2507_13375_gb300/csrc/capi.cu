@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <utility>
 #include <vector>
 
@@ -52,21 +53,71 @@ struct DeviceGuard {
   }
 };
 
-// Device allocations of one load (grid or forest), freed together.
+// FNV-1a over the 8 bytes of x.
+uint64_t fnv_mix(uint64_t h, uint64_t x) {
+  for (int i = 0; i < 8; ++i) {
+    h ^= (x >> (8 * i)) & 0xffu;
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+// Freed device blocks kept for reuse, by exact size.  A reload of a forest of
+// the same shape takes every block back (first in, first out among equal
+// sizes, so the arrays land at the same addresses), and nothing is allocated
+// or freed; a block that stays unused through a whole load is freed.
+struct DevPool {
+  struct Blk {
+    void* p;
+    uint64_t gen;
+  };
+  std::multimap<size_t, Blk> blocks;
+  uint64_t gen = 0;
+  void* take(size_t b) {
+    auto it = blocks.lower_bound(b);
+    if (it == blocks.end() || it->first != b) return nullptr;
+    void* p = it->second.p;
+    blocks.erase(it);
+    return p;
+  }
+  void put(void* p, size_t b) { blocks.emplace(b, Blk{p, gen}); }
+  void free_older_than(uint64_t g) {
+    for (auto it = blocks.begin(); it != blocks.end();) {
+      if (it->second.gen < g) {
+        cudaFree(it->second.p);
+        it = blocks.erase(it);
+      } else {
+        ++it;
+      }
+    }
+  }
+  void clear() { free_older_than(UINT64_MAX); }
+};
+
+// Device allocations of one load (grid or forest), released together (into
+// the pool when there is one).
 struct Allocs {
   std::vector<std::pair<void*, size_t>> list;
   size_t bytes = 0;
+  DevPool* pool = nullptr;
   template <typename T>
   la_status get(la_ctx* c, T** p, size_t n) {
     size_t b = n * sizeof(T);
     if (b == 0) b = 16;
     b = (b + 255) & ~size_t(255);
-    void* q = nullptr;
-    cudaError_t e = cudaMalloc(&q, b);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      *p = nullptr;
-      return set_err(c, LA_ERR_OOM, "device allocation of %zu bytes failed: %s", b, cudaGetErrorString(e));
+    void* q = pool ? pool->take(b) : nullptr;
+    if (!q) {
+      cudaError_t e = cudaMalloc(&q, b);
+      if (e == cudaErrorMemoryAllocation && pool && !pool->blocks.empty()) {
+        cudaGetLastError();
+        pool->clear();  // give the pooled blocks back and try once more
+        e = cudaMalloc(&q, b);
+      }
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return set_err(c, LA_ERR_OOM, "device allocation of %zu bytes failed: %s", b, cudaGetErrorString(e));
+      }
     }
     list.emplace_back(q, b);
     bytes += b;
@@ -74,7 +125,10 @@ struct Allocs {
     return LA_OK;
   }
   void release() {
-    for (auto& x : list) cudaFree(x.first);
+    for (auto& x : list) {
+      if (pool) pool->put(x.first, x.second);
+      else cudaFree(x.first);
+    }
     list.clear();
     bytes = 0;
   }
@@ -86,7 +140,9 @@ void gapla::set_noctx_error(const std::string& msg) { g_create_err = msg; }
 
 // Allocation groups live beside the context (kept out of the shared header).
 struct la_ctx_allocs {
+  DevPool pool;
   Allocs grid, forest;
+  la_ctx_allocs() { grid.pool = forest.pool = &pool; }
 };
 static la_ctx_allocs* allocs_of(la_ctx* c) { return reinterpret_cast<la_ctx_allocs*>(c->alloc_groups); }
 
@@ -175,6 +231,7 @@ la_status la_destroy(la_ctx* c) {
   if (la_ctx_allocs* a = allocs_of(c)) {
     a->forest.release();
     a->grid.release();
+    a->pool.clear();
     delete a;
   }
   if (c->d_err) cudaFree(c->d_err);
@@ -202,7 +259,9 @@ la_status la_set_stream(la_ctx* c, void* stream) {
 la_status la_device_bytes(const la_ctx* c, size_t* bytes) {
   if (!c || !bytes) return LA_ERR_INVALID;
   la_ctx_allocs* a = allocs_of(const_cast<la_ctx*>(c));
-  *bytes = a->grid.bytes + a->forest.bytes + sizeof(Stats) + sizeof(unsigned long long);
+  size_t pooled = 0;
+  for (const auto& kv : a->pool.blocks) pooled += kv.first;
+  *bytes = a->grid.bytes + a->forest.bytes + pooled + sizeof(Stats) + sizeof(unsigned long long);
   return LA_OK;
 }
 
@@ -376,9 +435,19 @@ la_status la_load_nets(la_ctx* c, const la_net_desc* nd) {
   tf.N = nf.N = nd->num_nets;
   tf.V = nf.V = nd->num_nodes;
   const size_t N = size_t(nf.N), V = size_t(nf.V);
+  la_ctx_allocs* al = allocs_of(c);
+  const uint64_t gen0 = ++al->pool.gen;
   Allocs na, ta;  // kept / temporary
+  na.pool = ta.pool = &al->pool;
+  BatchPlan old_plan;  // the old forest's plan, once the old forest is released
   la_status st = LA_OK;
-  auto fail = [&](la_status s2) { na.release(); ta.release(); return s2; };
+  auto fail = [&](la_status s2) {
+    na.release();
+    ta.release();
+    for (auto& e2 : old_plan.exec)
+      if (e2) cudaGraphExecDestroy(e2);
+    return s2;
+  };
   auto cuda_fail = [&]() { return fail(set_err(c, LA_ERR_CUDA, "la_load_nets: %s", cudaGetErrorString(cudaGetLastError()))); };
 #define GETK(p, n) if (st == LA_OK) st = na.get(c, &(p), (n))
 #define GETT(p, n) if (st == LA_OK) st = ta.get(c, &(p), (n))
@@ -399,6 +468,13 @@ la_status la_load_nets(la_ctx* c, const la_net_desc* nd) {
   if ((st = read_dev_err(c, &code, &idx))) return fail(st);
   if (code) return fail(set_err(c, LA_ERR_INVALID, "la_load_nets: %s (%s %lld)", dev_err_name(code),
                                  code == DE_NETPTR ? "net" : "node", idx));
+  // The input is valid: the old forest's blocks go back to the pool, where the
+  // new forest's arrays find them (same shape: same blocks, same addresses).
+  // Its batched plan is kept aside until the new forest's plan is known.
+  old_plan = c->plan;
+  c->plan = BatchPlan();
+  al->forest.release();
+  c->forest = Forest();
   int hmax = 0;
   if (cudaMemcpy(&hmax, d_hmax, sizeof hmax, cudaMemcpyDeviceToHost)) return cuda_fail();
   nf.Hmax = tf.Hmax = hmax;
@@ -419,6 +495,8 @@ la_status la_load_nets(la_ctx* c, const la_net_desc* nd) {
     return cuda_fail();
   nf.key_off.assign(nbk + 1, 0);
   for (size_t k = 0; k < nbk; ++k) nf.key_off[k + 1] = nf.key_off[k] + cnt[k];
+  nf.key_hash = 1469598103934665603ull;
+  for (int64_t x : nf.key_off) nf.key_hash = fnv_mix(nf.key_hash, uint64_t(x));
   nf.lvl_off.assign(hmax + 2, 0);
   for (int h = 0; h <= hmax + 1; ++h) nf.lvl_off[h] = nf.key_off[size_t(bucket_key(h, 0, 0))];
   if (cudaMemcpyAsync(d_cur, nf.key_off.data(), sizeof(int64_t) * nbk, cudaMemcpyHostToDevice, s)) return cuda_fail();
@@ -485,15 +563,22 @@ la_status la_load_nets(la_ctx* c, const la_net_desc* nd) {
   ++c->launches;
   if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) return cuda_fail();
   ta.release();
-  // success: replace the forest (and forget the batched plan of the old one)
-  for (auto& e2 : c->plan.exec)
-    if (e2) cudaGraphExecDestroy(e2);
-  c->plan = BatchPlan();
-  la_ctx_allocs* a = allocs_of(c);
-  a->forest.release();
-  a->forest = na;
+  al->pool.free_older_than(gen0);  // blocks no load took since the last one
+  al->forest = na;
   c->forest = nf;
   plan_from_memo(c);
+  // A plan taken from the memo keeps the old graphs: each replays only if the
+  // addresses and shapes it was captured with are unchanged (round_signature).
+  for (int i = 0; i < 2; ++i) {
+    if (c->plan.tuned && old_plan.exec[i]) {
+      c->plan.exec[i] = old_plan.exec[i];
+      c->plan.graph_launches[i] = old_plan.graph_launches[i];
+      c->plan.graph_sig[i] = old_plan.graph_sig[i];
+      for (int j = 0; j < 5; ++j) c->plan.w[i][j] = old_plan.w[i][j];
+    } else if (old_plan.exec[i]) {
+      cudaGraphExecDestroy(old_plan.exec[i]);
+    }
+  }
   return LA_OK;
 }
 
@@ -505,6 +590,27 @@ static la_status check_loaded(la_ctx* c) {
 }
 
 // ---- batched form ----
+// Everything a captured round bakes in: the device addresses it reads and
+// writes, the forest's shape and the plan.  A graph replays only while this
+// is unchanged (a reload of a same-shaped forest gets the same addresses back
+// from the pool and keeps its graphs).
+static uint64_t round_signature(la_ctx* c, int si) {
+  const Forest& f = c->forest;
+  const Grid& g = c->grid;
+  const BatchPlan& bp = c->plan;
+  const void* ptrs[] = {f.bl_nodes, f.bl_hoff, f.net_H, f.big_queue, f.queue_ctr, f.net_ptr, f.root_of_net,
+                        f.parent_g, f.net_of, f.pin, f.sink_cap, f.kappa, f.gk, f.r_drv, f.geo, f.child_start,
+                        f.nch, f.child_list, f.W_eq4, f.rho_eq4, f.W_adj, f.rho_adj, f.A, f.Cc, f.M, f.B,
+                        f.ncache[si], f.scache[si], f.sb, f.st, f.ent, f.Jroot, f.layer, f.b, f.t, f.red,
+                        g.cap, g.D, g.H, g.diff, g.P, g.T_dev, g.tofT_dev, g.tab_dev, c->d_stats, c->d_err};
+  uint64_t h = 1469598103934665603ull;
+  for (const void* q : ptrs) h = fnv_mix(h, uint64_t(reinterpret_cast<uintptr_t>(q)));
+  const int64_t vals[] = {f.N, f.V, f.Hmax, f.red_cap, c->LD, bp.k, bp.block, bp.grid, bp.cached ? 1 : 0,
+                          bp.n_big, bp.Hs, int64_t(f.key_hash)};
+  for (int64_t x : vals) h = fnv_mix(h, uint64_t(x));
+  return h;
+}
+
 static BatchPlan make_plan(la_ctx* c, int k, int block, bool one_per_sm) {
   Forest& f = c->forest;
   BatchPlan bp;
@@ -653,7 +759,8 @@ static la_status batched_graph(la_ctx* c, const RoundW& w, const double* W, cons
   BatchPlan& bp = c->plan;
   cudaStream_t s = c->s_cap;
   const double wv[5] = {w.w_cong, w.w_via, w.w_cap, w.w_d, w.hist_w};
-  bool same = bp.exec[si] != nullptr;
+  const uint64_t sig = round_signature(c, si);
+  bool same = bp.exec[si] != nullptr && bp.graph_sig[si] == sig;
   for (int i = 0; i < 5 && same; ++i) same = bp.w[si][i] == wv[i];
   if (!same) {
     if (bp.exec[si]) {
@@ -688,6 +795,7 @@ static la_status batched_graph(la_ctx* c, const RoundW& w, const double* W, cons
     cudaGraphDestroy(g);
     if (ei != cudaSuccess) return set_err(c, LA_ERR_CUDA, "la_assign_round: graph instantiate: %s", cudaGetErrorString(ei));
     bp.graph_launches[si] = c->launches - l0;
+    bp.graph_sig[si] = sig;
     c->launches = l0;
     for (int i = 0; i < 5; ++i) bp.w[si][i] = wv[i];
   }

@@ -111,6 +111,7 @@ struct Forest {
   int Hmax = 0;                         // max height (levels 0..Hmax)
   std::vector<int64_t> lvl_off;         // host copy: level h is [lvl_off[h], lvl_off[h+1])
   std::vector<int64_t> key_off;         // host copy: offsets of the (level, class, size class) buckets
+  uint64_t key_hash = 0;                // hash of key_off (a captured round depends on it)
   // Per-net level lists of the nets with size class >= kMinBigSc (input-order
   // slots of the net: bl_nodes[base + j] is the internal id of its j-th node
   // by height; bl_hoff[base + n + h] the start of height h, relative to base).
@@ -209,6 +210,7 @@ struct BatchPlan {
   cudaGraphExec_t exec[2] = {nullptr, nullptr};
   double w[2][5] = {{0, 0, 0, 0, 0}, {0, 0, 0, 0, 0}};  // what each graph was captured with
   long long graph_launches[2] = {0, 0};
+  uint64_t graph_sig[2] = {0, 0};  // the device addresses and shapes each graph was captured with
   double cache_wd[2] = {-1.0, -1.0}, cache_wcap[2] = {-1.0, -1.0};
 };
 

@@ -327,6 +327,19 @@ def test_batched_reload_reuses_tuning(la):
     for p, q in zip(first, again):
         for k in ("layer", "b", "t", "D", "H", "J"):
             assert np.array_equal(p[k], q[k]), k
+    # same trees, other caps and criticalities: the memo matches, the captured
+    # rounds replay on the new values, and they still equal the plain form
+    vals = dict(forest)
+    vals["kappa"] = forest["kappa"] * 0.5
+    vals["sink_cap"] = forest["sink_cap"] * 1.5
+    a.load_nets(vals)
+    rb = _rounds(a, la, la.LA_MODE_BATCHED, 2, adjoint=True)
+    assert rb[0]["stats"]["batch_trials"] == 0
+    rp = _rounds(a, la, la.LA_MODE_PLAIN, 2, adjoint=True)
+    for p, q in zip(rb, rp):
+        for k in ("layer", "b", "t", "D", "H", "J"):
+            assert np.array_equal(p[k], q[k]), k
+    assert not np.array_equal(rb[0]["J"], first[0]["J"])
     other = fg.make_forest(wl, 4)
     a.load_nets(other)
     st = a.assign_round(mode=la.LA_MODE_BATCHED, reset=True, **la.DEFAULT_WEIGHTS)
