@@ -262,7 +262,7 @@ struct Son1 {
 };
 template <int LMAX, int LDM, int DEG, bool ROOT, bool CACHED, int PINK, bool STAGED = false>
 __device__ __forceinline__ void dp_node(const DPArgs& a, const DevTables& s, const RoundTabs& rt, int L, int v,
-                                        int ldi, const Son1& so = Son1{}) {
+                                        int ldi, const Son1& so = Son1{}, long long* keybuf = nullptr) {
   static_assert(!STAGED || (DEG == 1 && !ROOT), "staged son rows are for one-son non-root nodes");
   const int LD = a.LD;
   const int pin = PINK == 0 ? -1 : a.pin[v];
@@ -364,6 +364,10 @@ __device__ __forceinline__ void dp_node(const DPArgs& a, const DevTables& s, con
   } else {
     // Two or more sons: every stack [b, t] with b <= lo_req <= hi_req <= t;
     // S[t] accumulates, son by son in order, the son's least key in [b, t].
+    // A son's keys are computed on its own direction's layers only and put
+    // in shared memory by layer, [t][thread] (conflict-free), for the scan
+    // over t (keybuf: LMAX x 256 entries, from the kernel).
+    long long* keyL = keybuf + threadIdx.x;
     const int nc = a.nch[v];
     int bk = INT_MAX;
     for (int b = 0; b <= lo_req; ++b) {
@@ -373,18 +377,24 @@ __device__ __forceinline__ void dp_node(const DPArgs& a, const DevTables& s, con
       for (int t = 0; t < LMAX; ++t) { S[t] = 0.0; ok[t] = true; }
       for (int j = 0; j < nc; ++j) {
         const int c = a.child_list[cs + j];
-        const uint32_t mask = s.mask[geo_dir(a.geo[c])];
+        const int dc = geo_dir(a.geo[c]);
+        const int nldc = s.nld[dc];
         const double* Bc = a.B + int64_t(c) * LD;
         const double* Mc = a.M + int64_t(c) * LD;
+#pragma unroll
+        for (int t = 0; t < LMAX; ++t) keyL[t * 256] = LLONG_MAX;
+#pragma unroll
+        for (int jj = 0; jj < LDM; ++jj) {
+          if (jj < nldc) {
+            const int lc = s.lay[dc][jj];
+            keyL[lc * 256] = dbits(fma(Mc[jj], rvl[lc], Bc[jj]));
+          }
+        }
         long long rbits = LLONG_MAX;
 #pragma unroll
         for (int lc = 0; lc < LMAX; ++lc) {
           if (lc < L && lc >= b) {
-            if ((mask >> lc) & 1u) {
-              const int jj = s.ld_of[lc];
-              const long long kb = dbits(fma(Mc[jj], rvl[lc], Bc[jj]));
-              if (kb < rbits) rbits = kb;
-            }
+            rbits = min(rbits, keyL[lc * 256]);
             if (lc >= hi_req) {
               if (rbits == LLONG_MAX) ok[lc] = false;
               else S[lc] = j == 0 ? __longlong_as_double(rbits) : S[lc] + __longlong_as_double(rbits);
@@ -400,30 +410,35 @@ __device__ __forceinline__ void dp_node(const DPArgs& a, const DevTables& s, con
         }
       }
     }
-    // each son's layer inside the winning stack
+    // each son's layer inside the winning stack (its own layers, ascending:
+    // the lowest layer wins ties)
     for (int j = 0; j < nc; ++j) {
       const int c = a.child_list[cs + j];
-      const uint32_t mask = s.mask[geo_dir(a.geo[c])];
+      const int dc = geo_dir(a.geo[c]);
+      const int nldc = s.nld[dc];
       const double* Bc = a.B + int64_t(c) * LD;
       const double* Mc = a.M + int64_t(c) * LD;
       long long rbits = LLONG_MAX;
-      int rl = -1;
+      int rj = -1;
 #pragma unroll
-      for (int lc = 0; lc < LMAX; ++lc) {
-        if (lc >= bb && lc <= bt && ((mask >> lc) & 1u)) {
-          const long long kb = dbits(fma(Mc[s.ld_of[lc]], rvl[lc], Bc[s.ld_of[lc]]));
-          if (rl < 0 || kb < rbits) { rl = lc; rbits = kb; }
+      for (int jj = 0; jj < LDM; ++jj) {
+        if (jj < nldc) {
+          const int lc = s.lay[dc][jj];
+          if (lc >= bb && lc <= bt) {
+            const long long kb = dbits(fma(Mc[jj], rvl[lc], Bc[jj]));
+            if (rj < 0 || kb < rbits) { rj = jj; rbits = kb; }
+          }
         }
       }
-      if (rl < 0) {  // cannot happen for a valid stack; report instead of indexing with -1
+      if (rj < 0) {  // cannot happen for a valid stack; report instead of indexing with -1
         dev_error(a.err, DE_NOSTACK, v);
         return;
       }
-      const int jj = s.ld_of[rl];
+      const int rl = s.lay[dc][rj];
       a.ent[int64_t(c) * LD + ldi] = int8_t(rl);
-      const double g = fma(Mc[jj], rvl[rl], a.A[int64_t(c) * LD + jj]);
+      const double g = fma(Mc[rj], rvl[rl], a.A[int64_t(c) * LD + rj]);
       sg = j == 0 ? g : sg + g;
-      sc = j == 0 ? a.Cc[int64_t(c) * LD + jj] : sc + a.Cc[int64_t(c) * LD + jj];
+      sc = j == 0 ? a.Cc[int64_t(c) * LD + rj] : sc + a.Cc[int64_t(c) * LD + rj];
     }
   }
 
@@ -513,28 +528,31 @@ __global__ void __launch_bounds__(256, (DEG <= 1 ? 4 : 2)) k_dp_level(LayerInfo 
     if (!in) return;
     dp_node<LMAX, LDM, DEG, ROOT, CACHED, PINK, true>(a, s, rt, li.L, v, ldi, so);
   } else {
+    // a node's candidate layers side by side (they share its sons' rows)
     const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     const int64_t node_i = ROOT ? k : k / a.LD;
     const int ldi = ROOT ? 0 : int(k - node_i * a.LD);
     if (node_i >= a.count) return;
-    dp_node<LMAX, LDM, DEG, ROOT, CACHED, PINK>(a, s, rt, li.L, int(a.base + node_i), ldi);
+    __shared__ long long s_keyL[DEG == 2 ? LMAX * 256 : 1];
+    dp_node<LMAX, LDM, DEG, ROOT, CACHED, PINK>(a, s, rt, li.L, int(a.base + node_i), ldi, Son1{}, s_keyL);
   }
 }
 
 
 // Any node: pick its class at run time (used where classes mix).
 template <int LMAX, int LDM, bool CACHED>
-__device__ void dp_node_any(const DPArgs& a, const DevTables& s, const RoundTabs& rt, int L, int v, int ldi) {
+__device__ void dp_node_any(const DPArgs& a, const DevTables& s, const RoundTabs& rt, int L, int v, int ldi,
+                            long long* keybuf) {
   const int nc = a.nch[v];
   if (a.parent_g[v] < 0) {
     if (ldi != 0) return;
     if (nc == 0) dp_node<LMAX, LDM, 0, true, CACHED, 2>(a, s, rt, L, v, 0);
     else if (nc == 1) dp_node<LMAX, LDM, 1, true, CACHED, 2>(a, s, rt, L, v, 0);
-    else dp_node<LMAX, LDM, 2, true, CACHED, 2>(a, s, rt, L, v, 0);
+    else dp_node<LMAX, LDM, 2, true, CACHED, 2>(a, s, rt, L, v, 0, Son1{}, keybuf);
   } else {
     if (nc == 0) dp_node<LMAX, LDM, 0, false, CACHED, 2>(a, s, rt, L, v, ldi);
     else if (nc == 1) dp_node<LMAX, LDM, 1, false, CACHED, 2>(a, s, rt, L, v, ldi);
-    else dp_node<LMAX, LDM, 2, false, CACHED, 2>(a, s, rt, L, v, ldi);
+    else dp_node<LMAX, LDM, 2, false, CACHED, 2>(a, s, rt, L, v, ldi, Son1{}, keybuf);
   }
 }
 
@@ -574,6 +592,7 @@ __global__ void __launch_bounds__(256) k_dp_bignets(LayerInfo li, DPArgs a, BigA
   __shared__ DevTables s;
   __shared__ RoundTabs rt;
   __shared__ int s_q;
+  __shared__ long long s_keyL[LMAX * 256];  // blockDim <= 256
   load_round_tabs(rt, a, li.via_c);
   load_tables(s, a.tab);
   const int LD = a.LD;
@@ -590,7 +609,7 @@ __global__ void __launch_bounds__(256) k_dp_bignets(LayerInfo li, DPArgs a, BigA
     for (int h = 0; h <= H; ++h) {
       const int lo = ho[h], cnt = ho[h + 1] - lo;
       for (int t = threadIdx.x; t < cnt * LD; t += blockDim.x)
-        dp_node_any<LMAX, LDM, CACHED>(a, s, rt, li.L, g.bl_nodes[base + lo + t / LD], t % LD);
+        dp_node_any<LMAX, LDM, CACHED>(a, s, rt, li.L, g.bl_nodes[base + lo + t / LD], t % LD, s_keyL);
       __syncthreads();
     }
   }
