@@ -1067,9 +1067,16 @@ la_status la_reweight_adjoint(la_ctx* c) {
   TRY(check_assigned(c));
   DeviceGuard g(c->device);
   Forest& f = c->forest;
-  // R and C of the assignment in scratch s3/s4; the adjoint with g = kappa at pins
-  launch_rc_from_assignment(c, f.s3, f.s4, nullptr, c->stream);
-  launch_elmore_bwd(c, f.s3, f.s4, f.gk, nullptr, nullptr, f.W_adj, f.rho_adj, c->stream);
+  // The adjoint with g = kappa at pins: W = Ws (the kappa sums below, which
+  // depend on the forest only: computed once per forest) and r_est = U (the
+  // top-down pass over the current assignment's R).
+  if (!f.wsum_valid) {
+    launch_rc_from_assignment(c, f.s3, f.s4, nullptr, c->stream);
+    launch_elmore_bwd(c, f.s3, f.s4, f.gk, nullptr, nullptr, f.W_adj, f.rho_adj, c->stream);
+    f.wsum_valid = true;
+  } else {
+    launch_elmore_adj_only(c, f.W_adj, f.rho_adj, c->stream);
+  }
   CK(cudaGetLastError());
   f.have_adj = true;
   return LA_OK;

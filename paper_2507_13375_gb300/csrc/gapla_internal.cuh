@@ -146,6 +146,7 @@ struct Forest {
   double* W_adj = nullptr;
   double* rho_adj = nullptr;
   bool have_adj = false;
+  bool wsum_valid = false;              // W_adj holds the kappa sums below each node (fixed per forest)
   // round tables
   double* A = nullptr;                  // [V][LD]
   double* Cc = nullptr;
@@ -306,6 +307,9 @@ void launch_rc_from_assignment(la_ctx* c, double* R, double* C, const int32_t* p
 void launch_elmore_fwd(la_ctx* c, const double* R, const double* C, double* delay, cudaStream_t s);
 void launch_elmore_bwd(la_ctx* c, const double* R, const double* C, const double* g, double* dR,
                        double* dC, double* Wsum_out, double* UJ_out, cudaStream_t s);
+// Top-down pass only: U from Ws (given) and R_seg = len x unit R of the
+// assignment's layer (the expression of la_rc_from_assignment), into UJ_out.
+void launch_elmore_adj_only(la_ctx* c, const double* Ws, double* UJ_out, cudaStream_t s);
 
 // error message of calls that have no context (read by la_last_error(NULL))
 void set_noctx_error(const std::string& msg);

@@ -37,6 +37,7 @@ void launch_rc_from_assignment(la_ctx* c, double* R, double* C, const int32_t* p
 
 struct ElmArgs {
   const int32_t *parent_g, *child_start, *nch, *child_list, *net_of;
+  const uint64_t* geo;  // k_elm_adj with R == null: R_seg from the geometry and the layer
   int64_t base, count;
   const int8_t *layer, *b, *t, *pin;
   const double *sink_cap, *r_drv, *R, *C, *g;
@@ -98,8 +99,10 @@ __global__ void k_elm_adj(ElmArgs a) {
     return;
   }
   const double w = a.Ws[v];
-  const double UX = a.UJ[p] + a.tab->rv[a.layer[p] * kMaxL + a.layer[v]] * w;
-  const double uj = UX + a.R[v] * w;
+  const int lv = a.layer[v];
+  const double Rv = a.R ? a.R[v] : double(geo_len(a.geo[v])) * a.tab->unit_r[lv];
+  const double UX = a.UJ[p] + a.tab->rv[a.layer[p] * kMaxL + lv] * w;
+  const double uj = UX + Rv * w;
   a.UJ[v] = uj;
   if (a.dR) {
     a.dR[v] = a.CdJ[v] * w;
@@ -112,7 +115,7 @@ static ElmArgs elm_args(la_ctx* c, const double* R, const double* C) {
   ElmArgs a{};
   a.parent_g = f.parent_g; a.child_start = f.child_start; a.nch = f.nch; a.child_list = f.child_list;
   a.net_of = f.net_of; a.layer = f.layer; a.b = f.b; a.t = f.t; a.pin = f.pin; a.sink_cap = f.sink_cap;
-  a.r_drv = f.r_drv; a.R = R; a.C = C; a.tab = c->grid.tab_dev;
+  a.r_drv = f.r_drv; a.R = R; a.C = C; a.tab = c->grid.tab_dev; a.geo = f.geo;
   return a;
 }
 
@@ -148,6 +151,13 @@ void launch_elmore_bwd(la_ctx* c, const double* R, const double* C, const double
   a.dR = dR;
   a.dC = dC;
   per_level(c, a, k_elm_up, true, s);
+  per_level(c, a, k_elm_adj, false, s);
+}
+
+void launch_elmore_adj_only(la_ctx* c, const double* Ws, double* UJ_out, cudaStream_t s) {
+  ElmArgs a = elm_args(c, nullptr, nullptr);
+  a.Ws = const_cast<double*>(Ws);
+  a.UJ = UJ_out;
   per_level(c, a, k_elm_adj, false, s);
 }
 
