@@ -408,6 +408,7 @@ la_status la_load_grid(la_ctx* c, const la_grid_desc* gd) {
   a->grid.release();
   c->forest = Forest();
   a->grid = na;
+  ng.fused_scan = prepare_fused_scan(ng.li);
   c->grid = ng;
   c->grid.loaded = true;
   c->grid.P_valid = false;
@@ -561,6 +562,37 @@ la_status la_load_nets(la_ctx* c, const la_net_desc* nd) {
   }
   launch_renumber(tf, in2int, nf, s);
   ++c->launches;
+  {
+    // the segments by (direction, line), for the demand pass
+    const int nl0 = c->grid.li.nlines[0], nkeys = nl0 + c->grid.li.nlines[1];
+    const size_t S = size_t(nf.V - nf.N);
+    int32_t* d_scnt = nullptr;
+    int64_t* d_scur = nullptr;
+    if ((st = ta.get(c, &d_scnt, size_t(nkeys))) || (st = ta.get(c, &d_scur, size_t(nkeys))) ||
+        (st = na.get(c, &nf.seg_node, std::max<size_t>(S, 1))) || (st = na.get(c, &nf.seg_geo, std::max<size_t>(S, 1))))
+      return fail(st);
+    if (cudaMemsetAsync(d_scnt, 0, sizeof(int32_t) * nkeys, s)) return cuda_fail();
+    launch_seg_sort(nf, nl0, d_scnt, nullptr, nullptr, nullptr, s);
+    std::vector<int32_t> scnt(nkeys);
+    if (cudaMemcpyAsync(scnt.data(), d_scnt, sizeof(int32_t) * nkeys, cudaMemcpyDeviceToHost, s) ||
+        cudaStreamSynchronize(s))
+      return cuda_fail();
+    std::vector<int64_t> scur(nkeys);
+    int64_t acc = 0;
+    for (int k = 0; k < nkeys; ++k) {
+      scur[k] = acc;
+      acc += scnt[k];
+    }
+    if (acc != int64_t(S)) return fail(set_err(c, LA_ERR_STATE, "la_load_nets: segment count mismatch"));
+    scur.push_back(acc);
+    if ((st = na.get(c, &nf.seg_off, size_t(nkeys) + 1))) return fail(st);
+    if (cudaMemcpyAsync(nf.seg_off, scur.data(), sizeof(int64_t) * (nkeys + 1), cudaMemcpyHostToDevice, s) ||
+        cudaMemcpyAsync(d_scur, scur.data(), sizeof(int64_t) * nkeys, cudaMemcpyHostToDevice, s))
+      return cuda_fail();
+    launch_seg_sort(nf, nl0, nullptr, d_scur, nf.seg_node, nf.seg_geo, s);
+    c->launches += 2;
+    nf.S = int64_t(S);
+  }
   if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) return cuda_fail();
   ta.release();
   al->pool.free_older_than(gen0);  // blocks no load took since the last one
@@ -602,6 +634,7 @@ static uint64_t round_signature(la_ctx* c, int si) {
                         f.parent_g, f.net_of, f.pin, f.sink_cap, f.kappa, f.gk, f.r_drv, f.geo, f.child_start,
                         f.nch, f.child_list, f.W_eq4, f.rho_eq4, f.W_adj, f.rho_adj, f.A, f.Cc, f.M, f.B,
                         f.ncache[si], f.scache[si], f.sb, f.st, f.ent, f.Jroot, f.layer, f.b, f.t, f.red,
+                        f.seg_node, f.seg_geo, f.seg_off,
                         g.cap, g.D, g.H, g.diff, g.P, g.T_dev, g.tofT_dev, g.tab_dev, c->d_stats, c->d_err};
   uint64_t h = 1469598103934665603ull;
   for (const void* q : ptrs) h = fnv_mix(h, uint64_t(reinterpret_cast<uintptr_t>(q)));
@@ -633,9 +666,8 @@ static BatchPlan make_plan(la_ctx* c, int k, int block, bool one_per_sm) {
 }
 
 // DP and backtrack of the batched form: small nets on `s`, big nets on s2.
-// fuse: the backtrack also updates the demand (not during tuning trials).
 static la_status enqueue_batched(la_ctx* c, const BatchPlan& bp, const RoundW& w, const double* W, const double* rho,
-                                 int si, bool fuse, cudaStream_t s) {
+                                 int si, cudaStream_t s) {
   const int cache = bp.cached ? si : kNoCache;
   Forest& f = c->forest;
   if (bp.n_big > 0) {
@@ -643,11 +675,11 @@ static la_status enqueue_batched(la_ctx* c, const BatchPlan& bp, const RoundW& w
     CK(cudaStreamWaitEvent(c->s2, c->ev_fork, 0));
     CK(cudaMemsetAsync(f.queue_ctr, 0, 2 * sizeof(int), c->s2));
     launch_dp_bignets(c, w, W, rho, bp.n_big, bp.grid, bp.block, cache, c->s2);
-    launch_backtrack_bignets(c, bp.n_big, bp.grid, bp.block, fuse, c->s2);
+    launch_backtrack_bignets(c, bp.n_big, bp.grid, bp.block, c->s2);
     CK(cudaEventRecord(c->ev_join, c->s2));
   }
   for (int h = 0; h <= bp.Hs; ++h) launch_dp_level(c, w, W, rho, h, bp.k, cache, s);
-  for (int h = bp.Hs; h >= 0; --h) launch_backtrack_level(c, h, bp.k, fuse, s);
+  for (int h = bp.Hs; h >= 0; --h) launch_backtrack_level(c, h, bp.k, s);
   if (bp.n_big > 0) CK(cudaStreamWaitEvent(s, c->ev_join, 0));
   CK(cudaGetLastError());
   return LA_OK;
@@ -704,7 +736,7 @@ static la_status autotune(la_ctx* c, const RoundW& w, const double* W, const dou
     double t = 1e30;
     for (int rep = 0; rep < 2; ++rep) {
       CK(cudaEventRecord(c->ev[1], s));
-      TRY(enqueue_batched(c, b, w, W, rho, si, false, s));
+      TRY(enqueue_batched(c, b, w, W, rho, si, s));
       CK(cudaEventRecord(c->ev[2], s));
       CK(cudaEventSynchronize(c->ev[2]));
       float ms = 0.f;
@@ -776,12 +808,11 @@ static la_status batched_graph(la_ctx* c, const RoundW& w, const double* W, cons
     };
     launch_node_round(c, w, rho, si, s);
     mark(c->ev[1]);
-    if (st == LA_OK) st = enqueue_batched(c, bp, w, W, rho, si, false, s);
+    if (st == LA_OK) st = enqueue_batched(c, bp, w, W, rho, si, s);
     mark(c->ev[3]);
     Forest& f = c->forest;
     if (st == LA_OK) {
-      launch_demand(c, s);
-      launch_scan_lines(c, true, w.hist_w, f.red, s);
+      launch_demand_scan(c, w.hist_w, f.red, s);
       launch_sum_roots(c, f.red + f.red_cap, nullptr, s);
     }
     mark(c->ev[4]);
@@ -848,10 +879,9 @@ la_status la_assign_round(la_ctx* c, const la_round_params* p, la_round_stats* s
     CK(cudaEventRecord(c->ev[1], s));
     for (int h = 0; h <= f.Hmax; ++h) launch_dp_level(c, w, W, rho, h, kSizeClasses - 1, kNoCache, s);
     CK(cudaEventRecord(c->ev[2], s));
-    for (int h = f.Hmax; h >= 0; --h) launch_backtrack_level(c, h, kSizeClasses - 1, false, s);
+    for (int h = f.Hmax; h >= 0; --h) launch_backtrack_level(c, h, kSizeClasses - 1, s);
     CK(cudaEventRecord(c->ev[3], s));
-    launch_demand(c, s);
-    launch_scan_lines(c, true, p->hist_w, tof_part, s);
+    launch_demand_scan(c, p->hist_w, tof_part, s);
     launch_sum_roots(c, J_part, nullptr, s);
     CK(cudaEventRecord(c->ev[4], s));
   }

@@ -168,6 +168,10 @@ struct Forest {
   double* s2 = nullptr;
   double* s3 = nullptr;
   double* s4 = nullptr;
+  int64_t S = 0;                        // segments (non-root nodes)
+  int32_t* seg_node = nullptr;          // [S] the segments' nodes, by (direction, line)
+  uint64_t* seg_geo = nullptr;          // [S] their geometry, same order
+  int64_t* seg_off = nullptr;           // [lines + 1] first segment of each line (line key as in the scan)
   double* red = nullptr;                // reduction partials: [red_cap] tof, [red_cap] J
   int red_cap = 0;
 };
@@ -192,6 +196,7 @@ struct Grid {
   DevTables tab;                        // host copy
   DevTables* tab_dev = nullptr;
   bool P_valid = false;                 // P holds the prefix of the current (D, H, hist_w)
+  bool fused_scan = false;              // the round's demand update runs inside the line scan
   double P_hist_w = -1.0;
 };
 
@@ -265,6 +270,10 @@ void launch_grid_to_internal(const LayerInfo& li, int X, int Y, const int32_t* p
                              bool to_internal, unsigned long long* err, cudaStream_t s);
 void launch_forest_prepare(la_ctx* c, Forest& f, const la_net_desc* d, int* d_hmax, cudaStream_t s);
 void launch_level_sort(Forest& f, int32_t* lvl_cnt, int64_t* lvl_cursor, cudaStream_t s);
+// segments by (direction, line): counts (cnt non-null, zeroed), then placement
+// (cursor holding the key offsets)
+void launch_seg_sort(const Forest& f, int nl0, int32_t* cnt, int64_t* cursor, int32_t* seg_node, uint64_t* seg_geo,
+                     cudaStream_t s);
 // in2int[input id] = internal id
 void launch_inverse_perm(int64_t V, const int32_t* int2in, int32_t* in2int, cudaStream_t s);
 // per-net level lists and the big-net queue (input-order forest `in`, internal ids via in2int)
@@ -283,18 +292,23 @@ struct RoundW {
   double w_cong, w_via, w_cap, w_d, hist_w;
 };
 void launch_scan_lines(la_ctx* c, bool from_diff, double hist_w, double* red_tof, cudaStream_t s);
+// the demand update and the line scan of the end of a round (fused when a
+// line's difference array fits in shared memory: prepare_fused_scan at load)
+constexpr size_t kFusedLineMaxBytes = 96 * 1024;
+size_t fused_line_bytes(const LayerInfo& li);
+bool prepare_fused_scan(const LayerInfo& li);
+void launch_demand_scan(la_ctx* c, double hist_w, double* red_tof, cudaStream_t s);
 // kmax: nodes of nets up to size class kmax (kSizeClasses - 1 = every node)
 // cache: the batched form's constant-cache set to read (0 Eq. 4, 1 adjoint), or
 // kNoCache to recompute the constants in the DP (the plain form)
 constexpr int kNoCache = -1;
 void launch_dp_level(la_ctx* c, const RoundW& w, const double* W, const double* rho, int level, int kmax,
                      int cache, cudaStream_t s);
-// fuse_demand: the batched form's backtrack also does the demand update
-void launch_backtrack_level(la_ctx* c, int level, int kmax, bool fuse_demand, cudaStream_t s);
+void launch_backtrack_level(la_ctx* c, int level, int kmax, cudaStream_t s);
 // the first n_big nets of the big-net queue, persistent grid
 void launch_dp_bignets(la_ctx* c, const RoundW& w, const double* W, const double* rho, int64_t n_big, int grid,
                        int block, int cache, cudaStream_t s);
-void launch_backtrack_bignets(la_ctx* c, int64_t n_big, int grid, int block, bool fuse_demand, cudaStream_t s);
+void launch_backtrack_bignets(la_ctx* c, int64_t n_big, int grid, int block, cudaStream_t s);
 void launch_seg_consts(la_ctx* c, const RoundW& w, const double* W, int cache, cudaStream_t s);
 void launch_node_round(la_ctx* c, const RoundW& w, const double* rho, int cache, cudaStream_t s);
 int bignet_blocks_per_sm(int L, int LD, int block);

@@ -181,6 +181,49 @@ __global__ void k_level_place(int64_t V, BucketIn b, unsigned long long* __restr
   if (act) out[base + __popc(peers & ((1u << lane) - 1u))] = int32_t(v);
 }
 
+// Segments by (direction, line): key = line for horizontal segments, nlines0 +
+// line for vertical ones; roots have no segment.  The demand pass walks them
+// in this order, so a warp's atomics land in one or two lines.
+__device__ __forceinline__ int seg_key(uint64_t g, int nl0) { return geo_dir(g) == 0 ? geo_line(g) : nl0 + geo_line(g); }
+__global__ void k_seg_count(int64_t V, const int32_t* __restrict__ parent_g, const uint64_t* __restrict__ geo,
+                            int nl0, int32_t* __restrict__ cnt) {
+  const int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const bool act = v < V && parent_g[v] >= 0;
+  const int key = act ? seg_key(geo[v], nl0) : -1;
+  const unsigned peers = __match_any_sync(0xffffffffu, key);
+  const int lane = threadIdx.x & 31;
+  if (act && lane == __ffs(peers) - 1) atomicAdd(&cnt[key], __popc(peers));
+}
+__global__ void k_seg_place(int64_t V, const int32_t* __restrict__ parent_g, const uint64_t* __restrict__ geo,
+                            int nl0, unsigned long long* __restrict__ cursor, int32_t* __restrict__ seg_node,
+                            uint64_t* __restrict__ seg_geo) {
+  const int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const bool act = v < V && parent_g[v] >= 0;
+  const uint64_t g = act ? geo[v] : 0;
+  const int key = act ? seg_key(g, nl0) : -1;
+  const unsigned peers = __match_any_sync(0xffffffffu, key);
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(peers) - 1;
+  unsigned long long base = 0;
+  if (act && lane == leader) base = atomicAdd(&cursor[key], (unsigned long long)__popc(peers));
+  base = __shfl_sync(peers, base, leader);
+  if (act) {
+    const unsigned long long pos = base + __popc(peers & ((1u << lane) - 1u));
+    seg_node[pos] = int32_t(v);
+    seg_geo[pos] = g;
+  }
+}
+
+void launch_seg_sort(const Forest& f, int nl0, int32_t* cnt, int64_t* cursor, int32_t* seg_node, uint64_t* seg_geo,
+                     cudaStream_t s) {
+  const int T = 256;
+  const unsigned B = (unsigned)((f.V + T - 1) / T);
+  if (cnt) k_seg_count<<<B, T, 0, s>>>(f.V, f.parent_g, f.geo, nl0, cnt);
+  if (cursor)
+    k_seg_place<<<B, T, 0, s>>>(f.V, f.parent_g, f.geo, nl0, reinterpret_cast<unsigned long long*>(cursor), seg_node,
+                                seg_geo);
+}
+
 // lvl_cnt: one zeroed int per bucket key; lvl_cursor: as many int64 holding
 // the bucket offsets on entry.  Within a bucket the order is whatever the
 // atomics give: nodes of one level never read each other's results.

@@ -35,6 +35,13 @@ struct ScanArgs {
   int from_diff;
   double* tof_part;         // one per block
   unsigned long long* relu;
+  // fused demand: the segments of line g are seg_node / seg_geo[seg_off[g] ..
+  // seg_off[g + 1]); their layers; WL per layer into stats
+  const int64_t* seg_off;
+  const int32_t* seg_node;
+  const uint64_t* seg_geo;
+  const int8_t* layer;
+  Stats* stats;
 };
 
 constexpr int kScanT = 256, kScanW = kScanT / 32;
@@ -53,8 +60,13 @@ __device__ __forceinline__ Tv warp_incl_scan(Tv x, int lane) {
 // The direction's penalty table sits in shared memory (it is on the path from
 // D to the second scan); every global load of a row is issued before the
 // row's first barrier.
-template <int NLD>
+// FUSED: the demand update of the round, too.  The block first adds its own
+// line's segments (+1 at the first edge, -1 past the last) into the line's
+// difference array in dynamic shared memory (shared atomics, integer: exact in
+// any order), then scans it: no global difference array and no global atomics.
+template <int NLD, bool FUSED>
 __global__ void __launch_bounds__(kScanT, (NLD <= 8 ? 3 : 1)) k_scan_lines(const DevTables* __restrict__ tab, ScanArgs a) {
+  extern __shared__ int32_t s_line[];  // FUSED: [npos][nld] difference array of this line
   __shared__ int32_t s_wd[2][kScanW][NLD];
   __shared__ int64_t s_wp[2][kScanW][NLD];
   __shared__ int64_t s_T[NLD][2][129];
@@ -79,7 +91,49 @@ __global__ void __launch_bounds__(kScanT, (NLD <= 8 ? 3 : 1)) k_scan_lines(const
     s_cD[0][threadIdx.x] = 0;
     s_cP[0][threadIdx.x] = 0;
   }
+  __shared__ unsigned long long s_wl[kMaxL];
+  __shared__ int8_t s_ldof[kMaxL];
+  if constexpr (FUSED) {
+    if (threadIdx.x < kMaxL) {
+      s_wl[threadIdx.x] = 0;
+      s_ldof[threadIdx.x] = tab->ld_of[threadIdx.x];
+    }
+    for (int i = threadIdx.x; i < npos * nld; i += kScanT) s_line[i] = 0;
+  }
   __syncthreads();
+  if constexpr (FUSED) {
+    // four segments per thread per step, every load issued before the first
+    // atomic; the step count is the same in every lane
+    constexpr int kU = 4;
+    const int64_t k0 = a.seg_off[gl], k1 = a.seg_off[gl + 1];
+    for (int64_t kb = k0; kb < k1; kb += kU * kScanT) {
+      int vq[kU];
+      uint64_t gq[kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int64_t k = kb + u * kScanT + threadIdx.x;
+        vq[u] = k < k1 ? __ldcs(a.seg_node + k) : -1;
+        gq[u] = k < k1 ? __ldcs(reinterpret_cast<const unsigned long long*>(a.seg_geo) + k) : 0;
+      }
+      int lq[kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) lq[u] = vq[u] >= 0 ? int(a.layer[vq[u]]) : -1;
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int l = lq[u];
+        const unsigned len = l >= 0 ? unsigned(geo_len(gq[u])) : 0u;
+        if (l >= 0) {
+          const int ld = s_ldof[l], lo = geo_lo(gq[u]);
+          atomicAdd(&s_line[lo * nld + ld], 1);
+          atomicAdd(&s_line[(lo + int(len)) * nld + ld], -1);
+        }
+        const unsigned peers = __match_any_sync(0xffffffffu, l);
+        const unsigned wsum = __reduce_add_sync(peers, len);
+        if (l >= 0 && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&s_wl[l], (unsigned long long)wsum);
+      }
+    }
+    __syncthreads();
+  }
   double tof = 0.0;
   unsigned long long relu = 0;
   int buf = 0;
@@ -92,7 +146,8 @@ __global__ void __launch_bounds__(kScanT, (NLD <= 8 ? 3 : 1)) k_scan_lines(const
 #pragma unroll
     for (int q = 0; q < NLD; ++q) {
       if (q < nld) {
-        Dv[q] = a.from_diff ? (valid ? a.diff[row + q] : 0) : (edge ? a.D[row + q] : 0);
+        if constexpr (FUSED) Dv[q] = valid ? s_line[pos * nld + q] : 0;
+        else Dv[q] = a.from_diff ? (valid ? a.diff[row + q] : 0) : (edge ? a.D[row + q] : 0);
         cv[q] = edge ? a.cap[row + q] : 0;
         hv[q] = edge ? a.H[row + q] : 0;
       }
@@ -101,7 +156,7 @@ __global__ void __launch_bounds__(kScanT, (NLD <= 8 ? 3 : 1)) k_scan_lines(const
 #pragma unroll
       for (int q = 0; q < NLD; ++q) {
         if (q < nld) {
-          if (valid) a.diff[row + q] = 0;
+          if (!FUSED && valid) a.diff[row + q] = 0;
           Dv[q] = warp_incl_scan<int32_t>(Dv[q], lane);
           if (lane == 31) s_wd[buf][w][q] = Dv[q];
         }
@@ -179,24 +234,99 @@ __global__ void __launch_bounds__(kScanT, (NLD <= 8 ? 3 : 1)) k_scan_lines(const
     a.tof_part[blockIdx.x] = t;
     if (r) atomicAdd(a.relu, r);
   }
+  if constexpr (FUSED) {
+    if (threadIdx.x < kMaxL && s_wl[threadIdx.x]) {
+      atomicAdd(&a.stats->wl_layer[threadIdx.x], s_wl[threadIdx.x]);
+      atomicAdd(&a.stats->wl, s_wl[threadIdx.x]);
+    }
+  }
 }
 
 int scan_blocks(const LayerInfo& li) { return li.nlines[0] + li.nlines[1]; }
 
-void launch_scan_lines(la_ctx* c, bool from_diff, double hist_w, double* tof_part, cudaStream_t s) {
+static ScanArgs scan_args(la_ctx* c, bool from_diff, double hist_w, double* tof_part) {
   Grid& g = c->grid;
+  Forest& f = c->forest;
   ScanArgs a;
   a.cap = g.cap; a.D = g.D; a.H = g.H; a.diff = g.diff; a.P = g.P; a.T = g.T_dev; a.tofT = g.tofT_dev;
   a.HW = llround(hist_w * 16777216.0);
   a.from_diff = from_diff ? 1 : 0;
   a.tof_part = tof_part;
   a.relu = &c->d_stats->relu;
+  a.seg_off = f.seg_off; a.seg_node = f.seg_node; a.seg_geo = f.seg_geo; a.layer = f.layer;
+  a.stats = c->d_stats;
+  return a;
+}
+
+template <bool FUSED>
+static void scan_launch(la_ctx* c, const ScanArgs& a, size_t dyn, cudaStream_t s) {
+  Grid& g = c->grid;
   const int nb = scan_blocks(g.li), nmax = std::max(g.li.nld[0], g.li.nld[1]);
-  if (nmax <= 4) k_scan_lines<4><<<nb, kScanT, 0, s>>>(g.tab_dev, a);
-  else if (nmax <= 6) k_scan_lines<6><<<nb, kScanT, 0, s>>>(g.tab_dev, a);
-  else if (nmax <= 8) k_scan_lines<8><<<nb, kScanT, 0, s>>>(g.tab_dev, a);
-  else k_scan_lines<kMaxL><<<nb, kScanT, 0, s>>>(g.tab_dev, a);
+  if (nmax <= 4) k_scan_lines<4, FUSED><<<nb, kScanT, dyn, s>>>(g.tab_dev, a);
+  else if (nmax <= 6) k_scan_lines<6, FUSED><<<nb, kScanT, dyn, s>>>(g.tab_dev, a);
+  else if (nmax <= 8) k_scan_lines<8, FUSED><<<nb, kScanT, dyn, s>>>(g.tab_dev, a);
+  else k_scan_lines<kMaxL, FUSED><<<nb, kScanT, dyn, s>>>(g.tab_dev, a);
   ++c->launches;
+}
+
+void launch_scan_lines(la_ctx* c, bool from_diff, double hist_w, double* tof_part, cudaStream_t s) {
+  scan_launch<false>(c, scan_args(c, from_diff, hist_w, tof_part), 0, s);
+}
+
+// The line's difference array in shared memory: the longest line of either
+// direction times its layers.
+size_t fused_line_bytes(const LayerInfo& li) {
+  return size_t(std::max(int64_t(li.npos[0]) * li.nld[0], int64_t(li.npos[1]) * li.nld[1])) * sizeof(int32_t);
+}
+
+bool prepare_fused_scan(const LayerInfo& li) {
+  const size_t bytes = fused_line_bytes(li);
+  if (bytes > kFusedLineMaxBytes) return false;
+  const int nmax = std::max(li.nld[0], li.nld[1]);
+  cudaError_t e;
+  if (nmax <= 4) e = cudaFuncSetAttribute(k_scan_lines<4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+  else if (nmax <= 6) e = cudaFuncSetAttribute(k_scan_lines<6, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+  else if (nmax <= 8) e = cudaFuncSetAttribute(k_scan_lines<8, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+  else e = cudaFuncSetAttribute(k_scan_lines<kMaxL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return true;
+}
+
+// Vias: the sum over nodes of t - b (warp, then block, then one atomic).
+__global__ void __launch_bounds__(256) k_vias(int64_t V, const int8_t* __restrict__ b, const int8_t* __restrict__ t,
+                                              Stats* stats) {
+  __shared__ unsigned s_v[8];
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  unsigned x = 0;
+  if (i < V) x = unsigned(__ldcs(reinterpret_cast<const signed char*>(t) + i) -
+                          __ldcs(reinterpret_cast<const signed char*>(b) + i));
+  x = __reduce_add_sync(0xffffffffu, x);
+  if ((threadIdx.x & 31) == 0) s_v[threadIdx.x >> 5] = x;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long sv = 0;
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) sv += s_v[w];
+    if (sv) atomicAdd(&stats->vias, sv);
+  }
+}
+
+// After the backtrack: demand, D, H += max(0, D - C), the statistics and the
+// next penalty prefix.  Fused into the line scan when a line fits in shared
+// memory; otherwise global atomics into the difference array, then the scan.
+void launch_demand_scan(la_ctx* c, double hist_w, double* tof_part, cudaStream_t s) {
+  Grid& g = c->grid;
+  Forest& f = c->forest;
+  if (g.fused_scan) {
+    k_vias<<<(unsigned)((f.V + 255) / 256), 256, 0, s>>>(f.V, f.b, f.t, c->d_stats);
+    ++c->launches;
+    scan_launch<true>(c, scan_args(c, true, hist_w, tof_part), fused_line_bytes(g.li), s);
+  } else {
+    launch_demand(c, s);
+    launch_scan_lines(c, true, hist_w, tof_part, s);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -621,35 +751,12 @@ struct BtArgs {
   const int32_t* parent_g;
   const int8_t *pin, *ent, *sb, *st;
   int8_t *layer, *b, *t;
-  // batched form: the demand update fused in (null: separate k_demand)
-  int32_t* diff;
-  const uint64_t* geo;
-  Stats* stats;
 };
-
-// Demand of node v's segment on its new layer (+1 at the first edge, -1 past
-// the last, in the difference array of its line); returns the segment length.
-__device__ __forceinline__ int demand_node(const BtArgs& a, int v, int l) {
-  if (a.parent_g[v] < 0) return 0;
-  const uint64_t g = a.geo[v];
-  const int d = geo_dir(g), len = geo_len(g);
-  const int nld = a.tab->nld[d];
-  const int64_t base = a.tab->grid_off[d] + (int64_t(geo_line(g)) * a.tab->npos[d] + geo_lo(g)) * nld + a.tab->ld_of[l];
-  atomicAdd(a.diff + base, 1);
-  atomicAdd(a.diff + base + int64_t(len) * nld, -1);
-  return len;
-}
 
 __global__ void __launch_bounds__(256) k_backtrack_bignets(BtArgs a, BigArgs g) {
   __shared__ int s_q;
   __shared__ int8_t s_ld[kMaxL];
-  __shared__ unsigned long long s_wl[kMaxL], s_vias;
-  if (threadIdx.x < kMaxL) {
-    s_ld[threadIdx.x] = a.tab->ld_of[threadIdx.x];
-    s_wl[threadIdx.x] = 0;
-  }
-  if (threadIdx.x == 0) s_vias = 0;
-  unsigned my_vias = 0;
+  if (threadIdx.x < kMaxL) s_ld[threadIdx.x] = a.tab->ld_of[threadIdx.x];
   for (;;) {
     if (threadIdx.x == 0) s_q = atomicAdd(g.ctr, 1);
     __syncthreads();
@@ -661,27 +768,11 @@ __global__ void __launch_bounds__(256) k_backtrack_bignets(BtArgs a, BigArgs g) 
     const int32_t* ho = g.bl_hoff + base + n;
     for (int h = g.net_H[n]; h >= 0; --h) {
       const int lo = ho[h], cnt = ho[h + 1] - lo;
-      for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
-        const int v = g.bl_nodes[base + lo + t];
-        backtrack_node(v, a.LD, s_ld, a.parent_g, a.pin, a.ent, a.sb, a.st, a.layer, a.b, a.t);
-        if (a.diff) {
-          const int l = a.layer[v];
-          const int len = demand_node(a, v, l);
-          if (len) atomicAdd(&s_wl[l], (unsigned long long)len);
-          my_vias += unsigned(a.t[v] - a.b[v]);
-        }
-      }
+      for (int t = threadIdx.x; t < cnt; t += blockDim.x)
+        backtrack_node(g.bl_nodes[base + lo + t], a.LD, s_ld, a.parent_g, a.pin, a.ent, a.sb, a.st, a.layer, a.b,
+                       a.t);
       __syncthreads();
     }
-  }
-  if (a.diff) {
-    if (my_vias) atomicAdd(&s_vias, (unsigned long long)my_vias);
-    __syncthreads();
-    if (threadIdx.x < kMaxL && s_wl[threadIdx.x]) {
-      atomicAdd(&a.stats->wl_layer[threadIdx.x], s_wl[threadIdx.x]);
-      atomicAdd(&a.stats->wl, s_wl[threadIdx.x]);
-    }
-    if (threadIdx.x == 0 && s_vias) atomicAdd(&a.stats->vias, s_vias);
   }
 }
 
@@ -785,51 +876,21 @@ struct Ranges {
 
 __global__ void __launch_bounds__(256) k_backtrack_level(Ranges r, BtArgs a) {
   __shared__ int8_t s_ld[kMaxL];
-  __shared__ unsigned long long s_wl[kMaxL], s_vias;
-  if (threadIdx.x < kMaxL) {
-    s_ld[threadIdx.x] = a.tab->ld_of[threadIdx.x];
-    s_wl[threadIdx.x] = 0;
-  }
-  if (threadIdx.x == 0) s_vias = 0;
+  if (threadIdx.x < kMaxL) s_ld[threadIdx.x] = a.tab->ld_of[threadIdx.x];
   __syncthreads();
   int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  unsigned vias = 0, len = 0;
-  int l = -1;
-  if (j < r.total) {
-    int k = 0;
-    while (k < kClasses - 1 && j >= r.cnt[k]) j -= r.cnt[k++];
-    const int v = int(r.lo[k] + j);
-    backtrack_node(v, a.LD, s_ld, a.parent_g, a.pin, a.ent, a.sb, a.st, a.layer, a.b, a.t);
-    if (a.diff) {
-      l = a.layer[v];
-      len = unsigned(demand_node(a, v, l));
-      vias = unsigned(a.t[v] - a.b[v]);
-      if (len == 0) l = -1;
-    }
-  }
-  if (a.diff) {
-    // warp-level sums first: one shared atomic per warp (vias) and per layer
-    const unsigned wv = __reduce_add_sync(0xffffffffu, vias);
-    if ((threadIdx.x & 31) == 0 && wv) atomicAdd(&s_vias, (unsigned long long)wv);
-    const unsigned peers = __match_any_sync(0xffffffffu, l);
-    const unsigned wl = __reduce_add_sync(peers, len);
-    if (l >= 0 && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&s_wl[l], (unsigned long long)wl);
-    __syncthreads();
-    if (threadIdx.x < kMaxL && s_wl[threadIdx.x]) {
-      atomicAdd(&a.stats->wl_layer[threadIdx.x], s_wl[threadIdx.x]);
-      atomicAdd(&a.stats->wl, s_wl[threadIdx.x]);
-    }
-    if (threadIdx.x == 0 && s_vias) atomicAdd(&a.stats->vias, s_vias);
-  }
+  if (j >= r.total) return;
+  int k = 0;
+  while (k < kClasses - 1 && j >= r.cnt[k]) j -= r.cnt[k++];
+  backtrack_node(int(r.lo[k] + j), a.LD, s_ld, a.parent_g, a.pin, a.ent, a.sb, a.st, a.layer, a.b, a.t);
 }
 
-static BtArgs bt_args(la_ctx* c, bool fuse_demand) {
+static BtArgs bt_args(la_ctx* c) {
   Forest& f = c->forest;
-  return BtArgs{c->LD,  c->grid.tab_dev, f.parent_g, f.pin, f.ent, f.sb, f.st, f.layer, f.b, f.t,
-                fuse_demand ? c->grid.diff : nullptr, f.geo, c->d_stats};
+  return BtArgs{c->LD, c->grid.tab_dev, f.parent_g, f.pin, f.ent, f.sb, f.st, f.layer, f.b, f.t};
 }
 
-void launch_backtrack_level(la_ctx* c, int level, int kmax, bool fuse_demand, cudaStream_t s) {
+void launch_backtrack_level(la_ctx* c, int level, int kmax, cudaStream_t s) {
   Forest& f = c->forest;
   Ranges r{};
   for (int cls = 0; cls < kClasses; ++cls) {
@@ -838,7 +899,7 @@ void launch_backtrack_level(la_ctx* c, int level, int kmax, bool fuse_demand, cu
     r.total += r.cnt[cls];
   }
   if (r.total == 0) return;
-  k_backtrack_level<<<(unsigned)((r.total + 255) / 256), 256, 0, s>>>(r, bt_args(c, fuse_demand));
+  k_backtrack_level<<<(unsigned)((r.total + 255) / 256), 256, 0, s>>>(r, bt_args(c));
   ++c->launches;
 }
 
@@ -847,9 +908,9 @@ static BigArgs big_args(la_ctx* c, int64_t n_big, int slot) {
   return BigArgs{f.big_queue, n_big, f.net_ptr, f.bl_nodes, f.bl_hoff, f.net_H, f.queue_ctr + slot};
 }
 
-void launch_backtrack_bignets(la_ctx* c, int64_t n_big, int grid, int block, bool fuse_demand, cudaStream_t s) {
+void launch_backtrack_bignets(la_ctx* c, int64_t n_big, int grid, int block, cudaStream_t s) {
   if (n_big == 0) return;
-  k_backtrack_bignets<<<grid, block, 0, s>>>(bt_args(c, fuse_demand), big_args(c, n_big, 1));
+  k_backtrack_bignets<<<grid, block, 0, s>>>(bt_args(c), big_args(c, n_big, 1));
   ++c->launches;
 }
 
@@ -956,39 +1017,48 @@ int bignet_blocks_per_sm(int L, int LD, int block) {
 // difference array of its line and layer (the line scan folds it into D),
 // plus vias and wirelength per layer.  Integer atomics: exact in any order.
 // ---------------------------------------------------------------------------
-struct DemandDir {
-  int64_t grid_off;   // this direction's first element
-  int32_t npos, nld;
-  uint64_t ld_of4;    // index of layer l within its direction in bits 4l..4l+3
-};
-
-// Every load of a node is issued at once (streaming: the node arrays are read
-// once and must not evict the difference array from L2).
-__global__ void __launch_bounds__(256) k_demand(int64_t V, int L, int dir, DemandDir g,
-                                                const int32_t* __restrict__ parent_g,
-                                                const uint64_t* __restrict__ geo, const int8_t* __restrict__ layer,
-                                                const int8_t* __restrict__ b, const int8_t* __restrict__ t,
-                                                int32_t* __restrict__ diff, Stats* stats) {
+// Thread i: the vias of node i (t - b), and the i-th segment in (direction,
+// line) order: +1 at its first edge and -1 past its last edge, in the
+// difference array of its line and layer.  A warp's segments lie on one or
+// two lines, so its atomics land in a few L2 sectors.  The node data is read
+// with streaming loads (each byte once).
+__global__ void __launch_bounds__(256) k_demand(int64_t V, int64_t S, int L, const DevTables* __restrict__ tab,
+                                                const int32_t* __restrict__ seg_node,
+                                                const uint64_t* __restrict__ seg_geo,
+                                                const int8_t* __restrict__ layer, const int8_t* __restrict__ b,
+                                                const int8_t* __restrict__ t, int32_t* __restrict__ diff,
+                                                Stats* stats) {
   __shared__ unsigned long long s_wl[kMaxL];
   __shared__ unsigned long long s_v[8];
-  if (threadIdx.x < kMaxL) s_wl[threadIdx.x] = 0;
+  __shared__ int64_t s_off[2];
+  __shared__ int32_t s_npos[2], s_nld[2];
+  __shared__ int8_t s_ld[kMaxL];
+  if (threadIdx.x < kMaxL) {
+    s_wl[threadIdx.x] = 0;
+    s_ld[threadIdx.x] = tab->ld_of[threadIdx.x];
+  }
+  if (threadIdx.x < 2) {
+    s_off[threadIdx.x] = tab->grid_off[threadIdx.x];
+    s_npos[threadIdx.x] = tab->npos[threadIdx.x];
+    s_nld[threadIdx.x] = tab->nld[threadIdx.x];
+  }
   __syncthreads();
-  const int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   unsigned vias = 0, len = 0;
   int l = -1;
-  if (v < V) {
-    const int32_t pg = __ldcs(parent_g + v);
-    const uint64_t gv = __ldcs(reinterpret_cast<const unsigned long long*>(geo) + v);
-    const int lv = __ldcs(reinterpret_cast<const signed char*>(layer) + v);
-    if (dir == 0) vias = unsigned(__ldcs(reinterpret_cast<const signed char*>(t) + v) -
-                                  __ldcs(reinterpret_cast<const signed char*>(b) + v));
-    if (pg >= 0 && geo_dir(gv) == dir) {
-      len = unsigned(geo_len(gv));
-      l = lv;
-      const int64_t base = g.grid_off + (int64_t(geo_line(gv)) * g.npos + geo_lo(gv)) * g.nld + int((g.ld_of4 >> (4 * lv)) & 15u);
-      atomicAdd(diff + base, 1);
-      atomicAdd(diff + base + int64_t(len) * g.nld, -1);
-    }
+  if (i < V)
+    vias = unsigned(__ldcs(reinterpret_cast<const signed char*>(t) + i) -
+                    __ldcs(reinterpret_cast<const signed char*>(b) + i));
+  if (i < S) {
+    const int v = __ldcs(seg_node + i);
+    const uint64_t g = __ldcs(reinterpret_cast<const unsigned long long*>(seg_geo) + i);
+    l = layer[v];
+    const int d = geo_dir(g);
+    len = unsigned(geo_len(g));
+    const int nld = s_nld[d];
+    const int64_t base = s_off[d] + (int64_t(geo_line(g)) * s_npos[d] + geo_lo(g)) * nld + s_ld[l];
+    atomicAdd(diff + base, 1);
+    atomicAdd(diff + base + int64_t(len) * nld, -1);
   }
   // warp sums first: one shared atomic per warp and layer
   const unsigned wv = __reduce_add_sync(0xffffffffu, vias);
@@ -1008,22 +1078,12 @@ __global__ void __launch_bounds__(256) k_demand(int64_t V, int L, int dir, Deman
   }
 }
 
-// One pass per direction: the atomics of a pass land in that direction's half
-// of the difference array, which stays resident in L2 while they land.
 void launch_demand(la_ctx* c, cudaStream_t s) {
   Forest& f = c->forest;
-  const LayerInfo& li = c->grid.li;
   const int T = 256;
-  for (int dir = 0; dir < 2; ++dir) {
-    DemandDir g{};
-    g.grid_off = li.grid_off[dir];
-    g.npos = li.npos[dir];
-    g.nld = li.nld[dir];
-    for (int l = 0; l < li.L; ++l) g.ld_of4 |= uint64_t(li.ld_of[l] & 15) << (4 * l);
-    k_demand<<<(unsigned)((f.V + T - 1) / T), T, 0, s>>>(f.V, li.L, dir, g, f.parent_g, f.geo, f.layer, f.b, f.t,
-                                                         c->grid.diff, c->d_stats);
-    ++c->launches;
-  }
+  k_demand<<<(unsigned)((f.V + T - 1) / T), T, 0, s>>>(f.V, f.S, c->grid.li.L, c->grid.tab_dev, f.seg_node,
+                                                     f.seg_geo, f.layer, f.b, f.t, c->grid.diff, c->d_stats);
+  ++c->launches;
 }
 
 // Per-block partial sums of the root costs J_n, in net order (deterministic).

@@ -122,6 +122,30 @@ def test_edge_cases_and_layer_counts(la, L):
         assert_same_round(got, ref, f"L={L} r={r}")
 
 
+@pytest.mark.parametrize("mode", ["plain", "batched"])
+def test_long_lines_take_the_global_demand_path(la, mode):
+    """Lines too long for the shared-memory difference array (13000 positions x
+    2 layers) take the global-atomics demand pass and the separate scan; the
+    result is the oracle's either way."""
+    X, Y, L = 13000, 6, 4
+    grid = simple_grid(X, Y, L, [6.0, 5.0, 2.0, 1.5], [0.2, 0.19, 0.17, 0.15], [2.0, 2.0, 2.0], 0.05, cap=2)
+    wl = fg.Workload("long", X, Y, L, (1, 3), 0.0, 400, 0, 2, 12, 0.0, False, (6.0, 5.0, 2.0, 1.5),
+                     (0.2, 0.19, 0.17, 0.15), 1)
+    forest = fg.make_forest(wl, seed=2)
+    a = _assigner(la, grid, forest)
+    m = la.LA_MODE_PLAIN if mode == "plain" else la.LA_MODE_BATCHED
+    D = H = None
+    for r in range(2):
+        st = a.assign_round(mode=m, reset=(r == 0), **la.DEFAULT_WEIGHTS)
+        got = dict(zip(("layer", "b", "t"), (x.cpu().numpy() for x in a.get_assignment())))
+        got["D"], got["H"] = (x.cpu().numpy() for x in a.get_state())
+        got["J"] = a.get_net_cost().cpu().numpy()
+        got["stats"] = st
+        ref = ref_round(grid, forest, la.DEFAULT_WEIGHTS, D=D, H=H)
+        assert_same_round(got, ref, f"{mode} r={r}")
+        D, H = got["D"], got["H"]
+
+
 def test_non_alternating_directions(la):
     X, Y, L = 16, 16, 6
     dirs = np.array([0, 0, 1, 1, 0, 1], np.int8)
