@@ -177,9 +177,10 @@ def dp_source_hash():
     return h.hexdigest()
 
 
-def dp_traffic(workload_name):
-    """DRAM bytes of one round's DP phase from the committed ncu record, if it
-    was taken on the current kernel sources for this workload (else None)."""
+def dp_capture_record(workload_name):
+    """The committed ncu record of one round's DP phase (DRAM bytes, issued
+    FP64 warp instructions), if it was taken on the current kernel sources for
+    this workload; else (None, why)."""
     p = os.path.join(ROOT, "profiles", "dp_traffic.json")
     if not os.path.exists(p):
         return None, "no capture record"
@@ -189,7 +190,7 @@ def dp_traffic(workload_name):
         return None, "capture record is for another workload"
     if rec.get("source_sha256") != dp_source_hash():
         return None, "kernels changed since the capture"
-    return float(rec["bytes_per_round"]), rec.get("how", "")
+    return rec, rec.get("how", "")
 
 
 def measured_peaks():
@@ -338,7 +339,18 @@ def bench_gpu(args):
     # entry written (A, Cc, M, B 32 B, stack 2 B), the parent's read of it
     # (32 B) and the parent's choice byte; a root's stack (2 B).
     dp_bytes = V * (8 + 32 + 17 + 8) + S * LD * (16 + 24 + 32 + 2 + 32 + 1) + N * 2
-    traffic, traffic_src = dp_traffic(wl.name)
+    rec, traffic_src = dp_capture_record(wl.name)
+    traffic = float(rec["bytes_per_round"]) if rec else None
+    # the FP64 pipe view: issued FP64 lane operations (any of FMA, ADD, MUL,
+    # conversion: one pipe slot each) per second against 2 per clock per SM
+    fp64_pipe = None
+    if rec and rec.get("fp64_warp_inst_per_round"):
+        lane_ops = 32.0 * float(rec["fp64_warp_inst_per_round"])
+        pipe_peak = 152 * 2 * 2070e6
+        fp64_pipe = {"issued_lane_ops_per_round": lane_ops, "achieved": round(lane_ops / (dp_ms * 1e-3) / 1e9, 1),
+                     "peak": round(pipe_peak / 1e9, 1), "unit": "G FP64 ops/s",
+                     "frac": round(lane_ops / (dp_ms * 1e-3) / pipe_peak, 4),
+                     "source": "issued counts from the committed ncu record (profiles/dp_traffic.json)"}
     hbm_achieved = dp_bytes / (dp_ms * 1e-3) / 1e9
     roofline = {"kernel": "k_dp_level / k_dp_bignets (all levels of one round; in the batched form the phase "
                           "also holds the backtrack)",
@@ -347,6 +359,7 @@ def bench_gpu(args):
                 "traffic_source": traffic_src,
                 "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk/SM x 2070 MHz x 2 flops (FP64 pipe)",
                 "algorithmic_flops_per_round": flops, "dp_ms_per_round": round(dp_ms, 4),
+                "fp64_pipe": fp64_pipe,
                 "hbm": {"achieved": round(hbm_achieved, 1), "peak": hbm_peak, "unit": "GB/s",
                         "frac": round(hbm_achieved / hbm_peak, 4), "algorithmic_bytes_per_round": int(dp_bytes),
                         "peak_source": f"{peak_src} hbm_gbs"}}
