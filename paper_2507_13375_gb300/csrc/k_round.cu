@@ -621,7 +621,7 @@ __device__ __forceinline__ void dp_node(const DPArgs& a, const DevTables& s, con
 // Leaves and one-son nodes fit 64 registers (4 blocks of 256 per SM); the
 // several-sons case keeps 2 blocks.
 template <int LMAX, int LDM, int DEG, bool ROOT, bool CACHED, int PINK>
-__global__ void __launch_bounds__(256, (DEG <= 1 ? 4 : 2)) k_dp_level(LayerInfo li, DPArgs a) {
+__global__ void __launch_bounds__(256, (DEG == 1 && !ROOT && PINK == 0 ? 5 : (DEG <= 1 ? 4 : 3))) k_dp_level(LayerInfo li, DPArgs a) {
   __shared__ DevTables s;
   __shared__ RoundTabs rt;
   load_round_tabs(rt, a, li.via_c);
