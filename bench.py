@@ -517,12 +517,56 @@ def profile_case(args):
                       "rounds": args.rounds, "last_round_ms": st["ms"], "device_bytes": a.device_bytes()}))
 
 
+def ablation(args):
+    """The look-ahead ablation (r_est = 0, the paper's Table VII "w/o ahead") and
+    a w_d x w_cap sweep (the paper's Fig. 10) on a synthetic workload: per
+    setting the workload's rounds (Eq. 4 weights, then adjoint reweighting),
+    then J (total look-ahead cost of the last round), T (sum over sinks of
+    kappa x Elmore delay of the final assignment), vias, total overflow (Eq. 3),
+    ReLU overflow (Eq. 2) and wirelength.  One JSON line per setting."""
+    import torch
+
+    import forestgen as fg
+    import paper_2507_13375_gb300 as la
+    import __graft_entry__
+
+    __graft_entry__.build()
+    wl = fg.WORKLOADS[args.workload]
+    if args.nets:
+        wl = wl.scaled(args.nets)
+    grid, forest = fg.make_grid(wl, 0), fg.make_forest(wl, 0)
+    a = la.LayerAssigner(0)
+    a.load_grid(grid)
+    a.load_nets(forest)
+    kap = torch.from_numpy(forest["kappa"] * (forest["pin_layer"] >= 0)).to("cuda")
+    base = dict(la.DEFAULT_WEIGHTS)
+    settings = [(True, base["w_d"], base["w_cap"]), (False, base["w_d"], base["w_cap"])]
+    for wd in (1e-4, 1e-3, 1e-2):
+        for wcap in (0.0, 0.1, 1.0):
+            if (wd, wcap) != (base["w_d"], base["w_cap"]):
+                settings.append((True, wd, wcap))
+    for ahead, wd, wcap in settings:
+        w = dict(base, w_d=wd, w_cap=wcap)
+        st = None
+        for r in range(wl.rounds):
+            st = a.assign_round(mode=la.LA_MODE_BATCHED, reset=(r == 0),
+                                weights=la.LA_WEIGHTS_EQ4 if r == 0 else la.LA_WEIGHTS_ADJOINT,
+                                look_ahead=ahead, **w)
+            a.reweight_adjoint()
+        R, C = a.rc_from_assignment()
+        T = float((kap * a.elmore(R, C)).sum())
+        print(json.dumps({"ablation": wl.name, "rounds": wl.rounds, "look_ahead": ahead, "w_d": wd, "w_cap": wcap,
+                          "J": st["total_cost"], "T": T, "vias": st["vias"], "tof": _finite(st["tof"]),
+                          "relu_overflow": st["relu_overflow"], "wl": st["wl"],
+                          "ms_last_round": round(st["ms"], 3)}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--workload", type=int, default=5, choices=[1, 2, 4, 5])
+    ap.add_argument("--workload", type=int, default=5, choices=[1, 2, 4, 5, 6])
     ap.add_argument("--mode", default="batched", choices=["plain", "batched"])
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-form comparison")
     ap.add_argument("--impl", default="gapla", choices=["gapla", "reference"])
@@ -531,9 +575,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", action="store_true", help="short untimed run for ncu captures")
     ap.add_argument("--rounds", type=int, default=1, help="rounds of the --profile run")
-    ap.add_argument("--nets", type=int, default=0, help="--profile: the workload's shape scaled to this many nets")
+    ap.add_argument("--nets", type=int, default=0,
+                    help="--profile / --ablation: the workload's shape scaled to this many nets")
+    ap.add_argument("--ablation", action="store_true",
+                    help="look-ahead ablation and w_d x w_cap sweep (quality metrics, not timed)")
     args = ap.parse_args()
-    if args.profile:
+    if args.ablation:
+        ablation(args)
+    elif args.profile:
         profile_case(args)
     elif args.impl == "reference":
         bench_reference(args)

@@ -89,7 +89,7 @@ class Workload:
     unit_r: tuple         # ohm per GCell edge, per layer
     unit_c: tuple         # fF per GCell edge, per layer
     rounds: int
-    via_r: float = 2.0    # ohm per via between adjacent layers
+    via_r: object = 2.0   # ohm per via between adjacent layers (one value, or L-1 values)
     via_c: float = 0.05   # fF per via
     n_centres: int = 64
     sigma: float = 20.0
@@ -134,6 +134,19 @@ WORKLOADS = {
 # Config 3 is config 2's forest with a fixed assignment (Elmore + adjoint).
 WORKLOADS[3] = WORKLOADS[2]
 
+# The modified NanGate 45 nm stack of the paper's Table I (10 metal layers: R in
+# kOhm/um, C in fF/um, the via resistance up to the next layer in kOhm), read
+# with a GCell edge of 1 um: R per GCell = 1000 R Ohm, C per GCell = C fF, via
+# R = 1000 Rvia Ohm.
+NANGATE45_R_KOHM_UM = (5.4286e-3, 3.5714e-3, 3.5714e-3, 1.5e-3, 1.5e-3, 1.5e-3, 1.875e-4, 1.875e-4, 3.75e-5, 3.75e-5)
+NANGATE45_C_FF_UM = (7.41819e-2, 6.74606e-2, 8.88758e-2, 1.07121e-1, 1.08964e-1, 1.02044e-1, 1.10436e-1,
+                     9.69714e-2, 3.6864e-2, 2.8042e-2)
+NANGATE45_VIA_KOHM = (5e-3, 5e-3, 5e-3, 3e-3, 3e-3, 3e-3, 1e-3, 1e-3, 0.5e-3)
+WORKLOADS[6] = Workload("nangate45-1024x1024x10-2M", 1024, 1024, 10, (8, 16), 0.05, 2_000_000, 1, 2, 64, 0.4, True,
+                        tuple(1000.0 * r for r in NANGATE45_R_KOHM_UM), NANGATE45_C_FF_UM, rounds=3,
+                        via_r=tuple(1000.0 * r for r in NANGATE45_VIA_KOHM),
+                        note="Table I stack, 2M nets, 2+Geom(0.4)<=64 clustered pins, 3 rounds")
+
 
 def _params(w: Workload, seed: int, threads: int = 0) -> _Params:
     p = _Params()
@@ -166,7 +179,8 @@ def make_grid(w: Workload, seed: int = 0, threads: int = 0) -> dict:
     lib.fg_grid_cap(ctypes.byref(p), cap.ctypes.data)
     return dict(X=w.X, Y=w.Y, L=w.L, dir=np.array(w.dirs, dtype=np.int8), cap=cap,
                 unit_r=np.array(w.unit_r, dtype=np.float64), unit_c=np.array(w.unit_c, dtype=np.float64),
-                via_r=np.full(w.L - 1, w.via_r, dtype=np.float64), via_c=float(w.via_c),
+                via_r=(np.array(w.via_r, dtype=np.float64) if isinstance(w.via_r, (tuple, list))
+                       else np.full(w.L - 1, w.via_r, dtype=np.float64)), via_c=float(w.via_c),
                 ofw=np.ones(w.L, dtype=np.float64))
 
 

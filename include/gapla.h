@@ -143,7 +143,8 @@ typedef struct {
   int32_t mode;            /* LA_MODE_*                                              */
   int32_t weights;         /* LA_WEIGHTS_*                                           */
   int32_t reset;           /* 1: start from D = 0 and H = 0 (first round)            */
-  int32_t reserved;
+  int32_t no_look_ahead;   /* 1: r_est = 0 for every node, the look-ahead ablation
+                            * of the paper's Table VII ("w/o ahead"); W unchanged   */
 } la_round_params;
 
 typedef struct {

@@ -626,7 +626,7 @@ static la_status check_loaded(la_ctx* c) {
 // writes, the forest's shape and the plan.  A graph replays only while this
 // is unchanged (a reload of a same-shaped forest gets the same addresses back
 // from the pool and keeps its graphs).
-static uint64_t round_signature(la_ctx* c, int si) {
+static uint64_t round_signature(la_ctx* c, int si, const double* W, const double* rho) {
   const Forest& f = c->forest;
   const Grid& g = c->grid;
   const BatchPlan& bp = c->plan;
@@ -638,6 +638,8 @@ static uint64_t round_signature(la_ctx* c, int si) {
                         g.cap, g.D, g.H, g.diff, g.P, g.T_dev, g.tofT_dev, g.tab_dev, c->d_stats, c->d_err};
   uint64_t h = 1469598103934665603ull;
   for (const void* q : ptrs) h = fnv_mix(h, uint64_t(reinterpret_cast<uintptr_t>(q)));
+  h = fnv_mix(h, uint64_t(reinterpret_cast<uintptr_t>(W)));
+  h = fnv_mix(h, uint64_t(reinterpret_cast<uintptr_t>(rho)));
   const int64_t vals[] = {f.N, f.V, f.Hmax, f.red_cap, c->LD, bp.k, bp.block, bp.grid, bp.cached ? 1 : 0,
                           bp.n_big, bp.Hs, int64_t(f.key_hash)};
   for (int64_t x : vals) h = fnv_mix(h, uint64_t(x));
@@ -791,7 +793,7 @@ static la_status batched_graph(la_ctx* c, const RoundW& w, const double* W, cons
   BatchPlan& bp = c->plan;
   cudaStream_t s = c->s_cap;
   const double wv[5] = {w.w_cong, w.w_via, w.w_cap, w.w_d, w.hist_w};
-  const uint64_t sig = round_signature(c, si);
+  const uint64_t sig = round_signature(c, si, W, rho);
   bool same = bp.exec[si] != nullptr && bp.graph_sig[si] == sig;
   for (int i = 0; i < 5 && same; ++i) same = bp.w[si][i] == wv[i];
   if (!same) {
@@ -849,8 +851,17 @@ la_status la_assign_round(la_ctx* c, const la_round_params* p, la_round_stats* s
   Grid& gr = c->grid;
   if (p->weights == LA_WEIGHTS_ADJOINT && !f.have_adj)
     return set_err(c, LA_ERR_STATE, "la_assign_round: no adjoint weights yet (call la_reweight_adjoint)");
+  if (p->no_look_ahead != 0 && p->no_look_ahead != 1)
+    return set_err(c, LA_ERR_INVALID, "la_assign_round: no_look_ahead must be 0 or 1");
   const double* W = p->weights == LA_WEIGHTS_ADJOINT ? f.W_adj : f.W_eq4;
   const double* rho = p->weights == LA_WEIGHTS_ADJOINT ? f.rho_adj : f.rho_eq4;
+  if (p->no_look_ahead) {
+    if (!f.rho_zero) {
+      TRY(allocs_of(c)->forest.get(c, &f.rho_zero, size_t(f.V)));
+      CK(cudaMemsetAsync(f.rho_zero, 0, sizeof(double) * size_t(f.V), c->stream));
+    }
+    rho = f.rho_zero;
+  }
   DeviceGuard g(c->device);
   cudaStream_t s = c->stream;
   RoundW w{p->w_cong, p->w_via, p->w_cap, p->w_d, p->hist_w};

@@ -145,6 +145,7 @@ struct Forest {
   double* rho_eq4 = nullptr;
   double* W_adj = nullptr;
   double* rho_adj = nullptr;
+  double* rho_zero = nullptr;           // [V] zeros: r_est of the look-ahead ablation (allocated on first use)
   bool have_adj = false;
   bool wsum_valid = false;              // W_adj holds the kappa sums below each node (fixed per forest)
   // round tables

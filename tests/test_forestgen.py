@@ -50,3 +50,16 @@ def test_l_shaped_edge_becomes_two_segments_and_a_bend_node():
             assert f["pin_layer"][a + 1] == -1 and f["parent"][a + 2] == 1
             assert f["x"][a + 1] == f["x"][a + 2] and f["y"][a + 1] == f["y"][a]
     assert set(np.unique(sizes)) <= {1, 2, 3} and (sizes == 3).sum() > 100
+
+
+def test_nangate45_workload_is_table1():
+    """The NanGate45 workload's stack is the paper's Table I read with a 1 um
+    GCell edge (R per GCell in Ohm = 1000 x kOhm/um; via R in Ohm)."""
+    from util_inputs import read_table1
+
+    rows = read_table1()
+    g = fg.make_grid(fg.WORKLOADS[6].scaled(50), 0)
+    assert g["L"] == len(rows) == 10
+    assert np.allclose(g["unit_r"], [1000.0 * r for _, r, _, _ in rows], rtol=1e-12)
+    assert np.allclose(g["unit_c"], [c for _, _, c, _ in rows], rtol=1e-12)
+    assert np.allclose(g["via_r"], [1000.0 * v for _, _, _, v in rows[:-1]], rtol=1e-12)

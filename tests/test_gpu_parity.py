@@ -372,3 +372,48 @@ def test_batched_reload_reuses_tuning(la):
     a.assign_round(mode=la.LA_MODE_PLAIN, reset=True, **la.DEFAULT_WEIGHTS)
     for k, x in zip(("layer", "b", "t"), a.get_assignment()):
         assert np.array_equal(got[k], x.cpu().numpy()), k
+
+
+@pytest.mark.parametrize("mode", ["plain", "batched"])
+def test_without_look_ahead(la, mode):
+    """The look-ahead ablation (r_est = 0, Table VII's "w/o ahead"): the oracle
+    with rho = 0, for the Eq. 4 and the adjoint weight sources; the batched
+    round's graph is re-captured when the switch changes and replayed after."""
+    wl = fg.WORKLOADS[2].scaled(20000)
+    grid, forest = fg.make_grid(wl, 11), fg.make_forest(wl, 11)
+    a = _assigner(la, grid, forest)
+    m = la.LA_MODE_PLAIN if mode == "plain" else la.LA_MODE_BATCHED
+    zero = np.zeros(int(forest["num_nodes"]), np.float64)
+    D = H = None
+    got = None
+    for r, (src, ahead) in enumerate([(0, False), (0, True), (0, False), (1, False), (1, False)]):
+        if r == 3:
+            a.reweight_adjoint()
+        st = a.assign_round(mode=m, reset=(r == 0), weights=src, look_ahead=ahead, **la.DEFAULT_WEIGHTS)
+        got = dict(zip(("layer", "b", "t"), (x.cpu().numpy() for x in a.get_assignment())))
+        got["D"], got["H"] = (x.cpu().numpy() for x in a.get_state())
+        got["J"] = a.get_net_cost().cpu().numpy()
+        got["stats"] = st
+        W, rho = (x.cpu().numpy() for x in a.get_weights(src))
+        ref = ref_round(grid, forest, la.DEFAULT_WEIGHTS, D=D, H=H, W=W, rho=rho if ahead else zero)
+        assert_same_round(got, ref, f"{mode} round {r} src {src} ahead {ahead}")
+        D, H = got["D"], got["H"]
+
+
+def test_nangate45_stack_against_oracle(la):
+    """The Table I stack (10 layers, per-layer via R) on a scaled forest: two
+    rounds against the oracle, plain and batched."""
+    wl = fg.WORKLOADS[6].scaled(20000)
+    grid, forest = fg.make_grid(wl, 12), fg.make_forest(wl, 12)
+    a = _assigner(la, grid, forest)
+    for mode in (la.LA_MODE_PLAIN, la.LA_MODE_BATCHED):
+        D = H = None
+        for r in range(2):
+            st = a.assign_round(mode=mode, reset=(r == 0), **la.DEFAULT_WEIGHTS)
+            got = dict(zip(("layer", "b", "t"), (x.cpu().numpy() for x in a.get_assignment())))
+            got["D"], got["H"] = (x.cpu().numpy() for x in a.get_state())
+            got["J"] = a.get_net_cost().cpu().numpy()
+            got["stats"] = st
+            ref = ref_round(grid, forest, la.DEFAULT_WEIGHTS, D=D, H=H)
+            assert_same_round(got, ref, f"mode {mode} round {r}")
+            D, H = got["D"], got["H"]
