@@ -111,7 +111,15 @@ typedef struct {
                               a node without a pin                                  */
   const double* kappa;     /* device, V: sink criticality >= 0 (edge weights, Eq. 4) */
   const double* r_drv;     /* device, N: driver resistance (ohm) >= 0                */
+  const int32_t* batch;    /* device, N, or null: the net's batch, 0 <= batch <
+                              LA_MAX_BATCHES.  A round assigns the batches one
+                              after the other in increasing id; each sees the
+                              demand the batches before it committed (the
+                              sequential batches of Sec. III-A).  Null: one batch,
+                              every net against one snapshot.  Several batches
+                              need LA_MODE_PLAIN.                                    */
 } la_net_desc;
+#define LA_MAX_BATCHES 4096
 
 /* Load the forest (after la_load_grid).  Validates it on the device (parent
  * order, straight segments of length >= 1 inside the grid, pins in range),

@@ -258,6 +258,57 @@ def assign_round(grid, forest, weights=None, D=None, H=None, W=None, rho=None, t
     return out
 
 
+def _net_subset(forest, nets):
+    """The sub-forest of the nets in `nets` (ascending), with the node ids of
+    the original forest that it keeps."""
+    ptr = forest["net_ptr"]
+    sizes = (ptr[1:] - ptr[:-1])[nets]
+    nodes = np.concatenate([np.arange(ptr[n], ptr[n + 1]) for n in nets]) if len(nets) else np.zeros(0, np.int64)
+    sub = {k: forest[k][nodes] for k in ("x", "y", "parent", "pin_layer", "sink_cap", "kappa")}
+    sub["r_drv"] = forest["r_drv"][nets]
+    sub["net_ptr"] = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    sub["num_nets"], sub["num_nodes"] = len(nets), int(len(nodes))
+    return sub, nodes
+
+
+def assign_round_batches(grid, forest, batch, weights=None, D=None, H=None, W=None, rho=None, layer_prev=None,
+                         threads: int = 0) -> dict:
+    """A round in sequential batches (Sec. III-A; Alg. 2 over the batches BS):
+    the batches go in increasing batch id.  Batch k is assigned against the
+    demand in which the nets of batches < k carry their new assignment of this
+    round and every other net its previous one (`layer_prev`; none in a round
+    that starts from D = 0).  H is the round's start history throughout; after
+    the last batch the new demand and history follow as in a single round."""
+    ww = dict(DEFAULT_WEIGHTS)
+    ww.update(weights or {})
+    E = num_edges(grid)
+    N, V = int(forest["num_nets"]), int(forest["num_nodes"])
+    D_cur = (np.zeros(E, np.int64) if D is None else D.astype(np.int64)).copy()
+    H = np.zeros(E, np.int32) if H is None else H
+    if W is None or rho is None:
+        W, rho = weights_eq4(grid, forest)
+    layer, b, t = np.full(V, -1, np.int8), np.full(V, -1, np.int8), np.full(V, -1, np.int8)
+    J = np.full(N, np.nan)
+    zeros = np.zeros(E, np.int32)
+    net_of = np.repeat(np.arange(N), np.diff(forest["net_ptr"]))
+    for k in np.unique(batch):
+        nets = np.nonzero(batch == k)[0]
+        pen = penalty(grid, np.minimum(D_cur, np.iinfo(np.int32).max).astype(np.int32), H, ww["hist_w"])
+        out = dp(grid, forest, ww, pen, W, rho, threads=threads)
+        sel = batch[net_of] == k
+        layer[sel], b[sel], t[sel] = out["layer"][sel], out["b"][sel], out["t"][sel]
+        J[nets] = out["J"][nets]
+        sub, nodes = _net_subset(forest, nets)
+        Dn, _, _ = demand(grid, sub, layer[nodes], b[nodes], t[nodes], zeros)
+        D_cur += Dn
+        if layer_prev is not None:
+            Do, _, _ = demand(grid, sub, layer_prev[nodes], b[nodes], t[nodes], zeros)
+            D_cur -= Do
+    Dn, Hn, st = demand(grid, forest, layer, b, t, H)
+    st["total_cost"] = float(np.sum(J))
+    return dict(layer=layer, b=b, t=t, J=J, D=Dn, H=Hn, stats=st, W=W, rho=rho)
+
+
 def rc_from_assignment(grid, forest, layer):
     keep = _Keep()
     V = int(forest["num_nodes"])

@@ -56,7 +56,7 @@ class NetDesc(ctypes.Structure):
     _fields_ = [("num_nets", ctypes.c_int64), ("num_nodes", ctypes.c_int64), ("net_ptr", ctypes.c_void_p),
                 ("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("parent", ctypes.c_void_p),
                 ("pin_layer", ctypes.c_void_p), ("sink_cap", ctypes.c_void_p), ("kappa", ctypes.c_void_p),
-                ("r_drv", ctypes.c_void_p)]
+                ("r_drv", ctypes.c_void_p), ("batch", ctypes.c_void_p)]
 
 
 class RoundParams(ctypes.Structure):
@@ -177,14 +177,19 @@ def la_load_grid(ctx, grid: dict, device: int = 0):
 
 
 def la_load_nets(ctx, forest: dict, device: int = 0):
-    """forest: net_ptr, x, y, parent, pin_layer, sink_cap, kappa, r_drv (numpy or torch)."""
+    """forest: net_ptr, x, y, parent, pin_layer, sink_cap, kappa, r_drv (numpy or torch); an optional
+    "batch" (int32 per net) splits a round into sequential batches."""
     t = dict(net_ptr=_dev(forest["net_ptr"], torch.int64, device), x=_dev(forest["x"], torch.int32, device),
              y=_dev(forest["y"], torch.int32, device), parent=_dev(forest["parent"], torch.int32, device),
              pin_layer=_dev(forest["pin_layer"], torch.int8, device),
              sink_cap=_dev(forest["sink_cap"], torch.float64, device),
              kappa=_dev(forest["kappa"], torch.float64, device), r_drv=_dev(forest["r_drv"], torch.float64, device))
+    batch = forest.get("batch")
+    if batch is not None:
+        t["batch"] = _dev(batch, torch.int32, device)
     d = NetDesc(int(t["r_drv"].numel()), int(t["x"].numel()), *(t[k].data_ptr() for k in
-                ("net_ptr", "x", "y", "parent", "pin_layer", "sink_cap", "kappa", "r_drv")))
+                ("net_ptr", "x", "y", "parent", "pin_layer", "sink_cap", "kappa", "r_drv")),
+                t["batch"].data_ptr() if batch is not None else None)
     _check(ctx, library().la_load_nets(ctx, ctypes.byref(d)))
 
 
@@ -244,6 +249,51 @@ def la_reweight_adjoint(ctx):
 
 def la_get_weights(ctx, source, W, rho):
     _check(ctx, library().la_get_weights(ctx, int(source), _ptr(W), _ptr(rho)))
+
+
+def batches_by_criticality(crit, slack=None, critical_frac: float = 0.5, slack_ratio: float = 0.7):
+    """Net batches after Alg. 1 (Sec. III-A), from per-net criticality `crit`
+    (>= 0; the paper counts critical paths through the net) and optionally
+    per-net slack (<= 0 is bad; the paper's net slack is its worst pin slack):
+
+      critical nets (crit >= critical_frac x C, C = max crit): one batch per
+        criticality interval [C, C], [C/2, C), [C/4, C/2), ...;
+      then the nets with slack worse than slack_ratio x WNS (WNS = min slack):
+        [WNS, WNS], [0.99 WNS, WNS), [0.96 WNS, 0.99 WNS), ... (edges 1 - k^2/100);
+      then every other net, in one batch.
+
+    Returns int32 batch ids, 0 first, with no empty batch in between."""
+    crit = np.asarray(crit, np.float64)
+    N = len(crit)
+    out = np.full(N, -1, np.int64)
+    C = float(crit.max()) if N else 0.0
+    nxt = 0
+    if C > 0:
+        is_crit = crit >= critical_frac * C
+        k = np.zeros(N, np.int64)
+        pos = is_crit & (crit < C)
+        k[pos] = np.ceil(np.log2(C / crit[pos]) - 1e-12).astype(np.int64)  # [C/2^k, C/2^(k-1))
+        ids = np.unique(k[is_crit])
+        for i, kk in enumerate(ids):
+            out[is_crit & (k == kk)] = nxt + i
+        nxt += len(ids)
+    if slack is not None:
+        slack = np.asarray(slack, np.float64)
+        wns = float(slack.min()) if N else 0.0
+        semi = (out < 0) & (slack <= slack_ratio * wns) if wns < 0 else np.zeros(N, bool)
+        if semi.any():
+            r = slack[semi] / wns  # in [slack_ratio, 1]
+            j = np.zeros(int(semi.sum()), np.int64)
+            below = r < 1.0
+            j[below] = np.maximum(1, np.ceil(np.sqrt(np.maximum(0.0, 1.0 - r[below]) * 100.0) - 1e-9)).astype(np.int64)
+            ids = np.unique(j)
+            sub = np.full(len(j), -1, np.int64)
+            for i, jj in enumerate(ids):
+                sub[j == jj] = nxt + i
+            out[semi] = sub
+            nxt += len(ids)
+    out[out < 0] = nxt
+    return out.astype(np.int32)
 
 
 def la_elmore_static(nets: dict, layer, b, t, L: int, via_r, via_c: float, R, C, delay, stream=None,

@@ -165,6 +165,7 @@ static const char* dev_err_name(int code) {
     case DE_ASSIGN: return "assignment layer of the wrong direction, or a via stack not covering it";
     case DE_DEGREE: return "too many sons";
     case DE_NOSTACK: return "no valid via stack";
+    case DE_BATCH: return "batch id out of range";
     default: return "unknown device check";
   }
 }
@@ -456,12 +457,12 @@ la_status la_load_nets(la_ctx* c, const la_net_desc* nd) {
   GETT(tf.parent_g, V); GETT(tf.net_of, V); GETT(tf.pin, V); GETT(tf.sink_cap, V); GETT(tf.kappa, V);
   GETT(tf.gk, V); GETT(tf.geo, V); GETT(tf.child_start, V); GETT(tf.nch, V); GETT(tf.child_list, V);
   GETT(tf.height, V); GETT(tf.W_eq4, V); GETT(tf.rho_eq4, V);
-  int* d_hmax = nullptr;
-  GETT(d_hmax, 1);
+  int* d_hmax = nullptr;  // [0] max height, [1] max batch id
+  GETT(d_hmax, 2);
   if (st) return fail(st);
   tf.net_ptr = nf.net_ptr;
   tf.r_drv = nf.r_drv;
-  if (reset_dev_err(c) || cudaMemsetAsync(d_hmax, 0, sizeof(int), s)) return cuda_fail();
+  if (reset_dev_err(c) || cudaMemsetAsync(d_hmax, 0, 2 * sizeof(int), s)) return cuda_fail();
   launch_forest_prepare(c, tf, nd, d_hmax, s);
   int code;
   long long idx;
@@ -476,19 +477,25 @@ la_status la_load_nets(la_ctx* c, const la_net_desc* nd) {
   c->plan = BatchPlan();
   al->forest.release();
   c->forest = Forest();
-  int hmax = 0;
-  if (cudaMemcpy(&hmax, d_hmax, sizeof hmax, cudaMemcpyDeviceToHost)) return cuda_fail();
+  int hb[2] = {0, 0};
+  if (cudaMemcpy(hb, d_hmax, sizeof hb, cudaMemcpyDeviceToHost)) return cuda_fail();
+  const int hmax = hb[0];
   nf.Hmax = tf.Hmax = hmax;
-  // levels: (level, class, size class) buckets
+  nf.nbatch = nd->batch ? hb[1] + 1 : 1;
+  nf.nlev = nf.nbatch * (hmax + 1);
+  // levels: (global level, class, size class) buckets, global level = batch (Hmax + 1) + height
+  if (int64_t(nf.nlev) * kClasses * kSizeClasses > (int64_t(1) << 28))
+    return fail(set_err(c, LA_ERR_INVALID, "la_load_nets: %d batches x %d levels is too many buckets", nf.nbatch,
+                        hmax + 1));
   int32_t* d_cnt = nullptr;
   int64_t* d_cur = nullptr;
-  const size_t nbk = size_t(bucket_key(hmax + 1, 0, 0));
+  const size_t nbk = size_t(bucket_key(nf.nlev, 0, 0));
   GETT(d_cnt, nbk); GETT(d_cur, nbk);
   GETK(nf.lvl_nodes, V);
   if (st) return fail(st);
   tf.lvl_nodes = nf.lvl_nodes;
   if (cudaMemsetAsync(d_cnt, 0, sizeof(int32_t) * nbk, s)) return cuda_fail();
-  launch_level_sort(tf, d_cnt, nullptr, s);
+  launch_level_sort(tf, nd->batch, hmax + 1, d_cnt, nullptr, s);
   ++c->launches;
   std::vector<int32_t> cnt(nbk);
   if (cudaMemcpyAsync(cnt.data(), d_cnt, sizeof(int32_t) * nbk, cudaMemcpyDeviceToHost, s) ||
@@ -498,10 +505,10 @@ la_status la_load_nets(la_ctx* c, const la_net_desc* nd) {
   for (size_t k = 0; k < nbk; ++k) nf.key_off[k + 1] = nf.key_off[k] + cnt[k];
   nf.key_hash = 1469598103934665603ull;
   for (int64_t x : nf.key_off) nf.key_hash = fnv_mix(nf.key_hash, uint64_t(x));
-  nf.lvl_off.assign(hmax + 2, 0);
-  for (int h = 0; h <= hmax + 1; ++h) nf.lvl_off[h] = nf.key_off[size_t(bucket_key(h, 0, 0))];
+  nf.lvl_off.assign(size_t(nf.nlev) + 1, 0);
+  for (int g = 0; g <= nf.nlev; ++g) nf.lvl_off[g] = nf.key_off[size_t(bucket_key(g, 0, 0))];
   if (cudaMemcpyAsync(d_cur, nf.key_off.data(), sizeof(int64_t) * nbk, cudaMemcpyHostToDevice, s)) return cuda_fail();
-  launch_level_sort(tf, nullptr, d_cur, s);
+  launch_level_sort(tf, nd->batch, hmax + 1, nullptr, d_cur, s);
   launch_weights_eq4(c->grid.li, tf, s);
   c->launches += 2;
   // per-net level lists and the big-net queue, then the internal order
@@ -640,7 +647,7 @@ static uint64_t round_signature(la_ctx* c, int si, const double* W, const double
   for (const void* q : ptrs) h = fnv_mix(h, uint64_t(reinterpret_cast<uintptr_t>(q)));
   h = fnv_mix(h, uint64_t(reinterpret_cast<uintptr_t>(W)));
   h = fnv_mix(h, uint64_t(reinterpret_cast<uintptr_t>(rho)));
-  const int64_t vals[] = {f.N, f.V, f.Hmax, f.red_cap, c->LD, bp.k, bp.block, bp.grid, bp.cached ? 1 : 0,
+  const int64_t vals[] = {f.N, f.V, f.Hmax, f.nbatch, f.red_cap, c->LD, bp.k, bp.block, bp.grid, bp.cached ? 1 : 0,
                           bp.n_big, bp.Hs, int64_t(f.key_hash)};
   for (int64_t x : vals) h = fnv_mix(h, uint64_t(x));
   return h;
@@ -876,9 +883,12 @@ la_status la_assign_round(la_ctx* c, const la_round_params* p, la_round_stats* s
   const long long launches0 = c->launches;
   double* tof_part = f.red;
   double* J_part = f.red + f.red_cap;
-  if (!gr.P_valid || gr.P_hist_w != p->hist_w) launch_scan_lines(c, false, p->hist_w, tof_part, s);
+  if (!gr.P_valid || gr.P_hist_w != p->hist_w) launch_scan_lines(c, 0, p->hist_w, tof_part, s);
   const bool batched = p->mode == LA_MODE_BATCHED;
   const int si = p->weights == LA_WEIGHTS_ADJOINT ? 1 : 0;
+  if (batched && f.nbatch > 1)
+    return set_err(c, LA_ERR_INVALID, "la_assign_round: a forest of %d sequential batches needs LA_MODE_PLAIN",
+                   f.nbatch);
   if (batched) {
     TRY(batched_caches(c, w, W, si, s));
     if (!c->plan.tuned) TRY(autotune(c, w, W, rho, si, s));
@@ -886,11 +896,39 @@ la_status la_assign_round(la_ctx* c, const la_round_params* p, la_round_stats* s
   CK(cudaEventRecord(c->ev[0], s));
   if (batched) {
     TRY(batched_graph(c, w, W, rho, si, s));
-  } else {
+  } else if (f.nbatch == 1) {
     CK(cudaEventRecord(c->ev[1], s));
     for (int h = 0; h <= f.Hmax; ++h) launch_dp_level(c, w, W, rho, h, kSizeClasses - 1, kNoCache, s);
     CK(cudaEventRecord(c->ev[2], s));
     for (int h = f.Hmax; h >= 0; --h) launch_backtrack_level(c, h, kSizeClasses - 1, s);
+    CK(cudaEventRecord(c->ev[3], s));
+    launch_demand_scan(c, p->hist_w, tof_part, s);
+    launch_sum_roots(c, J_part, nullptr, s);
+    CK(cudaEventRecord(c->ev[4], s));
+  } else {
+    // Sequential batches (Sec. III-A): batch k's DP and backtrack, then its
+    // nets' demand moves from their old layers (none after a reset) to the new
+    // ones and the penalty prefix is refreshed (H stays the round's), so batch
+    // k + 1 sees it.  The round's end is the single-batch one.
+    const int8_t* old = nullptr;
+    if (!p->reset && f.have_assign) {
+      if (!f.layer_old) TRY(allocs_of(c)->forest.get(c, &f.layer_old, size_t(f.V)));
+      CK(cudaMemcpyAsync(f.layer_old, f.layer, size_t(f.V), cudaMemcpyDeviceToDevice, s));
+      old = f.layer_old;
+    }
+    const int H1 = f.Hmax + 1;
+    CK(cudaEventRecord(c->ev[1], s));
+    for (int k = 0; k < f.nbatch; ++k) {
+      const int g0 = k * H1;
+      if (f.lvl_off[g0 + H1] == f.lvl_off[g0]) continue;  // an empty batch
+      for (int h = 0; h < H1; ++h) launch_dp_level(c, w, W, rho, g0 + h, kSizeClasses - 1, kNoCache, s);
+      for (int h = H1 - 1; h >= 0; --h) launch_backtrack_level(c, g0 + h, kSizeClasses - 1, s);
+      if (k + 1 < f.nbatch) {
+        launch_demand_delta(c, f.lvl_off[g0], f.lvl_off[g0 + H1], old, s);
+        launch_scan_lines(c, 2, p->hist_w, tof_part, s);
+      }
+    }
+    CK(cudaEventRecord(c->ev[2], s));
     CK(cudaEventRecord(c->ev[3], s));
     launch_demand_scan(c, p->hist_w, tof_part, s);
     launch_sum_roots(c, J_part, nullptr, s);

@@ -58,6 +58,7 @@ enum DevErr : int {
   DE_VALUE = 6,       // negative or non-finite cap / criticality / driver R; cap without a pin
   DE_ASSIGN = 7,      // assignment layer of the wrong direction / stack not covering
   DE_DEGREE = 8,      // more sons than the kernels support
+  DE_BATCH = 10,      // batch id out of range
   DE_NOSTACK = 9,     // DP found no valid stack (internal)
 };
 constexpr unsigned long long kNoErr = ~0ull;
@@ -109,7 +110,9 @@ __host__ __device__ inline int geo_len(uint64_t g) { return int(g & 0xFFFF); }
 struct Forest {
   int64_t N = 0, V = 0;
   int Hmax = 0;                         // max height (levels 0..Hmax)
-  std::vector<int64_t> lvl_off;         // host copy: level h is [lvl_off[h], lvl_off[h+1])
+  int nbatch = 1;                       // batches; batch k's level h is the global level k (Hmax + 1) + h
+  int nlev = 1;                         // global levels: nbatch (Hmax + 1)
+  std::vector<int64_t> lvl_off;         // host copy: global level g is [lvl_off[g], lvl_off[g+1])
   std::vector<int64_t> key_off;         // host copy: offsets of the (level, class, size class) buckets
   uint64_t key_hash = 0;                // hash of key_off (a captured round depends on it)
   // Per-net level lists of the nets with size class >= kMinBigSc (input-order
@@ -162,6 +165,7 @@ struct Forest {
   int8_t* layer = nullptr;              // [V]
   int8_t* b = nullptr;
   int8_t* t = nullptr;
+  int8_t* layer_old = nullptr;          // [V] the layers a multi-batch round starts from
   bool have_assign = false;
   // Elmore scratch (internal order)
   double* s0 = nullptr;                 // [V]
@@ -269,8 +273,15 @@ namespace gapla {
 // otherwise internal -> public (pub is written).
 void launch_grid_to_internal(const LayerInfo& li, int X, int Y, const int32_t* pub, int32_t* inter,
                              bool to_internal, unsigned long long* err, cudaStream_t s);
-void launch_forest_prepare(la_ctx* c, Forest& f, const la_net_desc* d, int* d_hmax, cudaStream_t s);
-void launch_level_sort(Forest& f, int32_t* lvl_cnt, int64_t* lvl_cursor, cudaStream_t s);
+// d_max: [0] max height, [1] max batch id
+void launch_forest_prepare(la_ctx* c, Forest& f, const la_net_desc* d, int* d_max, cudaStream_t s);
+// Between two batches of a round: the demand of the nodes [lo, hi) moves from
+// their old layers (layer_old, or none) to their new ones, into the
+// difference array (global atomics).
+void launch_demand_delta(la_ctx* c, int64_t lo, int64_t hi, const int8_t* layer_old, cudaStream_t s);
+// batch: the input's per-net batch ids (or null); hmax1 = Hmax + 1
+void launch_level_sort(Forest& f, const int32_t* batch, int hmax1, int32_t* lvl_cnt, int64_t* lvl_cursor,
+                       cudaStream_t s);
 // segments by (direction, line): counts (cnt non-null, zeroed), then placement
 // (cursor holding the key offsets)
 void launch_seg_sort(const Forest& f, int nl0, int32_t* cnt, int64_t* cursor, int32_t* seg_node, uint64_t* seg_geo,
@@ -292,7 +303,11 @@ void launch_permute64(int64_t V, const int32_t* perm, const double* src, double*
 struct RoundW {
   double w_cong, w_via, w_cap, w_d, hist_w;
 };
-void launch_scan_lines(la_ctx* c, bool from_diff, double hist_w, double* red_tof, cudaStream_t s);
+// from_diff: 0 the prefix of the current D and H; 1 D := the difference
+// array's prefix, then H += max(0, D - C) and the statistics; 2 D += that
+// prefix (between the batches of a round: H and the statistics untouched).
+// The difference array is cleared in modes 1 and 2.
+void launch_scan_lines(la_ctx* c, int from_diff, double hist_w, double* red_tof, cudaStream_t s);
 // the demand update and the line scan of the end of a round (fused when a
 // line's difference array fits in shared memory: prepare_fused_scan at load)
 constexpr size_t kFusedLineMaxBytes = 96 * 1024;

@@ -122,8 +122,8 @@ static ElmArgs elm_args(la_ctx* c, const double* R, const double* C) {
 template <typename K>
 static void per_level(la_ctx* c, ElmArgs a, K kernel, bool ascending, cudaStream_t s) {
   Forest& f = c->forest;
-  for (int q = 0; q <= f.Hmax; ++q) {
-    const int h = ascending ? q : f.Hmax - q;
+  for (int q = 0; q < f.nlev; ++q) {  // global levels: every batch's levels, ascending within it
+    const int h = ascending ? q : f.nlev - 1 - q;
     a.base = f.lvl_off[h];
     a.count = f.lvl_off[h + 1] - f.lvl_off[h];
     if (a.count == 0) continue;

@@ -48,7 +48,8 @@ struct PrepArgs {
   int8_t* pin;
   double *sink_cap, *kappa, *gk, *r_drv;
   uint64_t* geo;
-  int* hmax;
+  int* hmax;             // [0] max height, [1] max batch id
+  const int32_t* batch;  // per net, or null
   unsigned long long* err;
 };
 
@@ -83,6 +84,11 @@ __global__ void k_forest_prepare(PrepArgs a) {
   }
   if (bad) return;
   if (!finite_nonneg(a.rdrv_in[n])) { dev_error(a.err, DE_VALUE, base); return; }
+  if (a.batch) {
+    const int bt = a.batch[n];
+    if (bt < 0 || bt >= LA_MAX_BATCHES) { dev_error(a.err, DE_BATCH, n); return; }
+    atomicMax(a.hmax + 1, bt);
+  }
   a.net_ptr[n] = base;
   if (n == a.N - 1) a.net_ptr[a.N] = end;
   a.r_drv[n] = a.rdrv_in[n];
@@ -141,6 +147,7 @@ void launch_forest_prepare(la_ctx* c, Forest& f, const la_net_desc* d, int* d_hm
   a.nch = f.nch; a.child_list = f.child_list; a.height = f.height; a.pin = f.pin; a.sink_cap = f.sink_cap;
   a.kappa = f.kappa; a.gk = f.gk; a.r_drv = f.r_drv; a.geo = f.geo;
   a.hmax = d_hmax;
+  a.batch = d->batch;
   a.err = c->d_err;
   const int T = 128;
   k_forest_prepare<<<(unsigned)((f.N + T - 1) / T), T, 0, s>>>(a);
@@ -151,11 +158,14 @@ struct BucketIn {
   const int32_t *height, *nch, *parent_g, *net_of;
   const int64_t* net_ptr;
   const int8_t* pin;
+  const int32_t* batch;  // per net, or null
+  int hmax1;             // Hmax + 1: a batch's span of global levels
 };
 __device__ __forceinline__ long long node_bucket(int64_t v, const BucketIn& b) {
   const int cls = node_class(b.parent_g[v] < 0, b.nch[v], b.pin[v] >= 0);
   const int n = b.net_of[v];
-  return bucket_key(b.height[v], cls, size_class(b.net_ptr[n + 1] - b.net_ptr[n]));
+  const int64_t g = (b.batch ? int64_t(b.batch[n]) * b.hmax1 : 0) + b.height[v];
+  return bucket_key(g, cls, size_class(b.net_ptr[n + 1] - b.net_ptr[n]));
 }
 
 // Warp-aggregated counting: lanes with the same bucket add once.
@@ -227,10 +237,11 @@ void launch_seg_sort(const Forest& f, int nl0, int32_t* cnt, int64_t* cursor, in
 // lvl_cnt: one zeroed int per bucket key; lvl_cursor: as many int64 holding
 // the bucket offsets on entry.  Within a bucket the order is whatever the
 // atomics give: nodes of one level never read each other's results.
-void launch_level_sort(Forest& f, int32_t* lvl_cnt, int64_t* lvl_cursor, cudaStream_t s) {
+void launch_level_sort(Forest& f, const int32_t* batch, int hmax1, int32_t* lvl_cnt, int64_t* lvl_cursor,
+                       cudaStream_t s) {
   const int T = 256;
   const unsigned B = (unsigned)((f.V + T - 1) / T);
-  BucketIn b{f.height, f.nch, f.parent_g, f.net_of, f.net_ptr, f.pin};
+  BucketIn b{f.height, f.nch, f.parent_g, f.net_of, f.net_ptr, f.pin, batch, hmax1};
   if (lvl_cnt) k_level_count<<<B, T, 0, s>>>(f.V, b, lvl_cnt);
   if (lvl_cursor) k_level_place<<<B, T, 0, s>>>(f.V, b, reinterpret_cast<unsigned long long*>(lvl_cursor), f.lvl_nodes);
 }

@@ -174,6 +174,7 @@ __global__ void __launch_bounds__(kScanT, (NLD <= 8 ? 3 : 1)) k_scan_lines(const
           }
           Dv[q] += off;
           if (threadIdx.x == 0) s_cD[buf ^ 1][q] = tot;
+          if (!FUSED && a.from_diff == 2 && edge) Dv[q] += a.D[row + q];  // a batch's change on top
           if (edge) a.D[row + q] = Dv[q];
         }
       }
@@ -187,7 +188,7 @@ __global__ void __launch_bounds__(kScanT, (NLD <= 8 ? 3 : 1)) k_scan_lines(const
           const int32_t c = cv[q];
           int32_t h = hv[q];
           const int si = c > 0 ? 0 : 1;
-          if (a.from_diff) {
+          if (a.from_diff == 1) {
             const int32_t over = Dv[q] - c;
             const int l = s_lay[q];
             if (over > 0) { h += over; a.H[row + q] = h; relu += (unsigned long long)over; }
@@ -244,13 +245,13 @@ __global__ void __launch_bounds__(kScanT, (NLD <= 8 ? 3 : 1)) k_scan_lines(const
 
 int scan_blocks(const LayerInfo& li) { return li.nlines[0] + li.nlines[1]; }
 
-static ScanArgs scan_args(la_ctx* c, bool from_diff, double hist_w, double* tof_part) {
+static ScanArgs scan_args(la_ctx* c, int from_diff, double hist_w, double* tof_part) {
   Grid& g = c->grid;
   Forest& f = c->forest;
   ScanArgs a;
   a.cap = g.cap; a.D = g.D; a.H = g.H; a.diff = g.diff; a.P = g.P; a.T = g.T_dev; a.tofT = g.tofT_dev;
   a.HW = llround(hist_w * 16777216.0);
-  a.from_diff = from_diff ? 1 : 0;
+  a.from_diff = from_diff;
   a.tof_part = tof_part;
   a.relu = &c->d_stats->relu;
   a.seg_off = f.seg_off; a.seg_node = f.seg_node; a.seg_geo = f.seg_geo; a.layer = f.layer;
@@ -269,7 +270,7 @@ static void scan_launch(la_ctx* c, const ScanArgs& a, size_t dyn, cudaStream_t s
   ++c->launches;
 }
 
-void launch_scan_lines(la_ctx* c, bool from_diff, double hist_w, double* tof_part, cudaStream_t s) {
+void launch_scan_lines(la_ctx* c, int from_diff, double hist_w, double* tof_part, cudaStream_t s) {
   scan_launch<false>(c, scan_args(c, from_diff, hist_w, tof_part), 0, s);
 }
 
@@ -293,6 +294,39 @@ bool prepare_fused_scan(const LayerInfo& li) {
     return false;
   }
   return true;
+}
+
+// Between the batches of a round: node v's segment leaves its old layer (-1
+// at the first edge, +1 past the last) and takes its new one (+1, -1), in the
+// difference array (global atomics; integer, exact in any order).
+__global__ void __launch_bounds__(256) k_demand_delta(int64_t lo, int64_t hi, const DevTables* __restrict__ tab,
+                                                      const int32_t* __restrict__ parent_g,
+                                                      const uint64_t* __restrict__ geo,
+                                                      const int8_t* __restrict__ layer,
+                                                      const int8_t* __restrict__ layer_old,
+                                                      int32_t* __restrict__ diff) {
+  const int64_t v = lo + int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (v >= hi || parent_g[v] < 0) return;
+  const uint64_t g = geo[v];
+  const int d = geo_dir(g), nld = tab->nld[d];
+  const int64_t at = tab->grid_off[d] + (int64_t(geo_line(g)) * tab->npos[d] + geo_lo(g)) * nld;
+  const int64_t span = int64_t(geo_len(g)) * nld;
+  const int ln = tab->ld_of[layer[v]];
+  atomicAdd(diff + at + ln, 1);
+  atomicAdd(diff + at + span + ln, -1);
+  if (layer_old) {
+    const int lold = tab->ld_of[layer_old[v]];
+    atomicAdd(diff + at + lold, -1);
+    atomicAdd(diff + at + span + lold, 1);
+  }
+}
+
+void launch_demand_delta(la_ctx* c, int64_t lo, int64_t hi, const int8_t* layer_old, cudaStream_t s) {
+  if (hi <= lo) return;
+  Forest& f = c->forest;
+  k_demand_delta<<<(unsigned)((hi - lo + 255) / 256), 256, 0, s>>>(lo, hi, c->grid.tab_dev, f.parent_g, f.geo,
+                                                                    f.layer, layer_old, c->grid.diff);
+  ++c->launches;
 }
 
 // Vias: the sum over nodes of t - b (warp, then block, then one atomic).
@@ -322,10 +356,10 @@ void launch_demand_scan(la_ctx* c, double hist_w, double* tof_part, cudaStream_t
   if (g.fused_scan) {
     k_vias<<<(unsigned)((f.V + 255) / 256), 256, 0, s>>>(f.V, f.b, f.t, c->d_stats);
     ++c->launches;
-    scan_launch<true>(c, scan_args(c, true, hist_w, tof_part), fused_line_bytes(g.li), s);
+    scan_launch<true>(c, scan_args(c, 1, hist_w, tof_part), fused_line_bytes(g.li), s);
   } else {
     launch_demand(c, s);
-    launch_scan_lines(c, true, hist_w, tof_part, s);
+    launch_scan_lines(c, 1, hist_w, tof_part, s);
   }
 }
 

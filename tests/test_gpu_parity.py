@@ -417,3 +417,38 @@ def test_nangate45_stack_against_oracle(la):
             ref = ref_round(grid, forest, la.DEFAULT_WEIGHTS, D=D, H=H)
             assert_same_round(got, ref, f"mode {mode} round {r}")
             D, H = got["D"], got["H"]
+
+
+def test_sequential_batches_against_oracle(la):
+    """Sequential batches (Sec. III-A): batch k sees the demand of batches < k
+    with their new layers and every other net with its previous ones.  Two
+    plain rounds against the oracle, batches from the Alg. 1 partition of the
+    nets' criticality; the batched form refuses several batches; the Elmore
+    passes walk every batch's levels."""
+    wl = fg.WORKLOADS[2].scaled(12000)
+    grid, forest = fg.make_grid(wl, 13), fg.make_forest(wl, 13)
+    N = int(forest["num_nets"])
+    net_of = np.repeat(np.arange(N), np.diff(forest["net_ptr"]))
+    crit = np.zeros(N)
+    np.maximum.at(crit, net_of, forest["kappa"])
+    batch = la.batches_by_criticality(crit, critical_frac=0.6)
+    assert len(np.unique(batch)) >= 3
+    fb = dict(forest, batch=batch)
+    a = _assigner(la, grid, fb)
+    D = H = prev = None
+    for r in range(2):
+        st = a.assign_round(mode=la.LA_MODE_PLAIN, reset=(r == 0), **la.DEFAULT_WEIGHTS)
+        got = dict(zip(("layer", "b", "t"), (x.cpu().numpy() for x in a.get_assignment())))
+        got["D"], got["H"] = (x.cpu().numpy() for x in a.get_state())
+        got["J"] = a.get_net_cost().cpu().numpy()
+        got["stats"] = st
+        ref = oracle.assign_round_batches(grid, forest, batch, la.DEFAULT_WEIGHTS, D=D, H=H, layer_prev=prev)
+        assert_same_round(got, ref, f"round {r}")
+        D, H, prev = got["D"], got["H"], got["layer"]
+    with pytest.raises(la.LaError) as e:
+        a.assign_round(mode=la.LA_MODE_BATCHED, **la.DEFAULT_WEIGHTS)
+    assert e.value.status == la.LA_ERR_INVALID
+    R, C = a.rc_from_assignment()
+    d = a.elmore(R, C).cpu().numpy()
+    ref_d = oracle.elmore(grid, forest, prev, got["b"], got["t"], R.cpu().numpy(), C.cpu().numpy())
+    assert np.allclose(d, ref_d, rtol=1e-10, atol=0.0)

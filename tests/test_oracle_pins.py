@@ -381,3 +381,37 @@ def test_adjoint_cap_gradient_equals_common_path_sum():
             cd = sum(nodes[k][2] for k in range(len(nodes)) if Ji in path(k))
             kap = sum(k for s, k in sinks if s in below)
             assert dR[a + v] == pytest.approx(cd * kap, rel=1e-12, abs=1e-300)
+
+
+def test_sequential_batches_oracle():
+    """Sequential batches (Sec. III-A): one batch is the snapshot round; with
+    several, batch k's choice is the DP against the demand its predecessors
+    left, and the final demand is the demand of the final assignment."""
+    import forestgen as fg
+
+    wl = fg.WORKLOADS[2].scaled(3000)
+    grid, forest = fg.make_grid(wl, 5), fg.make_forest(wl, 5)
+    N = int(forest["num_nets"])
+    one = oracle.assign_round_batches(grid, forest, np.zeros(N, np.int32))
+    ref = oracle.assign_round(grid, forest)
+    for k in ("layer", "b", "t", "D", "H"):
+        assert np.array_equal(one[k], ref[k])
+    assert np.array_equal(one["J"], ref["J"])
+    rng = np.random.default_rng(1)
+    batch = rng.integers(0, 3, N).astype(np.int32)
+    r1 = oracle.assign_round_batches(grid, forest, batch)
+    Dchk, _, _ = oracle.demand(grid, forest, r1["layer"], r1["b"], r1["t"], np.zeros_like(r1["D"]))
+    assert np.array_equal(Dchk, r1["D"])
+    # batch 0 sees an empty map, so its nets match the snapshot round from zero
+    net_of = np.repeat(np.arange(N), np.diff(forest["net_ptr"]))
+    sel0 = batch[net_of] == 0
+    assert np.array_equal(r1["layer"][sel0], ref["layer"][sel0])
+    # the last batch sees batches 0 and 1 committed: its nets match a DP on that map
+    sub, nodes = oracle._net_subset(forest, np.nonzero(batch < 2)[0])
+    D01, _, _ = oracle.demand(grid, sub, r1["layer"][nodes], r1["b"][nodes], r1["t"][nodes], np.zeros_like(r1["D"]))
+    pen = oracle.penalty(grid, D01, np.zeros_like(D01), oracle.DEFAULT_WEIGHTS["hist_w"])
+    W, rho = oracle.weights_eq4(grid, forest)
+    out = oracle.dp(grid, forest, oracle.DEFAULT_WEIGHTS, pen, W, rho)
+    sel2 = batch[net_of] == 2
+    assert np.array_equal(out["layer"][sel2], r1["layer"][sel2])
+    assert not np.array_equal(r1["layer"], ref["layer"])  # the order changes the outcome
