@@ -559,6 +559,30 @@ def ablation(args):
                           "J": st["total_cost"], "T": T, "vias": st["vias"], "tof": _finite(st["tof"]),
                           "relu_overflow": st["relu_overflow"], "wl": st["wl"],
                           "ms_last_round": round(st["ms"], 3)}), flush=True)
+    # sequential batches (Sec. III-A): the Alg. 1 partition of the nets by
+    # criticality (here the largest sink kappa of the net), plain rounds,
+    # against the same plain rounds in one batch
+    import numpy as np
+
+    N = int(forest["num_nets"])
+    net_of = np.repeat(np.arange(N), np.diff(forest["net_ptr"]))
+    crit = np.zeros(N)
+    np.maximum.at(crit, net_of, forest["kappa"])
+    batch = la.batches_by_criticality(crit, critical_frac=0.5)
+    for name, fb in (("one batch", forest), ("criticality batches", dict(forest, batch=batch))):
+        a.load_nets(fb)
+        st = None
+        for r in range(wl.rounds):
+            st = a.assign_round(mode=la.LA_MODE_PLAIN, reset=(r == 0),
+                                weights=la.LA_WEIGHTS_EQ4 if r == 0 else la.LA_WEIGHTS_ADJOINT, **base)
+            a.reweight_adjoint()
+        R, C = a.rc_from_assignment()
+        T = float((kap * a.elmore(R, C)).sum())
+        print(json.dumps({"ablation": wl.name, "rounds": wl.rounds, "order": name,
+                          "batches": int(batch.max()) + 1 if name != "one batch" else 1, "w_d": base["w_d"],
+                          "w_cap": base["w_cap"], "J": st["total_cost"], "T": T, "vias": st["vias"],
+                          "tof": _finite(st["tof"]), "relu_overflow": st["relu_overflow"], "wl": st["wl"],
+                          "ms_last_round": round(st["ms"], 3)}), flush=True)
 
 
 def main():
