@@ -406,7 +406,7 @@ def bench_gpu(args):
                                 "demand_scan": round(statistics.mean(s["ms_demand"] for s in stats), 4),
                                 "adjoint": round(adj_ms, 4)},
         "load_ms": round(load_ms, 3), "generate_s": round(gen_s, 2),
-        "batched_plan": ({k: stats[-1][k] for k in ("batch_split", "batch_block", "batch_big_nets", "batch_cached", "batch_trials", "batch_tune_ms")}
+        "batched_plan": ({k: stats[-1][k] for k in ("batch_split", "batch_block", "batch_big_nets", "batch_cached", "batch_trials", "batch_tune_ms", "batch_levels", "batch_tail_level")}
                          if args.mode == "batched" else None),
         "roofline": roofline,
         "e2e": {"value": job_rate(world, N * wl.rounds, e2e_ms), "unit": "nets/s", "h2d_bytes_per_step": int(h2d),

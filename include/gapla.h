@@ -176,6 +176,9 @@ typedef struct {
                             * tuning memo (an earlier forest with the same level,
                             * class and size-class bucket offsets)                */
   double batch_tune_ms;    /* its DP + backtrack time when it was chosen         */
+  int32_t batch_levels;    /* levels of the small nets (the level waves + tail)   */
+  int32_t batch_tail_level;/* first level run by the one-block tail kernels
+                            * (= batch_levels: no tail)                          */
 } la_round_stats;
 
 /* Run one round against the current snapshot (D, H): every net sees the same

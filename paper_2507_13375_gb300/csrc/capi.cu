@@ -600,6 +600,24 @@ la_status la_load_nets(la_ctx* c, const la_net_desc* nd) {
     c->launches += 2;
     nf.S = int64_t(S);
   }
+  if (nf.nbatch == 1) {
+    // per split k, level and class: (first node, count) of the nets of at most
+    // 2^k nodes (the tail kernels' ranges)
+    const size_t H1 = size_t(nf.Hmax) + 1;
+    std::vector<int64_t> rt(size_t(kSizeClasses) * H1 * kClasses * 2);
+    for (int k = 0; k < kSizeClasses; ++k)
+      for (size_t h = 0; h < H1; ++h)
+        for (int cls = 0; cls < kClasses; ++cls) {
+          const int64_t lo = nf.key_off[size_t(bucket_key(int64_t(h), cls, 0))];
+          const int64_t hi = nf.key_off[size_t(bucket_key(int64_t(h), cls, k + 1))];
+          const size_t o = ((size_t(k) * H1 + h) * kClasses + cls) * 2;
+          rt[o] = lo;
+          rt[o + 1] = hi - lo;
+        }
+    if ((st = na.get(c, &nf.range_tab, rt.size()))) return fail(st);
+    if (cudaMemcpyAsync(nf.range_tab, rt.data(), sizeof(int64_t) * rt.size(), cudaMemcpyHostToDevice, s))
+      return cuda_fail();
+  }
   if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) return cuda_fail();
   ta.release();
   al->pool.free_older_than(gen0);  // blocks no load took since the last one
@@ -641,30 +659,45 @@ static uint64_t round_signature(la_ctx* c, int si, const double* W, const double
                         f.parent_g, f.net_of, f.pin, f.sink_cap, f.kappa, f.gk, f.r_drv, f.geo, f.child_start,
                         f.nch, f.child_list, f.W_eq4, f.rho_eq4, f.W_adj, f.rho_adj, f.A, f.Cc, f.M, f.B,
                         f.ncache[si], f.scache[si], f.sb, f.st, f.ent, f.Jroot, f.layer, f.b, f.t, f.red,
-                        f.seg_node, f.seg_geo, f.seg_off,
+                        f.seg_node, f.seg_geo, f.seg_off, f.range_tab,
                         g.cap, g.D, g.H, g.diff, g.P, g.T_dev, g.tofT_dev, g.tab_dev, c->d_stats, c->d_err};
   uint64_t h = 1469598103934665603ull;
   for (const void* q : ptrs) h = fnv_mix(h, uint64_t(reinterpret_cast<uintptr_t>(q)));
   h = fnv_mix(h, uint64_t(reinterpret_cast<uintptr_t>(W)));
   h = fnv_mix(h, uint64_t(reinterpret_cast<uintptr_t>(rho)));
   const int64_t vals[] = {f.N, f.V, f.Hmax, f.nbatch, f.red_cap, c->LD, bp.k, bp.block, bp.grid, bp.cached ? 1 : 0,
-                          bp.n_big, bp.Hs, int64_t(f.key_hash)};
+                          bp.n_big, bp.Hs, bp.tail_h, int64_t(f.key_hash)};
   for (int64_t x : vals) h = fnv_mix(h, uint64_t(x));
   return h;
 }
 
-static BatchPlan make_plan(la_ctx* c, int k, int block, bool one_per_sm) {
+// tail_T > 0: the top levels whose (node, candidate) task counts are all
+// below tail_T go to the one-block tail kernels instead of level waves.
+static BatchPlan make_plan(la_ctx* c, int k, int block, bool one_per_sm, int tail_T = 0) {
   Forest& f = c->forest;
   BatchPlan bp;
   bp.k = k;
   bp.block = block;
   for (int sc = std::max(k + 1, kMinBigSc); sc < kSizeClasses; ++sc) bp.n_big += f.big_sc_cnt[sc];
   bp.Hs = 0;
-  for (int h = f.Hmax; h >= 0; --h) {
+  auto tasks = [&](int h) {
     int64_t n = 0;
-    for (int cls = 0; cls < kClasses; ++cls)
-      n += f.key_off[size_t(bucket_key(h, cls, k + 1))] - f.key_off[size_t(bucket_key(h, cls, 0))];
-    if (n > 0) { bp.Hs = h; break; }
+    for (int cls = 0; cls < kClasses; ++cls) {
+      const int64_t m = f.key_off[size_t(bucket_key(h, cls, k + 1))] - f.key_off[size_t(bucket_key(h, cls, 0))];
+      n += m * ((cls >= 3 && cls <= 5) ? 1 : c->LD);
+    }
+    return n;
+  };
+  for (int h = f.Hmax; h >= 0; --h) {
+    if (tasks(h) > 0) { bp.Hs = h; break; }
+  }
+  if (tail_T > 0 && f.range_tab) {
+    int th = bp.Hs + 1;
+    while (th > 0 && tasks(th - 1) < tail_T) --th;
+    if (th + 1 <= bp.Hs) {  // at least two levels
+      bp.tail_h = th;
+      bp.tail_T = tail_T;
+    }
   }
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
@@ -687,8 +720,14 @@ static la_status enqueue_batched(la_ctx* c, const BatchPlan& bp, const RoundW& w
     launch_backtrack_bignets(c, bp.n_big, bp.grid, bp.block, c->s2);
     CK(cudaEventRecord(c->ev_join, c->s2));
   }
-  for (int h = 0; h <= bp.Hs; ++h) launch_dp_level(c, w, W, rho, h, bp.k, cache, s);
-  for (int h = bp.Hs; h >= 0; --h) launch_backtrack_level(c, h, bp.k, s);
+  const bool tail = bp.tail_h <= bp.Hs;
+  const int hw = tail ? bp.tail_h - 1 : bp.Hs;  // the last level-wave level
+  for (int h = 0; h <= hw; ++h) launch_dp_level(c, w, W, rho, h, bp.k, cache, s);
+  if (tail) {
+    launch_dp_tail(c, w, W, rho, bp.tail_h, bp.Hs, bp.k, cache, s);
+    launch_backtrack_tail(c, bp.tail_h, bp.Hs, bp.k, s);
+  }
+  for (int h = hw; h >= 0; --h) launch_backtrack_level(c, h, bp.k, s);
   if (bp.n_big > 0) CK(cudaStreamWaitEvent(s, c->ev_join, 0));
   CK(cudaGetLastError());
   return LA_OK;
@@ -755,9 +794,29 @@ static la_status autotune(la_ctx* c, const RoundW& w, const double* W, const dou
     if (t < best) { best = t; chosen = b; }
   }
   (void)f;
+  int trials = int(cand.size());
+  // then the winner with its top levels in the one-block tail kernels
+  for (int T : {2048, 8192, 32768}) {
+    BatchPlan b = make_plan(c, chosen.k, chosen.block, false, T);
+    if (b.tail_h > b.Hs) continue;
+    b.grid = chosen.grid;
+    b.cached = chosen.cached;
+    double t = 1e30;
+    for (int rep = 0; rep < 2; ++rep) {
+      CK(cudaEventRecord(c->ev[1], s));
+      TRY(enqueue_batched(c, b, w, W, rho, si, s));
+      CK(cudaEventRecord(c->ev[2], s));
+      CK(cudaEventSynchronize(c->ev[2]));
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, c->ev[1], c->ev[2]));
+      t = std::min(t, double(ms));
+    }
+    ++trials;
+    if (t < best) { best = t; chosen = b; }
+  }
   chosen.tuned = true;
   chosen.best_ms = best;
-  chosen.trials = int(cand.size());
+  chosen.trials = trials;
   for (int i = 0; i < 2; ++i) {
     chosen.cache_wd[i] = c->plan.cache_wd[i];
     chosen.cache_wcap[i] = c->plan.cache_wcap[i];
@@ -772,6 +831,7 @@ static la_status autotune(la_ctx* c, const RoundW& w, const double* W, const dou
   m.block = chosen.block;
   m.grid = chosen.grid;
   m.cached = chosen.cached;
+  m.tail_T = chosen.tail_T;
   m.best_ms = chosen.best_ms;
   m.trials = chosen.trials;
   return LA_OK;
@@ -782,7 +842,7 @@ static la_status autotune(la_ctx* c, const RoundW& w, const double* W, const dou
 static void plan_from_memo(la_ctx* c) {
   const TuneMemo& m = c->memo;
   if (!m.valid || m.L != c->grid.li.L || m.LD != c->LD || m.key_off != c->forest.key_off) return;
-  BatchPlan b = make_plan(c, m.k, m.block, false);
+  BatchPlan b = make_plan(c, m.k, m.block, false, m.tail_T);
   b.grid = m.grid;
   b.cached = m.cached;
   b.tuned = true;
@@ -988,6 +1048,8 @@ la_status la_assign_round(la_ctx* c, const la_round_params* p, la_round_stats* s
     stats->batch_tune_ms = c->plan.best_ms;
     stats->batch_cached = c->plan.cached ? 1 : 0;
     stats->batch_trials = c->plan.trials;
+    stats->batch_levels = c->plan.Hs + 1;
+    stats->batch_tail_level = std::min(c->plan.tail_h, c->plan.Hs + 1);
   }
   return LA_OK;
 }

@@ -177,6 +177,9 @@ struct Forest {
   int32_t* seg_node = nullptr;          // [S] the segments' nodes, by (direction, line)
   uint64_t* seg_geo = nullptr;          // [S] their geometry, same order
   int64_t* seg_off = nullptr;           // [lines + 1] first segment of each line (line key as in the scan)
+  // [kSizeClasses][Hmax + 1][kClasses] (first node, count) of the nets of at
+  // most 2^k nodes, per (level, class): the tail kernels' level ranges (one batch)
+  int64_t* range_tab = nullptr;
   double* red = nullptr;                // reduction partials: [red_cap] tof, [red_cap] J
   int red_cap = 0;
 };
@@ -215,6 +218,8 @@ struct BatchPlan {
   bool cached = true;         // read the constant caches (else recompute in the DP)
   int64_t n_big = 0;
   int Hs = 0;                 // highest level with a small-net node
+  int tail_h = 1 << 30;       // levels tail_h..Hs (if any) run in one persistent block, not as waves
+  int tail_T = 0;             // the task count below which a level joins the tail (0: no tail)
   double best_ms = 0.0;       // tuning time of the chosen plan
   int trials = 0;
   // one graph and one constant cache per weight source (0 Eq. 4, 1 adjoint)
@@ -233,6 +238,7 @@ struct TuneMemo {
   std::vector<int64_t> key_off;
   int k = 0, block = 0, grid = 0;
   bool cached = true;
+  int tail_T = 0;
   double best_ms = 0.0;
   int trials = 0;
 };
@@ -324,6 +330,11 @@ void launch_backtrack_level(la_ctx* c, int level, int kmax, cudaStream_t s);
 // the first n_big nets of the big-net queue, persistent grid
 void launch_dp_bignets(la_ctx* c, const RoundW& w, const double* W, const double* rho, int64_t n_big, int grid,
                        int block, int cache, cudaStream_t s);
+// The tail of the small-net level waves: levels h0..h1 in one block that
+// walks them in order (DP ascending / backtrack descending), any class.
+void launch_dp_tail(la_ctx* c, const RoundW& w, const double* W, const double* rho, int h0, int h1, int k, int cache,
+                    cudaStream_t s);
+void launch_backtrack_tail(la_ctx* c, int h0, int h1, int k, cudaStream_t s);
 void launch_backtrack_bignets(la_ctx* c, int64_t n_big, int grid, int block, cudaStream_t s);
 void launch_seg_consts(la_ctx* c, const RoundW& w, const double* W, int cache, cudaStream_t s);
 void launch_node_round(la_ctx* c, const RoundW& w, const double* rho, int cache, cudaStream_t s);

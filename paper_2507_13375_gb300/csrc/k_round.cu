@@ -779,6 +779,43 @@ __global__ void __launch_bounds__(256) k_dp_bignets(LayerInfo li, DPArgs a, BigA
   }
 }
 
+// One block walks levels h0..h1 of the small-net waves (the tail where every
+// level has few tasks): each level's (node, candidate layer) tasks over the
+// block's threads, the class chosen per node, __syncthreads between levels.
+// ranges: [level][class] (first node, count).  No wait crosses blocks.
+template <int LMAX, int LDM, bool CACHED>
+__global__ void __launch_bounds__(256, 1) k_dp_tail(LayerInfo li, DPArgs a, const int64_t* __restrict__ ranges,
+                                                    int h0, int h1) {
+  __shared__ DevTables s;
+  __shared__ RoundTabs rt;
+  __shared__ long long s_keyL[LMAX * 256];  // blockDim = 256
+  __shared__ int64_t s_lo[kClasses], s_n[kClasses];
+  load_round_tabs(rt, a, li.via_c);
+  load_tables(s, a.tab);
+  const int LD = a.LD;
+  for (int h = h0; h <= h1; ++h) {
+    if (threadIdx.x < kClasses) {
+      s_lo[threadIdx.x] = ranges[(int64_t(h) * kClasses + threadIdx.x) * 2];
+      s_n[threadIdx.x] = ranges[(int64_t(h) * kClasses + threadIdx.x) * 2 + 1];
+    }
+    __syncthreads();
+    int64_t total = 0;
+#pragma unroll
+    for (int cls = 0; cls < kClasses; ++cls) total += s_n[cls] * ((cls >= 3 && cls <= 5) ? 1 : LD);
+    for (int64_t t = threadIdx.x; t < total; t += blockDim.x) {
+      int64_t r = t;
+      int cls = 0;
+      while (cls < kClasses - 1 && r >= s_n[cls] * ((cls >= 3 && cls <= 5) ? 1 : LD)) {
+        r -= s_n[cls] * ((cls >= 3 && cls <= 5) ? 1 : LD);
+        ++cls;
+      }
+      const int ldc = (cls >= 3 && cls <= 5) ? 1 : LD;
+      dp_node_any<LMAX, LDM, CACHED>(a, s, rt, li.L, int(s_lo[cls] + r / ldc), int(r % ldc), s_keyL);
+    }
+    __syncthreads();
+  }
+}
+
 struct BtArgs {
   int LD;
   const DevTables* tab;
@@ -919,6 +956,30 @@ __global__ void __launch_bounds__(256) k_backtrack_level(Ranges r, BtArgs a) {
   backtrack_node(int(r.lo[k] + j), a.LD, s_ld, a.parent_g, a.pin, a.ent, a.sb, a.st, a.layer, a.b, a.t);
 }
 
+__global__ void __launch_bounds__(256) k_backtrack_tail(BtArgs a, const int64_t* __restrict__ ranges, int h0,
+                                                         int h1) {
+  __shared__ int8_t s_ld[kMaxL];
+  __shared__ int64_t s_lo[kClasses], s_n[kClasses];
+  if (threadIdx.x < kMaxL) s_ld[threadIdx.x] = a.tab->ld_of[threadIdx.x];
+  for (int h = h1; h >= h0; --h) {
+    if (threadIdx.x < kClasses) {
+      s_lo[threadIdx.x] = ranges[(int64_t(h) * kClasses + threadIdx.x) * 2];
+      s_n[threadIdx.x] = ranges[(int64_t(h) * kClasses + threadIdx.x) * 2 + 1];
+    }
+    __syncthreads();
+    int64_t total = 0;
+#pragma unroll
+    for (int cls = 0; cls < kClasses; ++cls) total += s_n[cls];
+    for (int64_t t = threadIdx.x; t < total; t += blockDim.x) {
+      int64_t r = t;
+      int cls = 0;
+      while (cls < kClasses - 1 && r >= s_n[cls]) r -= s_n[cls++];
+      backtrack_node(int(s_lo[cls] + r), a.LD, s_ld, a.parent_g, a.pin, a.ent, a.sb, a.st, a.layer, a.b, a.t);
+    }
+    __syncthreads();
+  }
+}
+
 static BtArgs bt_args(la_ctx* c) {
   Forest& f = c->forest;
   return BtArgs{c->LD, c->grid.tab_dev, f.parent_g, f.pin, f.ent, f.sb, f.st, f.layer, f.b, f.t};
@@ -945,6 +1006,43 @@ static BigArgs big_args(la_ctx* c, int64_t n_big, int slot) {
 void launch_backtrack_bignets(la_ctx* c, int64_t n_big, int grid, int block, cudaStream_t s) {
   if (n_big == 0) return;
   k_backtrack_bignets<<<grid, block, 0, s>>>(bt_args(c), big_args(c, n_big, 1));
+  ++c->launches;
+}
+
+void launch_backtrack_tail(la_ctx* c, int h0, int h1, int k, cudaStream_t s) {
+  Forest& f = c->forest;
+  const int64_t* ranges = f.range_tab + int64_t(k) * (f.Hmax + 1) * kClasses * 2;
+  k_backtrack_tail<<<1, 256, 0, s>>>(bt_args(c), ranges, h0, h1);
+  ++c->launches;
+}
+
+void launch_dp_tail(la_ctx* c, const RoundW& w, const double* W, const double* rho, int h0, int h1, int k, int cache,
+                    cudaStream_t s) {
+  Forest& f = c->forest;
+  DPArgs a = dp_args(c, w, W, rho);
+  const bool cached = cache >= 0;
+  if (cached) {
+    a.ncache = f.ncache[cache];
+    a.scache = f.scache[cache];
+  }
+  const int64_t* ranges = f.range_tab + int64_t(k) * (f.Hmax + 1) * kClasses * 2;
+  const int L = c->grid.li.L, LD = c->LD;
+#define TAIL(LM, LDM_)                                                                                \
+  do {                                                                                                \
+    if (cached) k_dp_tail<LM, LDM_, true><<<1, 256, 0, s>>>(c->grid.li, a, ranges, h0, h1);           \
+    else k_dp_tail<LM, LDM_, false><<<1, 256, 0, s>>>(c->grid.li, a, ranges, h0, h1);                 \
+  } while (0)
+  if (L <= 6) {
+    if (LD <= 3) TAIL(6, 3);
+    else TAIL(6, 6);
+  } else if (L <= 12) {
+    if (LD <= 6) TAIL(12, 6);
+    else TAIL(12, 12);
+  } else {
+    if (LD <= 8) TAIL(16, 8);
+    else TAIL(16, 16);
+  }
+#undef TAIL
   ++c->launches;
 }
 

@@ -452,3 +452,39 @@ def test_sequential_batches_against_oracle(la):
     d = a.elmore(R, C).cpu().numpy()
     ref_d = oracle.elmore(grid, forest, prev, got["b"], got["t"], R.cpu().numpy(), C.cpu().numpy())
     assert np.allclose(d, ref_d, rtol=1e-10, atol=0.0)
+
+
+def _chains(n, depth, X, Y, seed):
+    """n zig-zag chains of `depth` nodes (deep trees with one node per level)."""
+    from util_inputs import forest_from_rows
+    rng = np.random.default_rng(seed)
+    nets = []
+    for i in range(n):
+        x, y = int(rng.integers(0, X - depth // 2 - 2)), int(rng.integers(0, Y - depth // 2 - 2))
+        rows = [(-1, x, y, 0, 0.0, 0.0)]
+        for j in range(1, depth):
+            if j % 2:
+                x += 1
+            else:
+                y += 1
+            pin = 0 if j % 7 == 0 or j == depth - 1 else -1
+            rows.append((j - 1, x, y, pin, 1.0 if pin >= 0 else 0.0, float(rng.uniform(0.1, 1.0)) if pin >= 0 else 0.0))
+        nets.append(forest_from_rows(rows, r_drv=100.0 + i))
+    return nets
+
+
+def test_batched_tail_kernels_equal_plain(la):
+    """Deep trees (chains of 800 levels beside a Zipf forest): the tuner puts
+    the top levels in the one-block tail kernels, and the rounds equal the
+    plain form's bit for bit."""
+    wl = fg.WORKLOADS[4].scaled(4000)
+    grid = fg.make_grid(wl, 21)
+    forest = merge_forests([fg.make_forest(wl, 21)] + _chains(100, 800, wl.X, wl.Y, 21))
+    a = _assigner(la, grid, forest)
+    batched = _rounds(a, la, la.LA_MODE_BATCHED, 3, adjoint=True)
+    st = batched[0]["stats"]
+    assert st["batch_tail_level"] < st["batch_levels"], st
+    plain = _rounds(a, la, la.LA_MODE_PLAIN, 3, adjoint=True)
+    for r, (p, q) in enumerate(zip(batched, plain)):
+        for k in ("layer", "b", "t", "D", "H", "J"):
+            assert np.array_equal(p[k], q[k]), (r, k)
