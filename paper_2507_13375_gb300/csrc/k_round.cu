@@ -923,7 +923,6 @@ void launch_dp_level(la_ctx* c, const RoundW& w, const double* W, const double* 
     a.ncache = f.ncache[cache];
     a.scache = f.scache[cache];
   }
-  const int L = c->grid.li.L;
   for (int cls = 0; cls < kClasses; ++cls) {
     const int64_t lo = f.key_off[size_t(bucket_key(level, cls, 0))];
     const int64_t hi = f.key_off[size_t(bucket_key(level, cls, kmax + 1))];
