@@ -223,8 +223,7 @@ def run_step(a, la, rounds: int, mode: int, weights: dict, want_stats: bool, tor
             adj_ms.append((e0, e1))
         else:
             a.reweight_adjoint()
-    R, C = a.rc_from_assignment()
-    delay = a.elmore(R, C)
+    delay = a.elmore_assignment()
     return out, adj_ms, delay
 
 
@@ -518,8 +517,7 @@ def profile_case(args):
     for r in range(args.rounds):
         st = a.assign_round(mode=mode, reset=(r == 0), weights=la.LA_WEIGHTS_EQ4 if r == 0 else la.LA_WEIGHTS_ADJOINT)
         a.reweight_adjoint()
-    R, C = a.rc_from_assignment()
-    a.elmore(R, C)
+    a.elmore_assignment()
     torch.cuda.synchronize()
     print(json.dumps({"profile_case": wl.name, "nets": wl.num_nets, "nodes": int(forest["num_nodes"]),
                       "rounds": args.rounds, "last_round_ms": st["ms"], "device_bytes": a.device_bytes()}))
@@ -561,8 +559,7 @@ def ablation(args):
                                 weights=la.LA_WEIGHTS_EQ4 if r == 0 else la.LA_WEIGHTS_ADJOINT,
                                 look_ahead=ahead, **w)
             a.reweight_adjoint()
-        R, C = a.rc_from_assignment()
-        T = float((kap * a.elmore(R, C)).sum())
+        T = float((kap * a.elmore_assignment()).sum())
         print(json.dumps({"ablation": wl.name, "rounds": wl.rounds, "look_ahead": ahead, "w_d": wd, "w_cap": wcap,
                           "J": st["total_cost"], "T": T, "vias": st["vias"], "tof": _finite(st["tof"]),
                           "relu_overflow": st["relu_overflow"], "wl": st["wl"],
@@ -584,8 +581,7 @@ def ablation(args):
             st = a.assign_round(mode=la.LA_MODE_PLAIN, reset=(r == 0),
                                 weights=la.LA_WEIGHTS_EQ4 if r == 0 else la.LA_WEIGHTS_ADJOINT, **base)
             a.reweight_adjoint()
-        R, C = a.rc_from_assignment()
-        T = float((kap * a.elmore(R, C)).sum())
+        T = float((kap * a.elmore_assignment()).sum())
         print(json.dumps({"ablation": wl.name, "rounds": wl.rounds, "order": name,
                           "batches": int(batch.max()) + 1 if name != "one batch" else 1, "w_d": base["w_d"],
                           "w_cap": base["w_cap"], "J": st["total_cost"], "T": T, "vias": st["vias"],

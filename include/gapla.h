@@ -223,6 +223,13 @@ la_status la_elmore(la_ctx* ctx, const double* R_seg, const double* C_seg, doubl
  * keeping them from the forward pass. */
 la_status la_elmore_backward(la_ctx* ctx, const double* R_seg, const double* C_seg,
                              const double* grad_delay, double* dR_seg, double* dC_seg);
+
+/* The Elmore delays of the current assignment (after a round or
+ * la_set_assignment): the RC tree of la_rc_from_assignment's R_seg and C_seg,
+ * built from the layers inside the level passes, without the R / C arrays.
+ * Equal bit for bit to la_elmore(la_rc_from_assignment(...)).
+ *   delay: device, V, input order (written). */
+la_status la_elmore_assignment(la_ctx* ctx, double* delay);
 /* Timing sensitivities for the next round: with g = kappa on the current
  * assignment's RC tree, W[v] = sum of kappa below v (dT/dR = W * Cdown) and
  * r_est[v] = sum over resistors above v's junction of R * W (dT/dC at v).

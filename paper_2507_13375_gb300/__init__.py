@@ -35,7 +35,8 @@ EXPORTS = ("la_create", "la_destroy", "la_last_error", "la_set_stream", "la_devi
            "la_launch_count",
            "la_load_grid", "la_load_nets", "la_assign_round", "la_get_assignment", "la_set_assignment",
            "la_get_net_cost", "la_get_state", "la_set_state", "la_rc_from_assignment", "la_elmore",
-           "la_elmore_backward", "la_reweight_adjoint", "la_get_weights", "la_elmore_static")
+           "la_elmore_backward", "la_elmore_assignment", "la_reweight_adjoint", "la_get_weights",
+           "la_elmore_static")
 LA_STATIC_MAX_NODES = 1 << 21
 
 
@@ -97,7 +98,8 @@ def library() -> ctypes.CDLL:
         "la_get_assignment": [vp, vp, vp, vp], "la_set_assignment": [vp, vp, vp, vp],
         "la_get_net_cost": [vp, vp], "la_get_state": [vp, vp, vp], "la_set_state": [vp, vp, vp],
         "la_rc_from_assignment": [vp, vp, vp], "la_elmore": [vp, vp, vp, vp],
-        "la_elmore_backward": [vp, vp, vp, vp, vp, vp], "la_reweight_adjoint": [vp],
+        "la_elmore_backward": [vp, vp, vp, vp, vp, vp], "la_elmore_assignment": [vp, vp],
+        "la_reweight_adjoint": [vp],
         "la_get_weights": [vp, i32, vp, vp],
         "la_elmore_static": [P(NetDesc), vp, vp, vp, i32, vp, ctypes.c_double, vp, vp, vp, vp],
     }
@@ -238,6 +240,10 @@ def la_rc_from_assignment(ctx, R, C):
 
 def la_elmore(ctx, R, C, delay):
     _check(ctx, library().la_elmore(ctx, _ptr(R), _ptr(C), _ptr(delay)))
+
+
+def la_elmore_assignment(ctx, delay):
+    _check(ctx, library().la_elmore_assignment(ctx, _ptr(delay)))
 
 
 def la_elmore_backward(ctx, R, C, grad, dR, dC):
@@ -398,6 +404,14 @@ class LayerAssigner:
         R, C = R.contiguous(), C.contiguous()
         d = torch.empty_like(R)
         la_elmore(self.ctx, R, C, d)
+        return d
+
+    def elmore_assignment(self):
+        """Elmore delays (input order) of the current assignment, R and C taken
+        from its layers inside the level passes."""
+        self._sync_stream()
+        d = torch.empty(self.V, dtype=torch.float64, device=self.dev)
+        la_elmore_assignment(self.ctx, d)
         return d
 
     def elmore_backward(self, R, C, grad):

@@ -1183,6 +1183,15 @@ la_status la_elmore(la_ctx* c, const double* R, const double* C, double* delay) 
   return LA_OK;
 }
 
+la_status la_elmore_assignment(la_ctx* c, double* delay) {
+  TRY(check_assigned(c));
+  if (!delay) return set_err(c, LA_ERR_INVALID, "la_elmore_assignment: null pointer");
+  DeviceGuard g(c->device);
+  launch_elmore_assignment(c, delay, c->stream);
+  CK(cudaGetLastError());
+  return LA_OK;
+}
+
 la_status la_elmore_backward(la_ctx* c, const double* R, const double* C, const double* gd, double* dR, double* dC) {
   TRY(check_assigned(c));
   if (!R || !C || !gd || !dR || !dC) return set_err(c, LA_ERR_INVALID, "la_elmore_backward: null pointer");

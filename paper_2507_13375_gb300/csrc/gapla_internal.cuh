@@ -346,6 +346,8 @@ int scan_blocks(const LayerInfo& li);
 // R, C in internal order, or scattered to input order when perm != nullptr
 void launch_rc_from_assignment(la_ctx* c, double* R, double* C, const int32_t* perm, cudaStream_t s);
 void launch_elmore_fwd(la_ctx* c, const double* R, const double* C, double* delay, cudaStream_t s);
+// the delays of the current assignment (R_seg, C_seg from its layers), input order
+void launch_elmore_assignment(la_ctx* c, double* delay_input_order, cudaStream_t s);
 void launch_elmore_bwd(la_ctx* c, const double* R, const double* C, const double* g, double* dR,
                        double* dC, double* Wsum_out, double* UJ_out, cudaStream_t s);
 // Top-down pass only: U from Ws (given) and R_seg = len x unit R of the

@@ -37,7 +37,8 @@ void launch_rc_from_assignment(la_ctx* c, double* R, double* C, const int32_t* p
 
 struct ElmArgs {
   const int32_t *parent_g, *child_start, *nch, *child_list, *net_of;
-  const uint64_t* geo;  // k_elm_adj with R == null: R_seg from the geometry and the layer
+  const uint64_t* geo;  // R or C null: R_seg / C_seg from the geometry and the layer
+  const int32_t* out_perm;  // k_elm_delay: delay[out_perm[v]] (input order), or delay[v]
   int64_t base, count;
   const int8_t *layer, *b, *t, *pin;
   const double *sink_cap, *r_drv, *R, *C, *g;
@@ -45,19 +46,30 @@ struct ElmArgs {
   double *CdJ, *Ws, *dJ, *delay, *UJ, *dR, *dC;
 };
 
+// R_seg and C_seg of node v: the given arrays, or the assignment's len x unit
+// R / unit C of v's layer (the expressions of k_rc; 0 at roots).
+__device__ __forceinline__ double seg_r(const ElmArgs& a, int v) {
+  if (a.R) return a.R[v];
+  return a.parent_g[v] < 0 ? 0.0 : double(geo_len(a.geo[v])) * a.tab->unit_r[a.layer[v]];
+}
+__device__ __forceinline__ double seg_c(const ElmArgs& a, int v) {
+  if (a.C) return a.C[v];
+  return a.parent_g[v] < 0 ? 0.0 : double(geo_len(a.geo[v])) * a.tab->unit_c[a.layer[v]];
+}
+
 // Bottom-up: Cd_J(v) = C_seg[v]/2 + vc (t - b) + Cs_v + sum over sons of
 // (C_seg[c]/2 + Cd_J(c)); with g, also Ws(v) = g_v + sum over sons of Ws(c).
 __global__ void k_elm_up(ElmArgs a) {
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= a.count) return;
   const int v = int(a.base + i);
-  double s = a.parent_g[v] < 0 ? 0.0 : 0.5 * a.C[v];
+  double s = a.parent_g[v] < 0 ? 0.0 : 0.5 * seg_c(a, v);
   s = s + a.tab->via_c * double(a.t[v] - a.b[v]);
   s = s + a.sink_cap[v];
   const int cs = a.child_start[v], nc = a.nch[v];
   for (int j = 0; j < nc; ++j) {
     const int c = a.child_list[cs + j];
-    s = s + (0.5 * a.C[c] + a.CdJ[c]);
+    s = s + (0.5 * seg_c(a, c) + a.CdJ[c]);
   }
   a.CdJ[v] = s;
   if (a.Ws) {
@@ -78,12 +90,12 @@ __global__ void k_elm_delay(ElmArgs a) {
   if (p < 0) {
     dj = a.r_drv[a.net_of[v]] * a.CdJ[v];
   } else {
-    const double dX = a.dJ[p] + a.tab->rv[a.layer[p] * kMaxL + lv] * (0.5 * a.C[v] + a.CdJ[v]);
-    dj = dX + a.R[v] * a.CdJ[v];
+    const double dX = a.dJ[p] + a.tab->rv[a.layer[p] * kMaxL + lv] * (0.5 * seg_c(a, v) + a.CdJ[v]);
+    dj = dX + seg_r(a, v) * a.CdJ[v];
   }
   a.dJ[v] = dj;
   const int pin = a.pin[v];
-  a.delay[v] = pin >= 0 ? dj + a.tab->rv[lv * kMaxL + pin] * a.sink_cap[v] : dj;
+  a.delay[a.out_perm ? a.out_perm[v] : v] = pin >= 0 ? dj + a.tab->rv[lv * kMaxL + pin] * a.sink_cap[v] : dj;
 }
 
 // Top-down adjoint: U_J(root) = R_drv Ws(root); U_X(v) = U_J(p) + Rvia Ws(v);
@@ -100,7 +112,7 @@ __global__ void k_elm_adj(ElmArgs a) {
   }
   const double w = a.Ws[v];
   const int lv = a.layer[v];
-  const double Rv = a.R ? a.R[v] : double(geo_len(a.geo[v])) * a.tab->unit_r[lv];
+  const double Rv = seg_r(a, v);
   const double UX = a.UJ[p] + a.tab->rv[a.layer[p] * kMaxL + lv] * w;
   const double uj = UX + Rv * w;
   a.UJ[v] = uj;
@@ -159,6 +171,18 @@ void launch_elmore_adj_only(la_ctx* c, const double* Ws, double* UJ_out, cudaStr
   a.Ws = const_cast<double*>(Ws);
   a.UJ = UJ_out;
   per_level(c, a, k_elm_adj, false, s);
+}
+
+// The delays of the current assignment, with R_seg and C_seg from the layers,
+// written in input order.
+void launch_elmore_assignment(la_ctx* c, double* delay_input_order, cudaStream_t s) {
+  ElmArgs a = elm_args(c, nullptr, nullptr);
+  a.CdJ = c->forest.s0;
+  a.dJ = c->forest.s1;
+  a.delay = delay_input_order;
+  a.out_perm = c->forest.lvl_nodes;
+  per_level(c, a, k_elm_up, true, s);
+  per_level(c, a, k_elm_delay, false, s);
 }
 
 }  // namespace gapla

@@ -488,3 +488,16 @@ def test_batched_tail_kernels_equal_plain(la):
     for r, (p, q) in enumerate(zip(batched, plain)):
         for k in ("layer", "b", "t", "D", "H", "J"):
             assert np.array_equal(p[k], q[k]), (r, k)
+
+
+def test_elmore_of_the_assignment(la):
+    """la_elmore_assignment (R, C from the layers inside the passes, output in
+    input order) equals la_elmore of la_rc_from_assignment bit for bit."""
+    wl = fg.WORKLOADS[2].scaled(20000)
+    grid, forest = fg.make_grid(wl, 14), fg.make_forest(wl, 14)
+    a = _assigner(la, grid, forest)
+    a.assign_round(reset=True, **la.DEFAULT_WEIGHTS)
+    R, C = a.rc_from_assignment()
+    ref = a.elmore(R, C).cpu().numpy()
+    got = a.elmore_assignment().cpu().numpy()
+    assert np.array_equal(got, ref)
