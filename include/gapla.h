@@ -153,6 +153,11 @@ typedef struct {
   int32_t reset;           /* 1: start from D = 0 and H = 0 (first round)            */
   int32_t no_look_ahead;   /* 1: r_est = 0 for every node, the look-ahead ablation
                             * of the paper's Table VII ("w/o ahead"); W unchanged   */
+  int32_t tail_threshold;  /* batched form: 0 = the tuner's plan; T > 0 = the tuned
+                            * plan's split and block with the top small-net levels
+                            * whose (node, candidate) task counts are all below T
+                            * in the one-block tail kernels.  Results do not
+                            * depend on it; < 0 is LA_ERR_INVALID                */
 } la_round_params;
 
 typedef struct {

@@ -63,7 +63,8 @@ class NetDesc(ctypes.Structure):
 class RoundParams(ctypes.Structure):
     _fields_ = [("w_cong", ctypes.c_double), ("w_via", ctypes.c_double), ("w_cap", ctypes.c_double),
                 ("w_d", ctypes.c_double), ("hist_w", ctypes.c_double), ("mode", ctypes.c_int32),
-                ("weights", ctypes.c_int32), ("reset", ctypes.c_int32), ("no_look_ahead", ctypes.c_int32)]
+                ("weights", ctypes.c_int32), ("reset", ctypes.c_int32), ("no_look_ahead", ctypes.c_int32),
+                ("tail_threshold", ctypes.c_int32)]
 
 
 class RoundStats(ctypes.Structure):
@@ -197,11 +198,11 @@ def la_load_nets(ctx, forest: dict, device: int = 0):
 
 
 def la_assign_round(ctx, mode: int = LA_MODE_PLAIN, weights: int = LA_WEIGHTS_EQ4, reset: bool = False,
-                    stats: bool = True, look_ahead: bool = True, **w):
+                    stats: bool = True, look_ahead: bool = True, tail_threshold: int = 0, **w):
     ww = dict(DEFAULT_WEIGHTS)
     ww.update(w)
     p = RoundParams(ww["w_cong"], ww["w_via"], ww["w_cap"], ww["w_d"], ww["hist_w"], int(mode), int(weights),
-                    1 if reset else 0, 0 if look_ahead else 1)
+                    1 if reset else 0, 0 if look_ahead else 1, int(tail_threshold))
     if not stats:
         _check(ctx, library().la_assign_round(ctx, ctypes.byref(p), None))
         return None
@@ -360,9 +361,9 @@ class LayerAssigner:
         self.V = int(len(forest["x"]))
 
     def assign_round(self, mode=LA_MODE_PLAIN, weights=LA_WEIGHTS_EQ4, reset=False, stats=True, look_ahead=True,
-                     **w):
+                     tail_threshold=0, **w):
         self._sync_stream()
-        return la_assign_round(self.ctx, mode, weights, reset, stats, look_ahead, **w)
+        return la_assign_round(self.ctx, mode, weights, reset, stats, look_ahead, tail_threshold, **w)
 
     def get_assignment(self):
         self._sync_stream()

@@ -455,14 +455,14 @@ la_status la_load_nets(la_ctx* c, const la_net_desc* nd) {
 #define GETT(p, n) if (st == LA_OK) st = ta.get(c, &(p), (n))
   GETK(nf.net_ptr, N + 1); GETK(nf.r_drv, N);
   GETT(tf.parent_g, V); GETT(tf.net_of, V); GETT(tf.pin, V); GETT(tf.sink_cap, V); GETT(tf.kappa, V);
-  GETT(tf.gk, V); GETT(tf.geo, V); GETT(tf.child_start, V); GETT(tf.nch, V); GETT(tf.child_list, V);
+  GETT(tf.geo, V); GETT(tf.child_start, V); GETT(tf.nch, V); GETT(tf.child_list, V);
   GETT(tf.height, V); GETT(tf.W_eq4, V); GETT(tf.rho_eq4, V);
-  int* d_hmax = nullptr;  // [0] max height, [1] max batch id
-  GETT(d_hmax, 2);
+  int* d_hmax = nullptr;  // [0] max height, [1] max batch id, [2] bad net range
+  GETT(d_hmax, 3);
   if (st) return fail(st);
   tf.net_ptr = nf.net_ptr;
   tf.r_drv = nf.r_drv;
-  if (reset_dev_err(c) || cudaMemsetAsync(d_hmax, 0, 2 * sizeof(int), s)) return cuda_fail();
+  if (reset_dev_err(c) || cudaMemsetAsync(d_hmax, 0, 3 * sizeof(int), s)) return cuda_fail();
   launch_forest_prepare(c, tf, nd, d_hmax, s);
   int code;
   long long idx;
@@ -489,13 +489,15 @@ la_status la_load_nets(la_ctx* c, const la_net_desc* nd) {
                         hmax + 1));
   int32_t* d_cnt = nullptr;
   int64_t* d_cur = nullptr;
+  int32_t* in2int = nullptr;  // input id -> internal id
+  int32_t* key_of = nullptr;  // input id -> bucket
   const size_t nbk = size_t(bucket_key(nf.nlev, 0, 0));
-  GETT(d_cnt, nbk); GETT(d_cur, nbk);
+  GETT(d_cnt, nbk); GETT(d_cur, nbk); GETT(in2int, V); GETT(key_of, V);
   GETK(nf.lvl_nodes, V);
   if (st) return fail(st);
   tf.lvl_nodes = nf.lvl_nodes;
   if (cudaMemsetAsync(d_cnt, 0, sizeof(int32_t) * nbk, s)) return cuda_fail();
-  launch_level_sort(tf, nd->batch, hmax + 1, d_cnt, nullptr, s);
+  launch_level_sort(tf, nd->batch, hmax + 1, int64_t(nbk), d_cnt, nullptr, nullptr, nullptr, s);
   ++c->launches;
   std::vector<int32_t> cnt(nbk);
   if (cudaMemcpyAsync(cnt.data(), d_cnt, sizeof(int32_t) * nbk, cudaMemcpyDeviceToHost, s) ||
@@ -508,20 +510,17 @@ la_status la_load_nets(la_ctx* c, const la_net_desc* nd) {
   nf.lvl_off.assign(size_t(nf.nlev) + 1, 0);
   for (int g = 0; g <= nf.nlev; ++g) nf.lvl_off[g] = nf.key_off[size_t(bucket_key(g, 0, 0))];
   if (cudaMemcpyAsync(d_cur, nf.key_off.data(), sizeof(int64_t) * nbk, cudaMemcpyHostToDevice, s)) return cuda_fail();
-  launch_level_sort(tf, nd->batch, hmax + 1, nullptr, d_cur, s);
-  launch_weights_eq4(c->grid.li, tf, s);
-  c->launches += 2;
+  launch_level_sort(tf, nd->batch, hmax + 1, int64_t(nbk), nullptr, d_cur, in2int, key_of, s);
+  ++c->launches;
   // per-net level lists and the big-net queue, then the internal order
-  int32_t* in2int = nullptr;
   int32_t* d_sc = nullptr;
   int64_t* d_sccur = nullptr;
-  GETT(in2int, V); GETT(d_sc, kSizeClasses); GETT(d_sccur, kSizeClasses);
+  GETT(d_sc, kSizeClasses); GETT(d_sccur, kSizeClasses);
   GETK(nf.bl_nodes, V); GETK(nf.bl_hoff, V + N); GETK(nf.net_H, N); GETK(nf.queue_ctr, 4);
   if (st) return fail(st);
   if (cudaMemsetAsync(d_sc, 0, sizeof(int32_t) * kSizeClasses, s)) return cuda_fail();
-  launch_inverse_perm(tf.V, nf.lvl_nodes, in2int, s);
   launch_net_levels(tf, in2int, nf, d_sc, nullptr, s);
-  c->launches += 2;
+  ++c->launches;
   std::vector<int32_t> sc_cnt(kSizeClasses);
   if (cudaMemcpyAsync(sc_cnt.data(), d_sc, sizeof(int32_t) * kSizeClasses, cudaMemcpyDeviceToHost, s) ||
       cudaStreamSynchronize(s))
@@ -567,7 +566,7 @@ la_status la_load_nets(la_ctx* c, const la_net_desc* nd) {
     for (const void* q : need)
       if (!q) return fail(set_err(c, LA_ERR_STATE, "la_load_nets: internal allocation missing"));
   }
-  launch_renumber(tf, in2int, nf, s);
+  launch_renumber(tf, in2int, key_of, int64_t(nbk), nf, s);
   ++c->launches;
   {
     // the segments by (direction, line), for the demand pass
@@ -579,7 +578,7 @@ la_status la_load_nets(la_ctx* c, const la_net_desc* nd) {
         (st = na.get(c, &nf.seg_node, std::max<size_t>(S, 1))) || (st = na.get(c, &nf.seg_geo, std::max<size_t>(S, 1))))
       return fail(st);
     if (cudaMemsetAsync(d_scnt, 0, sizeof(int32_t) * nkeys, s)) return cuda_fail();
-    launch_seg_sort(nf, nl0, d_scnt, nullptr, nullptr, nullptr, s);
+    launch_seg_sort(nf, nl0, nkeys, d_scnt, nullptr, nullptr, nullptr, s);
     std::vector<int32_t> scnt(nkeys);
     if (cudaMemcpyAsync(scnt.data(), d_scnt, sizeof(int32_t) * nkeys, cudaMemcpyDeviceToHost, s) ||
         cudaStreamSynchronize(s))
@@ -596,7 +595,7 @@ la_status la_load_nets(la_ctx* c, const la_net_desc* nd) {
     if (cudaMemcpyAsync(nf.seg_off, scur.data(), sizeof(int64_t) * (nkeys + 1), cudaMemcpyHostToDevice, s) ||
         cudaMemcpyAsync(d_scur, scur.data(), sizeof(int64_t) * nkeys, cudaMemcpyHostToDevice, s))
       return cuda_fail();
-    launch_seg_sort(nf, nl0, nullptr, d_scur, nf.seg_node, nf.seg_geo, s);
+    launch_seg_sort(nf, nl0, nkeys, nullptr, d_scur, nf.seg_node, nf.seg_geo, s);
     c->launches += 2;
     nf.S = int64_t(S);
   }
@@ -851,6 +850,28 @@ static void plan_from_memo(la_ctx* c) {
   c->plan = b;
 }
 
+// The current plan's split, block, grid and caching with tail threshold T
+// (0: no tail).  The graphs and constant caches stay with the plan; a graph
+// replays only if its signature, which holds the tail level, still matches.
+static void set_tail(la_ctx* c, int T) {
+  const BatchPlan& o = c->plan;
+  BatchPlan b = make_plan(c, o.k, o.block, false, T);
+  b.grid = o.grid;
+  b.cached = o.cached;
+  b.tuned = o.tuned;
+  b.best_ms = o.best_ms;
+  b.trials = 0;
+  for (int i = 0; i < 2; ++i) {
+    b.exec[i] = o.exec[i];
+    b.graph_launches[i] = o.graph_launches[i];
+    b.graph_sig[i] = o.graph_sig[i];
+    for (int j = 0; j < 5; ++j) b.w[i][j] = o.w[i][j];
+    b.cache_wd[i] = o.cache_wd[i];
+    b.cache_wcap[i] = o.cache_wcap[i];
+  }
+  c->plan = b;
+}
+
 // The round after the penalty prefix, as one CUDA graph (captured once per
 // weights and parameter set on the context's own capture stream, replayed on
 // the caller's stream every round; the caller's stream may be the legacy
@@ -920,6 +941,7 @@ la_status la_assign_round(la_ctx* c, const la_round_params* p, la_round_stats* s
     return set_err(c, LA_ERR_STATE, "la_assign_round: no adjoint weights yet (call la_reweight_adjoint)");
   if (p->no_look_ahead != 0 && p->no_look_ahead != 1)
     return set_err(c, LA_ERR_INVALID, "la_assign_round: no_look_ahead must be 0 or 1");
+  if (p->tail_threshold < 0) return set_err(c, LA_ERR_INVALID, "la_assign_round: tail_threshold must be >= 0");
   const double* W = p->weights == LA_WEIGHTS_ADJOINT ? f.W_adj : f.W_eq4;
   const double* rho = p->weights == LA_WEIGHTS_ADJOINT ? f.rho_adj : f.rho_eq4;
   if (p->no_look_ahead) {
@@ -952,6 +974,8 @@ la_status la_assign_round(la_ctx* c, const la_round_params* p, la_round_stats* s
   if (batched) {
     TRY(batched_caches(c, w, W, si, s));
     if (!c->plan.tuned) TRY(autotune(c, w, W, rho, si, s));
+    const int T = p->tail_threshold > 0 ? p->tail_threshold : c->memo.tail_T;
+    if (T != c->plan.tail_T) set_tail(c, T);
   }
   CK(cudaEventRecord(c->ev[0], s));
   if (batched) {

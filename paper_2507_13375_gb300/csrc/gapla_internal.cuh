@@ -279,29 +279,30 @@ namespace gapla {
 // otherwise internal -> public (pub is written).
 void launch_grid_to_internal(const LayerInfo& li, int X, int Y, const int32_t* pub, int32_t* inter,
                              bool to_internal, unsigned long long* err, cudaStream_t s);
-// d_max: [0] max height, [1] max batch id
+// d_max: [0] max height, [1] max batch id, [2] set when a net range is bad
 void launch_forest_prepare(la_ctx* c, Forest& f, const la_net_desc* d, int* d_max, cudaStream_t s);
 // Between two batches of a round: the demand of the nodes [lo, hi) moves from
 // their old layers (layer_old, or none) to their new ones, into the
 // difference array (global atomics).
 void launch_demand_delta(la_ctx* c, int64_t lo, int64_t hi, const int8_t* layer_old, cudaStream_t s);
-// batch: the input's per-net batch ids (or null); hmax1 = Hmax + 1
-void launch_level_sort(Forest& f, const int32_t* batch, int hmax1, int32_t* lvl_cnt, int64_t* lvl_cursor,
-                       cudaStream_t s);
+// batch: the input's per-net batch ids (or null); hmax1 = Hmax + 1; nkeys buckets;
+// counts (lvl_cnt non-null, zeroed), then placement (lvl_cursor holding the
+// bucket offsets) into in2int[input id] = internal id and key_of[input id] = bucket
+void launch_level_sort(Forest& f, const int32_t* batch, int hmax1, int64_t nkeys, int32_t* lvl_cnt,
+                       int64_t* lvl_cursor, int32_t* in2int, int32_t* key_of, cudaStream_t s);
 // segments by (direction, line): counts (cnt non-null, zeroed), then placement
 // (cursor holding the key offsets)
-void launch_seg_sort(const Forest& f, int nl0, int32_t* cnt, int64_t* cursor, int32_t* seg_node, uint64_t* seg_geo,
-                     cudaStream_t s);
-// in2int[input id] = internal id
-void launch_inverse_perm(int64_t V, const int32_t* int2in, int32_t* in2int, cudaStream_t s);
+void launch_seg_sort(const Forest& f, int nl0, int nkeys, int32_t* cnt, int64_t* cursor, int32_t* seg_node,
+                     uint64_t* seg_geo, cudaStream_t s);
 // per-net level lists and the big-net queue (input-order forest `in`, internal ids via in2int)
 void launch_net_levels(const Forest& in, const int32_t* in2int, Forest& out, int32_t* sc_cnt, int64_t* sc_cur,
                        cudaStream_t s);
-void launch_weights_eq4(const LayerInfo& li, Forest& f, cudaStream_t s);
 void launch_check_assignment(la_ctx* c, const int8_t* layer, const int8_t* b, const int8_t* t,
                              cudaStream_t s);
-// input-order forest `in` (after prepare, level sort and weights) -> internal order `out`
-void launch_renumber(const Forest& in, const int32_t* in2int, Forest& out, cudaStream_t s);
+// input-order forest `in` (after prepare and level sort) -> internal order `out`,
+// out.lvl_nodes[internal id] = input id
+void launch_renumber(const Forest& in, const int32_t* in2int, const int32_t* key_of, int64_t nkeys, Forest& out,
+                     cudaStream_t s);
 // dst[i] = src[perm[i]] (gather into internal order) or dst[perm[i]] = src[i] (scatter)
 void launch_permute8(int64_t V, const int32_t* perm, const int8_t* src, int8_t* dst, bool gather, cudaStream_t s);
 void launch_permute64(int64_t V, const int32_t* perm, const double* src, double* dst, bool gather, cudaStream_t s);

@@ -275,11 +275,12 @@ def test_malformed_forest_is_rejected(la, case):
 # Batched form (size buckets, persistent block-per-net kernels, autotuner,
 # CUDA graph): bit-identical to the plain form and to the oracle.
 # ---------------------------------------------------------------------------
-def _rounds(a, la, mode, n, weights=None, adjoint=False):
+def _rounds(a, la, mode, n, weights=None, adjoint=False, tail_threshold=0):
     out = []
     for r in range(n):
         src = la.LA_WEIGHTS_ADJOINT if (adjoint and r > 0) else la.LA_WEIGHTS_EQ4
-        st = a.assign_round(mode=mode, reset=(r == 0), weights=src, **(weights or la.DEFAULT_WEIGHTS))
+        st = a.assign_round(mode=mode, reset=(r == 0), weights=src, tail_threshold=tail_threshold,
+                            **(weights or la.DEFAULT_WEIGHTS))
         got = dict(zip(("layer", "b", "t"), (x.cpu().numpy() for x in a.get_assignment())))
         got["D"], got["H"] = (x.cpu().numpy() for x in a.get_state())
         got["J"] = a.get_net_cost().cpu().numpy()
@@ -474,20 +475,24 @@ def _chains(n, depth, X, Y, seed):
 
 
 def test_batched_tail_kernels_equal_plain(la):
-    """Deep trees (chains of 800 levels beside a Zipf forest): the tuner puts
-    the top levels in the one-block tail kernels, and the rounds equal the
-    plain form's bit for bit."""
+    """Deep trees (chains of 800 levels beside a Zipf forest): the top
+    small-net levels in the one-block tail kernels (tail_threshold), with the
+    tuner's own plan, and the plain form give the same rounds bit for bit."""
     wl = fg.WORKLOADS[4].scaled(4000)
     grid = fg.make_grid(wl, 21)
     forest = merge_forests([fg.make_forest(wl, 21)] + _chains(100, 800, wl.X, wl.Y, 21))
     a = _assigner(la, grid, forest)
-    batched = _rounds(a, la, la.LA_MODE_BATCHED, 3, adjoint=True)
-    st = batched[0]["stats"]
-    assert st["batch_tail_level"] < st["batch_levels"], st
+    tail = _rounds(a, la, la.LA_MODE_BATCHED, 3, adjoint=True, tail_threshold=32768)
+    for q in tail:
+        assert q["stats"]["batch_tail_level"] < q["stats"]["batch_levels"], q["stats"]
+    tuned = _rounds(a, la, la.LA_MODE_BATCHED, 3, adjoint=True)
     plain = _rounds(a, la, la.LA_MODE_PLAIN, 3, adjoint=True)
-    for r, (p, q) in enumerate(zip(batched, plain)):
+    for r, (p, q, u) in enumerate(zip(tail, plain, tuned)):
         for k in ("layer", "b", "t", "D", "H", "J"):
             assert np.array_equal(p[k], q[k]), (r, k)
+            assert np.array_equal(u[k], q[k]), (r, k)
+    with pytest.raises(RuntimeError, match="tail_threshold"):
+        a.assign_round(mode=la.LA_MODE_BATCHED, reset=True, tail_threshold=-1, **la.DEFAULT_WEIGHTS)
 
 
 def test_elmore_of_the_assignment(la):
