@@ -150,6 +150,16 @@ def job_rate(world: int, units_per_rank: float, ms: float) -> float:
     return world * units_per_rank / (ms * 1e-3)
 
 
+# the forest arrays la_load_nets takes, with their element types
+INPUT_KEYS = ("net_ptr", "x", "y", "parent", "pin_layer", "sink_cap", "kappa", "r_drv")
+
+
+def _input_dtypes():
+    import torch
+    return dict(net_ptr=torch.int64, x=torch.int32, y=torch.int32, parent=torch.int32, pin_layer=torch.int8,
+                sink_cap=torch.float64, kappa=torch.float64, r_drv=torch.float64)
+
+
 def nvtx_push(torch, name):
     """Mark the timed region for profilers (ncu --nvtx --nvtx-include name/)."""
     try:
@@ -299,9 +309,7 @@ def bench_gpu(args):
     value = job_rate(world, N * wl.rounds, step_ms)
 
     # ---- end to end through the C ABI, inputs from pinned host memory ----
-    keys = ("net_ptr", "x", "y", "parent", "pin_layer", "sink_cap", "kappa", "r_drv")
-    dt = dict(net_ptr=torch.int64, x=torch.int32, y=torch.int32, parent=torch.int32, pin_layer=torch.int8,
-              sink_cap=torch.float64, kappa=torch.float64, r_drv=torch.float64)
+    keys, dt = INPUT_KEYS, _input_dtypes()
     host = {k: torch.from_numpy(np.ascontiguousarray(forest[k])).to(dt[k]).pin_memory() for k in keys}
     devb = {k: torch.empty_like(host[k], device="cuda") for k in keys}
     out_host = [torch.empty(V, dtype=torch.int8).pin_memory() for _ in range(3)]
@@ -311,10 +319,8 @@ def bench_gpu(args):
     # the host-to-device copies spread over four streams (several copy engines)
     main_s = torch.cuda.current_stream()
     copy_s = [torch.cuda.Stream() for _ in range(4)]
-    torch.cuda.synchronize()
-    w0 = time.perf_counter()
-    e_start.record()
-    for _ in range(e2e_steps):
+
+    def copy_inputs():
         for i, k in enumerate(keys):
             cs = copy_s[i % len(copy_s)]
             cs.wait_stream(main_s)
@@ -322,6 +328,12 @@ def bench_gpu(args):
                 devb[k].copy_(host[k], non_blocking=True)
         for cs in copy_s:
             main_s.wait_stream(cs)
+
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    e_start.record()
+    for _ in range(e2e_steps):
+        copy_inputs()
         a.load_nets(devb)
         run_step(a, la, wl.rounds, mode, weights, False, torch)
         lay, bb, tt_ = a.get_assignment()
@@ -331,6 +343,16 @@ def bench_gpu(args):
     torch.cuda.synchronize()
     e2e_ms = max_over_ranks(e_start.elapsed_time(e_end) / e2e_steps, dist, red_dev)
     e2e_wall_ms = max_over_ranks((time.perf_counter() - w0) * 1e3 / e2e_steps, dist, red_dev)
+    # its copy and load parts, once more after the timed steps
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    torch.cuda.synchronize()
+    ev[0].record()
+    copy_inputs()
+    ev[1].record()
+    a.load_nets(devb)
+    ev[2].record()
+    torch.cuda.synchronize()
+    e2e_h2d_ms, e2e_load_ms = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
 
     # ---- roofline of the dominant kernel (the DP) ----
     # GB300 issues FP64 at 2 FMA/clk/SM: 152 SMs x 2 x 2070 MHz x 2 flops
@@ -410,6 +432,7 @@ def bench_gpu(args):
         "roofline": roofline,
         "e2e": {"value": job_rate(world, N * wl.rounds, e2e_ms), "unit": "nets/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "ms_per_step": round(e2e_ms, 3),
+                "h2d_ms": round(e2e_h2d_ms, 3), "load_ms": round(e2e_load_ms, 3),
                 "wall_ms_per_step": round(e2e_wall_ms, 3)},
         "gpu_launches": int(launches),
         "plain_form": plain,
@@ -498,7 +521,9 @@ def bench_reference(args):
 
 def profile_case(args):
     """A short run for ncu: load the workload, `--rounds` rounds and one adjoint
-    reweighting plus an Elmore forward, no timing, no CPU baseline."""
+    reweighting plus an Elmore forward, no timing, no CPU baseline; with
+    `--reloads K`, K reloads of the forest before the rounds."""
+    import numpy as np
     import torch
 
     import forestgen as fg
@@ -513,6 +538,22 @@ def profile_case(args):
     a = la.LayerAssigner(0)
     a.load_grid(grid)
     a.load_nets(forest)
+    load_ms = []
+    if args.reloads:
+        # reloads of the same forest from device buffers; the last one inside
+        # the NVTX range load_timed (ncu --nvtx --nvtx-include load_timed/)
+        dt = _input_dtypes()
+        devb = {k: torch.from_numpy(np.ascontiguousarray(forest[k])).to(dt[k]).cuda() for k in INPUT_KEYS}
+        for i in range(args.reloads):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            if i == args.reloads - 1:
+                nvtx_push(torch, "load_timed")
+            a.load_nets(devb)
+            torch.cuda.synchronize()
+            if i == args.reloads - 1:
+                nvtx_pop(torch)
+            load_ms.append(round((time.perf_counter() - t0) * 1e3, 3))
     mode = la.LA_MODE_BATCHED if args.mode == "batched" else la.LA_MODE_PLAIN
     for r in range(args.rounds):
         st = a.assign_round(mode=mode, reset=(r == 0), weights=la.LA_WEIGHTS_EQ4 if r == 0 else la.LA_WEIGHTS_ADJOINT)
@@ -520,7 +561,8 @@ def profile_case(args):
     a.elmore_assignment()
     torch.cuda.synchronize()
     print(json.dumps({"profile_case": wl.name, "nets": wl.num_nets, "nodes": int(forest["num_nodes"]),
-                      "rounds": args.rounds, "last_round_ms": st["ms"], "device_bytes": a.device_bytes()}))
+                      "rounds": args.rounds, "last_round_ms": st["ms"], "device_bytes": a.device_bytes(),
+                      "reload_wall_ms": load_ms}))
 
 
 def ablation(args):
@@ -603,6 +645,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", action="store_true", help="short untimed run for ncu captures")
     ap.add_argument("--rounds", type=int, default=1, help="rounds of the --profile run")
+    ap.add_argument("--reloads", type=int, default=0,
+                    help="--profile: reload the forest from device buffers this many times (the last one inside "
+                         "the NVTX range load_timed)")
     ap.add_argument("--nets", type=int, default=0,
                     help="--profile / --ablation: the workload's shape scaled to this many nets")
     ap.add_argument("--ablation", action="store_true",
