@@ -184,6 +184,9 @@ typedef struct {
   int32_t batch_levels;    /* levels of the small nets (the level waves + tail)   */
   int32_t batch_tail_level;/* first level run by the one-block tail kernels
                             * (= batch_levels: no tail)                          */
+  int32_t batch_graph_captured; /* 1: this round captured its CUDA graph (first
+                            * round of a weight source, or new addresses, shape,
+                            * plan or weights); 0: it replayed the kept graph    */
 } la_round_stats;
 
 /* Run one round against the current snapshot (D, H): every net sees the same

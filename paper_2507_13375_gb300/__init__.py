@@ -75,7 +75,7 @@ class RoundStats(ctypes.Structure):
                 ("launches", ctypes.c_int64), ("batch_split", ctypes.c_int32), ("batch_block", ctypes.c_int32),
                 ("batch_big_nets", ctypes.c_int64), ("batch_cached", ctypes.c_int32), ("batch_trials", ctypes.c_int32),
                 ("batch_tune_ms", ctypes.c_double), ("batch_levels", ctypes.c_int32),
-                ("batch_tail_level", ctypes.c_int32)]
+                ("batch_tail_level", ctypes.c_int32), ("batch_graph_captured", ctypes.c_int32)]
 
 
 _lib = None
@@ -212,7 +212,8 @@ def la_assign_round(ctx, mode: int = LA_MODE_PLAIN, weights: int = LA_WEIGHTS_EQ
                 wl_per_layer=list(s.wl_per_layer), ms=s.ms, ms_dp=s.ms_dp, ms_backtrack=s.ms_backtrack,
                 ms_demand=s.ms_demand, launches=s.launches, batch_split=s.batch_split, batch_block=s.batch_block,
                 batch_big_nets=s.batch_big_nets, batch_cached=s.batch_cached, batch_trials=s.batch_trials,
-                batch_tune_ms=s.batch_tune_ms, batch_levels=s.batch_levels, batch_tail_level=s.batch_tail_level)
+                batch_tune_ms=s.batch_tune_ms, batch_levels=s.batch_levels, batch_tail_level=s.batch_tail_level,
+                batch_graph_captured=s.batch_graph_captured)
 
 
 def la_get_assignment(ctx, layer, b, t):

@@ -80,6 +80,16 @@ struct DevPool {
     blocks.erase(it);
     return p;
   }
+  // the block at p of b bytes, if the pool holds it
+  void* take_exact(void* p, size_t b) {
+    auto r = blocks.equal_range(b);
+    for (auto it = r.first; it != r.second; ++it)
+      if (it->second.p == p) {
+        blocks.erase(it);
+        return p;
+      }
+    return nullptr;
+  }
   void put(void* p, size_t b) { blocks.emplace(b, Blk{p, gen}); }
   void free_older_than(uint64_t g) {
     for (auto it = blocks.begin(); it != blocks.end();) {
@@ -95,22 +105,32 @@ struct DevPool {
 };
 
 // Device allocations of one load (grid or forest), released together (into
-// the pool when there is one).
+// the pool when there is one).  With a hint (the previous load's list, in
+// call order), the i-th allocation takes the block the i-th took last time
+// when the pool holds it: a same-shaped reload puts every array at its old
+// address.
 struct Allocs {
   std::vector<std::pair<void*, size_t>> list;
   size_t bytes = 0;
   DevPool* pool = nullptr;
+  DevPool* spare = nullptr;  // another pool, emptied too before an allocation fails
+  const std::vector<std::pair<void*, size_t>>* hint = nullptr;
+  size_t next = 0;
   template <typename T>
   la_status get(la_ctx* c, T** p, size_t n) {
     size_t b = n * sizeof(T);
     if (b == 0) b = 16;
     b = (b + 255) & ~size_t(255);
-    void* q = pool ? pool->take(b) : nullptr;
+    void* q = nullptr;
+    if (pool && hint && next < hint->size() && (*hint)[next].second == b) q = pool->take_exact((*hint)[next].first, b);
+    ++next;
+    if (!q && pool) q = pool->take(b);
     if (!q) {
       cudaError_t e = cudaMalloc(&q, b);
-      if (e == cudaErrorMemoryAllocation && pool && !pool->blocks.empty()) {
+      if (e == cudaErrorMemoryAllocation && pool && (!pool->blocks.empty() || (spare && !spare->blocks.empty()))) {
         cudaGetLastError();
         pool->clear();  // give the pooled blocks back and try once more
+        if (spare) spare->clear();
         e = cudaMalloc(&q, b);
       }
       if (e != cudaSuccess) {
@@ -139,10 +159,18 @@ struct Allocs {
 void gapla::set_noctx_error(const std::string& msg) { g_create_err = msg; }
 
 // Allocation groups live beside the context (kept out of the shared header).
+// The forest's arrays and the loads' temporaries keep separate pools, so a
+// temporary never takes the block an array of the next forest wants.
 struct la_ctx_allocs {
-  DevPool pool;
+  DevPool pool;   // temporaries (and the grid)
+  DevPool fpool;  // forest arrays
   Allocs grid, forest;
-  la_ctx_allocs() { grid.pool = forest.pool = &pool; }
+  la_ctx_allocs() {
+    grid.pool = &pool;
+    forest.pool = &fpool;
+    grid.spare = &fpool;
+    forest.spare = &pool;
+  }
 };
 static la_ctx_allocs* allocs_of(la_ctx* c) { return reinterpret_cast<la_ctx_allocs*>(c->alloc_groups); }
 
@@ -233,6 +261,7 @@ la_status la_destroy(la_ctx* c) {
     a->forest.release();
     a->grid.release();
     a->pool.clear();
+    a->fpool.clear();
     delete a;
   }
   if (c->d_err) cudaFree(c->d_err);
@@ -262,6 +291,7 @@ la_status la_device_bytes(const la_ctx* c, size_t* bytes) {
   la_ctx_allocs* a = allocs_of(const_cast<la_ctx*>(c));
   size_t pooled = 0;
   for (const auto& kv : a->pool.blocks) pooled += kv.first;
+  for (const auto& kv : a->fpool.blocks) pooled += kv.first;
   *bytes = a->grid.bytes + a->forest.bytes + pooled + sizeof(Stats) + sizeof(unsigned long long);
   return LA_OK;
 }
@@ -439,8 +469,13 @@ la_status la_load_nets(la_ctx* c, const la_net_desc* nd) {
   const size_t N = size_t(nf.N), V = size_t(nf.V);
   la_ctx_allocs* al = allocs_of(c);
   const uint64_t gen0 = ++al->pool.gen;
+  al->fpool.gen = gen0;
   Allocs na, ta;  // kept / temporary
-  na.pool = ta.pool = &al->pool;
+  na.pool = &al->fpool;
+  ta.pool = &al->pool;
+  na.spare = &al->pool;
+  ta.spare = &al->fpool;
+  std::vector<std::pair<void*, size_t>> prev_list;  // the old forest's arrays, in allocation order
   BatchPlan old_plan;  // the old forest's plan, once the old forest is released
   la_status st = LA_OK;
   auto fail = [&](la_status s2) {
@@ -453,15 +488,15 @@ la_status la_load_nets(la_ctx* c, const la_net_desc* nd) {
   auto cuda_fail = [&]() { return fail(set_err(c, LA_ERR_CUDA, "la_load_nets: %s", cudaGetErrorString(cudaGetLastError()))); };
 #define GETK(p, n) if (st == LA_OK) st = na.get(c, &(p), (n))
 #define GETT(p, n) if (st == LA_OK) st = ta.get(c, &(p), (n))
-  GETK(nf.net_ptr, N + 1); GETK(nf.r_drv, N);
+  // the input-order forest (temporaries); the kept arrays are allocated only
+  // once the old forest is released, so that they can take its blocks
+  GETT(tf.net_ptr, N + 1); GETT(tf.r_drv, N);
   GETT(tf.parent_g, V); GETT(tf.net_of, V); GETT(tf.pin, V); GETT(tf.sink_cap, V); GETT(tf.kappa, V);
   GETT(tf.geo, V); GETT(tf.child_start, V); GETT(tf.nch, V); GETT(tf.child_list, V);
   GETT(tf.height, V); GETT(tf.W_eq4, V); GETT(tf.rho_eq4, V);
   int* d_hmax = nullptr;  // [0] max height, [1] max batch id, [2] bad net range
   GETT(d_hmax, 3);
   if (st) return fail(st);
-  tf.net_ptr = nf.net_ptr;
-  tf.r_drv = nf.r_drv;
   if (reset_dev_err(c) || cudaMemsetAsync(d_hmax, 0, 3 * sizeof(int), s)) return cuda_fail();
   launch_forest_prepare(c, tf, nd, d_hmax, s);
   int code;
@@ -470,13 +505,21 @@ la_status la_load_nets(la_ctx* c, const la_net_desc* nd) {
   if ((st = read_dev_err(c, &code, &idx))) return fail(st);
   if (code) return fail(set_err(c, LA_ERR_INVALID, "la_load_nets: %s (%s %lld)", dev_err_name(code),
                                  code == DE_NETPTR ? "net" : "node", idx));
-  // The input is valid: the old forest's blocks go back to the pool, where the
-  // new forest's arrays find them (same shape: same blocks, same addresses).
-  // Its batched plan is kept aside until the new forest's plan is known.
+  // The input is valid: the old forest's blocks go back to the forest pool,
+  // where the new forest's arrays find them, each the block the same
+  // allocation took last time (same shape: same addresses).  Its batched plan
+  // is kept aside until the new forest's plan is known.
   old_plan = c->plan;
   c->plan = BatchPlan();
+  prev_list = al->forest.list;
   al->forest.release();
   c->forest = Forest();
+  na.hint = &prev_list;
+  GETK(nf.net_ptr, N + 1); GETK(nf.r_drv, N);
+  if (st) return fail(st);
+  if (cudaMemcpyAsync(nf.net_ptr, tf.net_ptr, sizeof(int64_t) * (N + 1), cudaMemcpyDeviceToDevice, s) ||
+      cudaMemcpyAsync(nf.r_drv, tf.r_drv, sizeof(double) * N, cudaMemcpyDeviceToDevice, s))
+    return cuda_fail();
   int hb[2] = {0, 0};
   if (cudaMemcpy(hb, d_hmax, sizeof hb, cudaMemcpyDeviceToHost)) return cuda_fail();
   const int hmax = hb[0];
@@ -620,7 +663,10 @@ la_status la_load_nets(la_ctx* c, const la_net_desc* nd) {
   if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) return cuda_fail();
   ta.release();
   al->pool.free_older_than(gen0);  // blocks no load took since the last one
+  al->fpool.free_older_than(gen0);
   al->forest = na;
+  al->forest.hint = nullptr;  // the hint names this load's local list
+  al->forest.next = 0;
   c->forest = nf;
   plan_from_memo(c);
   // A plan taken from the memo keeps the old graphs: each replays only if the
@@ -877,13 +923,14 @@ static void set_tail(la_ctx* c, int T) {
 // the caller's stream every round; the caller's stream may be the legacy
 // default stream, which cannot be captured).
 static la_status batched_graph(la_ctx* c, const RoundW& w, const double* W, const double* rho, int si,
-                               cudaStream_t s_run) {
+                               cudaStream_t s_run, bool* captured) {
   BatchPlan& bp = c->plan;
   cudaStream_t s = c->s_cap;
   const double wv[5] = {w.w_cong, w.w_via, w.w_cap, w.w_d, w.hist_w};
   const uint64_t sig = round_signature(c, si, W, rho);
   bool same = bp.exec[si] != nullptr && bp.graph_sig[si] == sig;
   for (int i = 0; i < 5 && same; ++i) same = bp.w[si][i] == wv[i];
+  *captured = !same;
   if (!same) {
     if (bp.exec[si]) {
       cudaGraphExecDestroy(bp.exec[si]);
@@ -977,9 +1024,10 @@ la_status la_assign_round(la_ctx* c, const la_round_params* p, la_round_stats* s
     const int T = p->tail_threshold > 0 ? p->tail_threshold : c->memo.tail_T;
     if (T != c->plan.tail_T) set_tail(c, T);
   }
+  bool captured = false;
   CK(cudaEventRecord(c->ev[0], s));
   if (batched) {
-    TRY(batched_graph(c, w, W, rho, si, s));
+    TRY(batched_graph(c, w, W, rho, si, s, &captured));
   } else if (f.nbatch == 1) {
     CK(cudaEventRecord(c->ev[1], s));
     for (int h = 0; h <= f.Hmax; ++h) launch_dp_level(c, w, W, rho, h, kSizeClasses - 1, kNoCache, s);
@@ -1074,6 +1122,7 @@ la_status la_assign_round(la_ctx* c, const la_round_params* p, la_round_stats* s
     stats->batch_trials = c->plan.trials;
     stats->batch_levels = c->plan.Hs + 1;
     stats->batch_tail_level = std::min(c->plan.tail_h, c->plan.Hs + 1);
+    stats->batch_graph_captured = captured ? 1 : 0;
   }
   return LA_OK;
 }

@@ -345,10 +345,13 @@ def test_batched_reload_reuses_tuning(la):
     a = _assigner(la, grid, forest)
     first = _rounds(a, la, la.LA_MODE_BATCHED, 2)
     assert first[0]["stats"]["batch_trials"] > 0
+    assert [q["stats"]["batch_graph_captured"] for q in first] == [1, 0]
     a.load_nets(forest)
     again = _rounds(a, la, la.LA_MODE_BATCHED, 2)
     assert again[0]["stats"]["batch_trials"] == 0
     assert again[0]["stats"]["batch_split"] == first[0]["stats"]["batch_split"]
+    # the reloaded forest's arrays sit at the same addresses: the graph replays
+    assert [q["stats"]["batch_graph_captured"] for q in again] == [0, 0]
     for p, q in zip(first, again):
         for k in ("layer", "b", "t", "D", "H", "J"):
             assert np.array_equal(p[k], q[k]), k
@@ -360,6 +363,7 @@ def test_batched_reload_reuses_tuning(la):
     a.load_nets(vals)
     rb = _rounds(a, la, la.LA_MODE_BATCHED, 2, adjoint=True)
     assert rb[0]["stats"]["batch_trials"] == 0
+    assert rb[0]["stats"]["batch_graph_captured"] == 0
     rp = _rounds(a, la, la.LA_MODE_PLAIN, 2, adjoint=True)
     for p, q in zip(rb, rp):
         for k in ("layer", "b", "t", "D", "H", "J"):
