@@ -479,8 +479,9 @@ void launch_check_assignment(la_ctx* c, const int8_t* layer, const int8_t* b, co
 // level sort placed (kHistT x kHistItems nodes), so each key's nodes of the
 // tile hold one run of positions; sorting the tile by position in shared
 // memory then only needs each key's count and first position, and every
-// field is written run by run, coalesced.  Plain form (more keys than the
-// shared counters hold): each thread writes its node's fields where they go.
+// field is written run by run, coalesced.  Plain form (more than kRnMaxKeys
+// keys, or the level sort's global-counter path): each thread writes its
+// node's fields where they go.
 struct RenumArgs {
   int64_t V;
   const int32_t *in2int, *key_of;
