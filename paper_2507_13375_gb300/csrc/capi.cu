@@ -906,7 +906,7 @@ static void set_tail(la_ctx* c, int T) {
   b.cached = o.cached;
   b.tuned = o.tuned;
   b.best_ms = o.best_ms;
-  b.trials = 0;
+  b.trials = o.trials;  // the trials that chose the shape (0: the memo's)
   for (int i = 0; i < 2; ++i) {
     b.exec[i] = o.exec[i];
     b.graph_launches[i] = o.graph_launches[i];
