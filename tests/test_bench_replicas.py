@@ -1,7 +1,8 @@
 """The multi-GPU form of the bench is N independent replicas (one process per
 GPU, seed = rank, no data-path collective): its host logic on 2 gloo ranks on
 the CPU - max-over-ranks timing, whole-job throughput, one forest per rank -
-and the reference arm's ranks other than 0 exiting without work."""
+and the reference arm: its ranks other than 0 exit without work, rank 0
+prints the bench line."""
 import json
 import os
 import socket
@@ -60,3 +61,24 @@ def test_reference_arm_other_ranks_exit_without_work():
                         "--warmup", "3"], env=env, capture_output=True, text=True, timeout=120)
     assert p.returncode == 0
     assert p.stdout.strip() == ""
+
+
+def test_reference_arm_line_on_rank0():
+    """Rank 0 of the reference arm (the oracle on the host cores) prints one JSON
+    line with the bench keys, a cpu_baseline describing the run and an e2e of
+    its own value with no host-device bytes."""
+    env = dict(os.environ, RANK="0", WORLD_SIZE="1", LOCAL_RANK="0")
+    p = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "0", "--workload", "1"], env=env, capture_output=True, text=True, timeout=300)
+    assert p.returncode == 0, p.stderr[-2000:]
+    lines = [l for l in p.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+              "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["value"] > 0 and d["unit"] == "nets/s" and d["higher_is_better"]
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["cpu_baseline"]["cores"] >= 1 and d["cpu_baseline"]["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": "nets/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert d["config"]["workload"] == "plain-64x64x6-2k"
