@@ -1,0 +1,38 @@
+"""The bench's algorithmic DP flop count (the roofline's numerator) on a tree
+counted by hand from the per-item costs its docstring lists."""
+import os
+import sys
+
+import numpy as np
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+import bench  # noqa: E402
+
+
+def _net(x0):
+    # root (pin) at (x0, 0) -> bend (no pin) at (x0 + 5, 0) -> sink (pin) at (x0 + 5, 3)
+    return dict(x=[x0, x0 + 5, x0 + 5], y=[0, 0, 3], parent=[-1, 0, 1], pin_layer=[0, -1, 0])
+
+
+def _forest(nets):
+    cat = {k: np.array(sum((n[k] for n in nets), []), dtype=np.int32 if k != "pin_layer" else np.int8)
+           for k in ("x", "y", "parent", "pin_layer")}
+    sizes = [len(n["x"]) for n in nets]
+    cat["net_ptr"] = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    cat["num_nodes"], cat["num_nets"] = sum(sizes), len(nets)
+    return cat
+
+
+def test_dp_flops_by_hand():
+    """Layers (H, V, H, V): two per direction.
+      root: 1 candidate; one son on 2 layers, a pin:
+            per layer 4 + 2 (son sum) + 4 (sink) + 2*2 (keys) + 2 (g) + 3 (f') = 19;
+            per node 3 + 1 (pin) = 4                                 -> 23
+      bend: 2 candidates (H); one son on 2 layers (V), no pin, not a root:
+            per layer 4 + 2 + 4 + 2 + 3 + 9 (entry) = 24; per node 3 + 1 -> 52
+      sink: 2 candidates (V); no son, a pin, not a root:
+            per layer 4 + 4 + 2 + 9 = 19; per node 3 + 1 + 1 = 5     -> 43
+    118 per net; a second net checks the per-net parent offsets."""
+    dirs = (0, 1, 0, 1)
+    assert bench.dp_algorithmic_flops(_forest([_net(0)]), dirs) == 118.0
+    assert bench.dp_algorithmic_flops(_forest([_net(0), _net(20)]), dirs) == 236.0
