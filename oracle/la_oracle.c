@@ -462,7 +462,7 @@ void or_demand(const or_grid* g, const or_forest* f, const int8_t* layer, const 
 }
 
 /* ------------------------------------------------------------------------ */
-/* Elmore delay on the RC tree of an assignment, and its adjoint             */
+/* Elmore delay (Sec. II-C, the d_34 example of Sec. III-D) and its adjoint  */
 /* ------------------------------------------------------------------------ */
 /* R_seg = len r_l, C_seg = len c_l on the assigned layer; 0 at roots. */
 void or_rc_from_assignment(const or_grid* g, const or_forest* f, const int8_t* layer,
