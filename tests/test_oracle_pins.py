@@ -415,3 +415,43 @@ def test_sequential_batches_oracle():
     sel2 = batch[net_of] == 2
     assert np.array_equal(out["layer"][sel2], r1["layer"][sel2])
     assert not np.array_equal(r1["layer"], ref["layer"])  # the order changes the outcome
+
+
+# ---------------------------------------------------------------------------
+# Tie rules (reading of Alg. 3, Kernel 1 and Kernel 2): exact ties resolved as
+# documented, checked against the full set of brute-force minimisers
+# ---------------------------------------------------------------------------
+def _tie_check(case):
+    from util_inputs import TIE_WEIGHTS
+
+    grid, forest, want_layers, want_stacks = case
+    out = oracle.assign_round(grid, forest, TIE_WEIGHTS)
+    net = br.nets_of(forest)[0]
+    lay, bt, W = _net_assignment(forest, out, 0)
+    Jb, arg = br.brute_force(grid, net, out["pen"], TIE_WEIGHTS, W)
+    # w_d = 0: the DP is exact; the case has several minimisers
+    assert out["J"][0] == float(Jb)
+    assert len(arg) >= 2 and lay in arg
+    assert lay == want_layers
+    assert bt == want_stacks
+    return arg
+
+
+def test_son_takes_its_lowest_tied_layer():
+    """Kernel 1: inside a stack, a son whose keys tie on two layers takes the
+    lower one (here the H leaf on layer 0, not 2)."""
+    from util_inputs import son_tie_case
+
+    arg = _tie_check(son_tie_case())
+    assert [0, 2, 3] in arg  # the other minimiser, which the rule excludes
+
+
+def test_stack_tie_fewest_vias_then_lowest_bottom():
+    """Kernel 2: stacks of equal f' are ordered by via count, then by their
+    bottom layer (here [1, 2] over [2, 3] at the bend, so the leaf goes on
+    layer 1, not 3; and not the wider [0, 2] a lowest-bottom-first order
+    would take)."""
+    from util_inputs import stack_tie_case
+
+    arg = _tie_check(stack_tie_case())
+    assert [0, 2, 3] in arg

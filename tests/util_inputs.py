@@ -120,3 +120,37 @@ def edge_case_forest(X: int, Y: int, L: int, seed: int = 0) -> dict:
     nets.append(forest_from_rows([(-1, 4, 4, 0, 0.0, 0.0), (0, 9, 4, 0, 1.5, u()), (0, 4, 7, -1, 0.0, 0.0),
                                   (2, 1, 7, -1, 0.0, 0.0)], r_drv=150.0))
     return merge_forests(nets)
+
+
+# Exact-tie cases for the tie rules (w_d = 0, no via cost, zero snapshot): on
+# a 4-layer stack (0 H, 1 V, 2 H, 3 V) with equal unit R and C, two layers of
+# one direction whose overflow weights are equal give exactly equal keys.
+TIE_WEIGHTS = dict(w_cong=1.0, w_via=0.0, w_cap=0.0, w_d=0.0, hist_w=1.0)
+
+
+def tie_grid(ofw):
+    grid = simple_grid(12, 12, 4, (1.0, 1.0, 1.0, 1.0), (0.2, 0.2, 0.2, 0.2), (1.0, 1.0, 1.0), 0.0, cap=8)
+    grid["ofw"] = np.array(ofw, np.float64)
+    return grid
+
+
+def son_tie_case():
+    """A root (driver pin on layer 0) with an H leaf and a V leaf, both with a
+    pin on layer 0; layer 3 (V) is cheaper (overflow weight 1/2), so the root's
+    stack reaches layer 3 and holds both H layers 0 and 2, whose keys for the
+    H leaf are equal.  Returns (grid, forest, the documented layers and
+    stacks): the son takes the lowest of its tied layers."""
+    forest = forest_from_rows([(-1, 2, 2, 0, 0.0, 0.0), (0, 6, 2, 0, 1.0, 0.5), (0, 2, 7, 0, 1.0, 0.5)], r_drv=100.0)
+    return tie_grid((1.0, 1.0, 1.0, 0.5)), forest, [0, 0, 3], [(0, 3), (0, 0), (0, 3)]
+
+
+def stack_tie_case():
+    """A root (driver pin on layer 0), an H bend v without a pin, and a V leaf
+    c below it with a pin on layer 0; layer 0 is dearer for wires (overflow
+    weight 3), so v goes on layer 2, and c's layers 1 and 3 have equal keys.
+    At v the stacks [1, 2] and [2, 3] tie on cost and on via count, and wider
+    ones tie on cost.  Returns (grid, forest, the documented layers and
+    stacks): fewest vias, then the lowest b."""
+    forest = forest_from_rows([(-1, 2, 2, 0, 0.0, 0.0), (0, 8, 2, -1, 0.0, 0.0), (1, 8, 7, 0, 1.0, 0.5)],
+                              r_drv=100.0)
+    return tie_grid((3.0, 1.0, 1.0, 1.0)), forest, [0, 2, 1], [(0, 2), (1, 2), (0, 1)]
