@@ -71,6 +71,16 @@ la_status la_device_bytes(const la_ctx* ctx, size_t* bytes);
 la_status la_check(la_ctx* ctx);
 /* Number of CUDA kernels this context has launched since it was created. */
 la_status la_launch_count(const la_ctx* ctx, int64_t* launches);
+/* Failure-path hook for tests: the next step of the context that can fail in
+ * the given way reports `code` from the host side, exactly as the real
+ * failure would be reported; nothing is changed on the device and nothing
+ * faults there.  LA_ERR_OOM: the next device allocation of the context fails.
+ * LA_ERR_CUDA, LA_ERR_TIMEOUT, LA_ERR_DEVICE_CHECK: the next read of the
+ * context's device error word (la_check, la_load_grid, la_load_nets,
+ * la_assign_round with stats, la_set_assignment, la_set_state) reports that
+ * error, which poisons the context.  LA_OK clears a pending fault; any other
+ * code is LA_ERR_INVALID.  The paper has no counterpart. */
+la_status la_inject_fault(la_ctx* ctx, la_status code);
 
 /* ---------------------------------------------------------------------------
  * Grid: the GCell grid graph with per-layer edge capacity (Sec. II-A, Alg. 2
@@ -127,8 +137,9 @@ typedef struct {
  * builds the children lists, segment geometry, and the Eq. 4 edge weights W
  * and the look-ahead upstream resistances r_est (Sec. III-D).  Synchronises
  * the stream.  LA_ERR_INVALID if the forest is malformed (message names the
- * first bad node); the forest loaded before stays loaded.  After any other
- * error the context holds no forest.  A forest of the same shape as the one
+ * first bad node); the forest loaded before stays loaded, and so it does after
+ * an allocation failure (LA_ERR_OOM) before the new forest has passed
+ * validation.  After any later error the context holds no forest.  A forest of the same shape as the one
  * before reuses its device blocks and, with the batched form, its tuned plan
  * and captured rounds. */
 la_status la_load_nets(la_ctx* ctx, const la_net_desc* nets);
@@ -158,6 +169,12 @@ typedef struct {
                             * whose (node, candidate) task counts are all below T
                             * in the one-block tail kernels.  Results do not
                             * depend on it; < 0 is LA_ERR_INVALID                */
+  int32_t force_split;     /* batched form: 0 = the tuner's split; k in [4, 15] =
+                            * nets of more than 2^k nodes in the persistent
+                            * block-per-net kernels, the rest in level waves
+                            * (the tuned block and caching kept).  Results do
+                            * not depend on it; other values are
+                            * LA_ERR_INVALID                                     */
 } la_round_params;
 
 typedef struct {
@@ -247,6 +264,16 @@ la_status la_reweight_adjoint(la_ctx* ctx);
  * source (LA_WEIGHTS_EQ4 or LA_WEIGHTS_ADJOINT). */
 la_status la_get_weights(la_ctx* ctx, int32_t source, double* W, double* rho);
 
+/* Measurement helper (the paper has no counterpart): the rate of FP64 fused
+ * multiply-adds this GPU sustains, from a kernel of independent FMA chains on
+ * every SM (about 40 G FMAs, timed with CUDA events on `stream` after a
+ * warm-up launch).  The tree DP is bound by FP64 arithmetic on GB300, so its
+ * roofline is reported against this rate beside the nominal pipe peak.
+ * `device` becomes current for the call and the previous device is restored;
+ * allocates and frees a small output buffer; synchronises the stream.
+ *   dfma_per_s: host, written with the FMAs per second. */
+la_status la_probe_fp64(int device, void* stream, double* dfma_per_s);
+
 /* ---------------------------------------------------------------------------
  * Allocation-free Elmore forward pass.  The paper has no counterpart: this
  * entry point exists for callers that cannot allocate device memory at all,
@@ -254,12 +281,15 @@ la_status la_get_weights(la_ctx* ctx, int32_t source, double* W, double* rho);
  * allocator, or code on a latency-critical path that must not call
  * cudaMalloc (which may synchronise the device and takes unbounded time).
  *
- * It computes exactly what la_elmore computes (delay[v] at v's pin point for
- * pin nodes, at its junction otherwise) for a forest and an assignment given
- * directly, without a context, and makes no allocation of any kind.  Its
- * scratch (2 doubles per node) is a fixed device array compiled into the
- * library, LA_STATIC_MAX_NODES nodes large (32 MiB), which every GPU that
- * loads the library holds until the process exits.
+ * It computes what la_elmore computes (delay[v] at v's pin point for pin
+ * nodes, at its junction otherwise), with the same expressions in the same
+ * order (downstream caps summed over the sons in increasing id), so the two
+ * agree bit for bit; it takes the forest and the assignment directly, without
+ * a context, and its own code allocates nothing.  Its scratch (16 bytes per
+ * node: a downstream cap and two son links, plus a 256-byte header) is a fixed
+ * device array compiled into the library, LA_STATIC_MAX_NODES nodes large
+ * (32 MiB), which every GPU that has loaded the library's device code holds
+ * until the process exits.
  *   nets:           device pointers; net_ptr, parent, pin_layer, sink_cap and
  *                   r_drv are read (x, y, kappa are not)
  *   layer, b, t:    device, V: junction layers and via stacks (input order,
@@ -268,13 +298,20 @@ la_status la_get_weights(la_ctx* ctx, int32_t source, double* W, double* rho);
  *   R_seg, C_seg:   device, V (root entries ignored); delay: device, V output
  *   stream:         cudaStream_t to enqueue on (NULL = legacy default stream)
  * Runs on the calling thread's current CUDA device; all pointers must be on
- * it.  The first call on a device looks up the device address of the scratch
- * array (cudaGetSymbolAddress); make that first call before any stream
- * capture.  Every call uses the same scratch, which keeps the last call's
- * contents, so calls that overlap on the GPU (other streams, other host
- * threads) race.  Returns LA_ERR_INVALID for more than LA_STATIC_MAX_NODES
- * nodes or bad arguments (la_last_error(NULL) says which); a net whose parent
- * ids are out of order or whose layers are out of range gets NaN delays. */
+ * it.  The first call on a device does a one-time set-up there: with CUDA's
+ * lazy module loading the runtime loads the library's device code and commits
+ * the fixed array at that point (an allocation by the CUDA runtime, which may
+ * synchronise), and the call looks up the array's device address
+ * (cudaGetSymbolAddress).  Make one warm-up call per device before any
+ * latency-critical use and before any stream capture.  Every call uses the
+ * same scratch, which keeps the last call's contents (each call clears the
+ * flag word it needs), so calls that overlap on the GPU (other streams, other
+ * host threads) race.  Returns LA_ERR_INVALID for more than
+ * LA_STATIC_MAX_NODES nodes or bad arguments (la_last_error(NULL) says
+ * which).  Malformed input is reported in the output instead of faulting: if
+ * net_ptr does not rise strictly from 0 to num_nodes every delay is NaN; a net
+ * whose parent ids are out of order, or whose layers, pins or stacks are out
+ * of range, gets NaN delays and the other nets are computed as usual. */
 #define LA_STATIC_MAX_NODES (1 << 21)
 la_status la_elmore_static(const la_net_desc* nets, const int8_t* layer, const int8_t* b, const int8_t* t,
                            int32_t L, const double* via_r, double via_c, const double* R_seg,

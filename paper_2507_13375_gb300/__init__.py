@@ -36,7 +36,7 @@ EXPORTS = ("la_create", "la_destroy", "la_last_error", "la_set_stream", "la_devi
            "la_load_grid", "la_load_nets", "la_assign_round", "la_get_assignment", "la_set_assignment",
            "la_get_net_cost", "la_get_state", "la_set_state", "la_rc_from_assignment", "la_elmore",
            "la_elmore_backward", "la_elmore_assignment", "la_reweight_adjoint", "la_get_weights",
-           "la_elmore_static")
+           "la_inject_fault", "la_probe_fp64", "la_elmore_static")
 LA_STATIC_MAX_NODES = 1 << 21
 
 
@@ -64,7 +64,7 @@ class RoundParams(ctypes.Structure):
     _fields_ = [("w_cong", ctypes.c_double), ("w_via", ctypes.c_double), ("w_cap", ctypes.c_double),
                 ("w_d", ctypes.c_double), ("hist_w", ctypes.c_double), ("mode", ctypes.c_int32),
                 ("weights", ctypes.c_int32), ("reset", ctypes.c_int32), ("no_look_ahead", ctypes.c_int32),
-                ("tail_threshold", ctypes.c_int32)]
+                ("tail_threshold", ctypes.c_int32), ("force_split", ctypes.c_int32)]
 
 
 class RoundStats(ctypes.Structure):
@@ -101,7 +101,8 @@ def library() -> ctypes.CDLL:
         "la_rc_from_assignment": [vp, vp, vp], "la_elmore": [vp, vp, vp, vp],
         "la_elmore_backward": [vp, vp, vp, vp, vp, vp], "la_elmore_assignment": [vp, vp],
         "la_reweight_adjoint": [vp],
-        "la_get_weights": [vp, i32, vp, vp],
+        "la_get_weights": [vp, i32, vp, vp], "la_inject_fault": [vp, ctypes.c_int],
+        "la_probe_fp64": [ctypes.c_int, vp, P(ctypes.c_double)],
         "la_elmore_static": [P(NetDesc), vp, vp, vp, i32, vp, ctypes.c_double, vp, vp, vp, vp],
     }
     for name, args in sig.items():
@@ -198,11 +199,12 @@ def la_load_nets(ctx, forest: dict, device: int = 0):
 
 
 def la_assign_round(ctx, mode: int = LA_MODE_PLAIN, weights: int = LA_WEIGHTS_EQ4, reset: bool = False,
-                    stats: bool = True, look_ahead: bool = True, tail_threshold: int = 0, **w):
+                    stats: bool = True, look_ahead: bool = True, tail_threshold: int = 0, force_split: int = 0,
+                    **w):
     ww = dict(DEFAULT_WEIGHTS)
     ww.update(w)
     p = RoundParams(ww["w_cong"], ww["w_via"], ww["w_cap"], ww["w_d"], ww["hist_w"], int(mode), int(weights),
-                    1 if reset else 0, 0 if look_ahead else 1, int(tail_threshold))
+                    1 if reset else 0, 0 if look_ahead else 1, int(tail_threshold), int(force_split))
     if not stats:
         _check(ctx, library().la_assign_round(ctx, ctypes.byref(p), None))
         return None
@@ -260,6 +262,12 @@ def la_get_weights(ctx, source, W, rho):
     _check(ctx, library().la_get_weights(ctx, int(source), _ptr(W), _ptr(rho)))
 
 
+def la_inject_fault(ctx, code: int):
+    """The next step of the context that can fail in this way reports `code`
+    from the host side (a test hook: nothing faults on the device)."""
+    _check(ctx, library().la_inject_fault(ctx, int(code)))
+
+
 def batches_by_criticality(crit, slack=None, critical_frac: float = 0.5, slack_ratio: float = 0.7):
     """Net batches after Alg. 1 (Sec. III-A), from per-net criticality `crit`
     (>= 0; the paper counts critical paths through the net) and optionally
@@ -305,21 +313,54 @@ def batches_by_criticality(crit, slack=None, critical_frac: float = 0.5, slack_r
     return out.astype(np.int32)
 
 
+def la_probe_fp64(device: int = 0, stream=None) -> float:
+    """FP64 fused multiply-adds per second that this GPU sustains (measured)."""
+    lib = library()
+    if stream is None:
+        stream = torch.cuda.current_stream(device).cuda_stream
+    r = ctypes.c_double()
+    st = lib.la_probe_fp64(int(device), ctypes.c_void_p(stream), ctypes.byref(r))
+    if st != LA_OK:
+        raise LaError(st, lib.la_last_error(None).decode())
+    return float(r.value)
+
+
 def la_elmore_static(nets: dict, layer, b, t, L: int, via_r, via_c: float, R, C, delay, stream=None,
                      num_nodes: int | None = None):
     """The allocation-free Elmore forward pass (see include/gapla.h).
 
-    nets: CUDA tensors net_ptr, parent, pin_layer, sink_cap, r_drv (x, y,
-    kappa optional); layer, b, t, R, C, delay: CUDA tensors in input order.
-    Nothing is allocated on the device by the library for this call."""
+    nets: CUDA tensors net_ptr (int64), parent (int32), pin_layer (int8),
+    sink_cap and r_drv (float64); layer, b, t (int8), R, C, delay (float64):
+    CUDA tensors in input order, all on the current CUDA device.  The library
+    allocates nothing on the device for this call.  The types, device and
+    sizes are checked here before the C call (the C side sees bare pointers);
+    `num_nodes` overrides the node count passed to C (only to exercise the
+    library's own size refusal: the arrays are not read then)."""
     lib = library()
-    keep = np.ascontiguousarray(via_r, np.float64)
+    L = int(L)
+    keep = np.ascontiguousarray(via_r, np.float64).ravel()
+    if keep.size < L - 1:
+        raise LaError(LA_ERR_INVALID, f"la_elmore_static: via_r has {keep.size} entries, needs L - 1 = {L - 1}")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    V = int(nets["parent"].numel())
+    N = int(nets["r_drv"].numel())
+    want = dict(net_ptr=(torch.int64, N + 1), parent=(torch.int32, V), pin_layer=(torch.int8, V),
+                sink_cap=(torch.float64, V), r_drv=(torch.float64, N))
+    arrays = [(k, nets[k]) + want[k] for k in want]
+    arrays += [(k, x, dt, V) for k, x, dt in (("layer", layer, torch.int8), ("b", b, torch.int8),
+                                              ("t", t, torch.int8), ("R", R, torch.float64),
+                                              ("C", C, torch.float64), ("delay", delay, torch.float64))]
+    for k, x, dt, n in arrays:
+        if not isinstance(x, torch.Tensor) or x.device != dev or x.dtype != dt or not x.is_contiguous():
+            raise LaError(LA_ERR_INVALID, f"la_elmore_static: {k} must be a contiguous {dt} tensor on {dev}")
+        if num_nodes is None and x.numel() != n:
+            raise LaError(LA_ERR_INVALID, f"la_elmore_static: {k} has {x.numel()} entries, needs {n}")
     z = lambda k: nets[k].data_ptr() if k in nets and nets[k] is not None else None
-    d = NetDesc(int(nets["r_drv"].numel()), int(num_nodes if num_nodes is not None else nets["parent"].numel()),
+    d = NetDesc(N, int(num_nodes if num_nodes is not None else V),
                 z("net_ptr"), z("x"), z("y"), z("parent"), z("pin_layer"), z("sink_cap"), z("kappa"), z("r_drv"))
     if stream is None:
         stream = torch.cuda.current_stream().cuda_stream
-    st = lib.la_elmore_static(ctypes.byref(d), _ptr(layer), _ptr(b), _ptr(t), int(L), keep.ctypes.data,
+    st = lib.la_elmore_static(ctypes.byref(d), _ptr(layer), _ptr(b), _ptr(t), L, keep.ctypes.data,
                               float(via_c), _ptr(R), _ptr(C), _ptr(delay), ctypes.c_void_p(stream))
     if st != LA_OK:
         raise LaError(st, lib.la_last_error(None).decode())
@@ -362,9 +403,9 @@ class LayerAssigner:
         self.V = int(len(forest["x"]))
 
     def assign_round(self, mode=LA_MODE_PLAIN, weights=LA_WEIGHTS_EQ4, reset=False, stats=True, look_ahead=True,
-                     tail_threshold=0, **w):
+                     tail_threshold=0, force_split=0, **w):
         self._sync_stream()
-        return la_assign_round(self.ctx, mode, weights, reset, stats, look_ahead, tail_threshold, **w)
+        return la_assign_round(self.ctx, mode, weights, reset, stats, look_ahead, tail_threshold, force_split, **w)
 
     def get_assignment(self):
         self._sync_stream()

@@ -121,6 +121,11 @@ struct Allocs {
     size_t b = n * sizeof(T);
     if (b == 0) b = 16;
     b = (b + 255) & ~size_t(255);
+    if (c->inject == LA_ERR_OOM) {  // a test's injected allocation failure
+      c->inject = LA_OK;
+      *p = nullptr;
+      return set_err(c, LA_ERR_OOM, "device allocation of %zu bytes failed: injected fault", b);
+    }
     void* q = nullptr;
     if (pool && hint && next < hint->size() && (*hint)[next].second == b) q = pool->take_exact((*hint)[next].first, b);
     ++next;
@@ -203,6 +208,15 @@ static la_status read_dev_err(la_ctx* c, int* code, long long* index) {
   CK(cudaStreamSynchronize(c->stream));
   unsigned long long e = kNoErr;
   CK(cudaMemcpy(&e, c->d_err, sizeof e, cudaMemcpyDeviceToHost));
+  if (c->inject == LA_ERR_DEVICE_CHECK) {  // a test's injected failures, reported like real ones
+    c->inject = LA_OK;
+    e = uint64_t(DE_NOSTACK);
+  } else if (c->inject == LA_ERR_CUDA || c->inject == LA_ERR_TIMEOUT) {
+    const la_status k = c->inject;
+    c->inject = LA_OK;
+    return set_err(c, k, k == LA_ERR_CUDA ? "cudaStreamSynchronize: injected fault"
+                                          : "a bounded device wait ran out: injected fault");
+  }
   if (e == kNoErr) {
     *code = 0;
     *index = 0;
@@ -299,6 +313,15 @@ la_status la_device_bytes(const la_ctx* c, size_t* bytes) {
 la_status la_launch_count(const la_ctx* c, int64_t* n) {
   if (!c || !n) return LA_ERR_INVALID;
   *n = c->launches;
+  return LA_OK;
+}
+
+la_status la_inject_fault(la_ctx* c, la_status code) {
+  if (!c) return LA_ERR_INVALID;
+  if (code != LA_OK && code != LA_ERR_OOM && code != LA_ERR_CUDA && code != LA_ERR_TIMEOUT &&
+      code != LA_ERR_DEVICE_CHECK)
+    return set_err(c, LA_ERR_INVALID, "la_inject_fault: code %d cannot be injected", int(code));
+  c->inject = code;
   return LA_OK;
 }
 
@@ -896,13 +919,15 @@ static void plan_from_memo(la_ctx* c) {
   c->plan = b;
 }
 
-// The current plan's split, block, grid and caching with tail threshold T
-// (0: no tail).  The graphs and constant caches stay with the plan; a graph
-// replays only if its signature, which holds the tail level, still matches.
-static void set_tail(la_ctx* c, int T) {
+// The current plan's block and caching with split k and tail threshold T
+// (0: no tail); the persistent grid is the tuned one while the split is the
+// tuned one, else the occupancy grid of the new split.  The graphs and
+// constant caches stay with the plan; a graph replays only if its signature,
+// which holds the split and the tail level, still matches.
+static void set_shape(la_ctx* c, int k, int T) {
   const BatchPlan& o = c->plan;
-  BatchPlan b = make_plan(c, o.k, o.block, false, T);
-  b.grid = o.grid;
+  BatchPlan b = make_plan(c, k, o.block, false, T);
+  if (k == c->memo.k) b.grid = c->memo.grid;
   b.cached = o.cached;
   b.tuned = o.tuned;
   b.best_ms = o.best_ms;
@@ -989,6 +1014,9 @@ la_status la_assign_round(la_ctx* c, const la_round_params* p, la_round_stats* s
   if (p->no_look_ahead != 0 && p->no_look_ahead != 1)
     return set_err(c, LA_ERR_INVALID, "la_assign_round: no_look_ahead must be 0 or 1");
   if (p->tail_threshold < 0) return set_err(c, LA_ERR_INVALID, "la_assign_round: tail_threshold must be >= 0");
+  if (p->force_split != 0 && (p->force_split < kMinBigSc - 1 || p->force_split > kSizeClasses - 1))
+    return set_err(c, LA_ERR_INVALID, "la_assign_round: force_split must be 0 or in [%d, %d]", kMinBigSc - 1,
+                   kSizeClasses - 1);
   const double* W = p->weights == LA_WEIGHTS_ADJOINT ? f.W_adj : f.W_eq4;
   const double* rho = p->weights == LA_WEIGHTS_ADJOINT ? f.rho_adj : f.rho_eq4;
   if (p->no_look_ahead) {
@@ -1022,7 +1050,8 @@ la_status la_assign_round(la_ctx* c, const la_round_params* p, la_round_stats* s
     TRY(batched_caches(c, w, W, si, s));
     if (!c->plan.tuned) TRY(autotune(c, w, W, rho, si, s));
     const int T = p->tail_threshold > 0 ? p->tail_threshold : c->memo.tail_T;
-    if (T != c->plan.tail_T) set_tail(c, T);
+    const int k = p->force_split > 0 ? p->force_split : c->memo.k;
+    if (T != c->plan.tail_T || k != c->plan.k) set_shape(c, k, T);
   }
   bool captured = false;
   CK(cudaEventRecord(c->ev[0], s));

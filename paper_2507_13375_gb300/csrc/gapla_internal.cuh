@@ -254,6 +254,7 @@ struct la_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
   bool poisoned = false;
+  la_status inject = LA_OK;             // la_inject_fault: the failure the next matching step reports
   std::string err;
   size_t bytes = 0;
   gapla::Grid grid;

@@ -525,8 +525,71 @@ __device__ __forceinline__ void dp_node(const DPArgs& a, const DevTables& s, con
     a.ent[int64_t(c) * LD + ldi] = int8_t(lc);
     sg = fma(Mc[bj], rvl[lc], Ac[bj]);
     sc = Ccc[bj];
+  } else if (a.nch[v] == 2) {
+    // Two sons (most several-son nodes): every stack [b, t] with b <= lo_req
+    // <= hi_req <= t.  Each son's key for every layer of its direction is
+    // computed once per (node, l) and held by layer (LLONG_MAX at the other
+    // direction's layers); the tail costs T(k) = fma(k, sigma_v, z), k < L,
+    // once per thread in shared memory ([k][thread], conflict-free; keybuf's
+    // LMAX x 256 entries).  f'(b, t) = (key0 + key1) + T(t - b) with each
+    // son's least key in [b, t], the oracle's sum in son order.
+    const int c0 = a.child_list[cs], c1 = a.child_list[cs + 1];
+    const int d0 = geo_dir(a.geo[c0]), d1 = geo_dir(a.geo[c1]);
+    const double* B0 = a.B + int64_t(c0) * LD;
+    const double* M0 = a.M + int64_t(c0) * LD;
+    const double* B1 = a.B + int64_t(c1) * LD;
+    const double* M1 = a.M + int64_t(c1) * LD;
+    long long k0[LMAX], k1[LMAX];
+#pragma unroll
+    for (int t = 0; t < LMAX; ++t) {
+      k0[t] = LLONG_MAX;
+      k1[t] = LLONG_MAX;
+      if (t < L) {
+        const int jt = s.ld_of[t];
+        if (s.dir[t] == d0) k0[t] = dbits(fma(M0[jt], rvl[t], B0[jt]));
+        if (s.dir[t] == d1) k1[t] = dbits(fma(M1[jt], rvl[t], B1[jt]));
+      }
+    }
+    double* tl = reinterpret_cast<double*>(keybuf) + threadIdx.x;
+    for (int k = 0; k < L; ++k) tl[k * 256] = fma(s.kd[k], sigma_v, z);
+    int bk = INT_MAX;
+    for (int b = 0; b <= lo_req; ++b) {
+      long long r0 = LLONG_MAX, r1 = LLONG_MAX;
+#pragma unroll
+      for (int t = 0; t < LMAX; ++t) {
+        if (t < L && t >= b) {
+          r0 = min(r0, k0[t]);
+          r1 = min(r1, k1[t]);
+          if (t >= hi_req && r0 != LLONG_MAX && r1 != LLONG_MAX) {
+            const double S = __longlong_as_double(r0) + __longlong_as_double(r1);
+            const long long f = dbits(S + tl[(t - b) * 256]);
+            if (stack_better(f, t - b, b, bfp, bk, bb)) { bfp = f; bk = t - b; bb = b; bt = t; }
+          }
+        }
+      }
+    }
+    if (bfp == LLONG_MAX) {  // cannot happen for a valid forest; report it
+      dev_error(a.err, DE_NOSTACK, v);
+      return;
+    }
+    // each son's least key inside the winning stack (ascending layers: the
+    // lowest layer wins ties), and its g = fma(M, Rvia(l, lc), A)
+    long long m0 = LLONG_MAX, m1 = LLONG_MAX;
+    int l0 = -1, l1 = -1;
+#pragma unroll
+    for (int t = 0; t < LMAX; ++t) {
+      if (t >= bb && t <= bt) {
+        if (k0[t] < m0) { m0 = k0[t]; l0 = t; }
+        if (k1[t] < m1) { m1 = k1[t]; l1 = t; }
+      }
+    }
+    const int j0 = s.ld_of[l0], j1 = s.ld_of[l1];
+    a.ent[int64_t(c0) * LD + ldi] = int8_t(l0);
+    a.ent[int64_t(c1) * LD + ldi] = int8_t(l1);
+    sg = fma(M0[j0], rvl[l0], a.A[int64_t(c0) * LD + j0]) + fma(M1[j1], rvl[l1], a.A[int64_t(c1) * LD + j1]);
+    sc = a.Cc[int64_t(c0) * LD + j0] + a.Cc[int64_t(c1) * LD + j1];
   } else {
-    // Two or more sons: every stack [b, t] with b <= lo_req <= hi_req <= t;
+    // Three or more sons: every stack [b, t] with b <= lo_req <= hi_req <= t;
     // S[t] accumulates, son by son in order, the son's least key in [b, t].
     // A son's keys are computed on its own direction's layers only and put
     // in shared memory by layer, [t][thread] (conflict-free), for the scan

@@ -1,7 +1,8 @@
 // k_static.cu - la_elmore_static: the Elmore forward pass without any device
-// allocation.  Its scratch (downstream caps and junction delays, 2 doubles per
-// node) lives in the fixed file-scope device array below, which every GPU that
-// loads the library holds until the process exits.
+// allocation.  Its scratch (a downstream cap and two son links per node, plus
+// a small header holding the net-pointer check flag) lives in the fixed
+// file-scope device array below, which every GPU that loads the library holds
+// until the process exits.
 #include <cmath>
 #include <cstdio>
 #include <mutex>
@@ -11,61 +12,103 @@
 
 namespace gapla {
 
-// 2 * LA_STATIC_MAX_NODES doubles = 32 MiB.
-static __device__ __align__(256) double g_static_scratch[2 * LA_STATIC_MAX_NODES];
+// Header (32 doubles = 256 bytes: the flag word first), then per node
+// Cd_J (a double) and the son links head / next (two int32): 16 bytes per
+// node, 32 MiB for LA_STATIC_MAX_NODES nodes.
+constexpr int64_t kStaticHeader = 32;
+static __device__ __align__(256) double g_static_scratch[kStaticHeader + 2 * int64_t(LA_STATIC_MAX_NODES)];
 
 struct RviaTable {
   double rv[kMaxL * kMaxL];  // Rvia(a, b) at a * L + b
 };
 
-// One thread per net; nodes of a net are visited in id order (parents first)
-// or reverse id order (sons first), which needs no son lists.  A node whose
-// parent id is out of order, or whose layers/pin are out of range, makes the
-// whole net's delays NaN (no access outside the given arrays is made).
+// net_ptr must rise strictly from 0 to V; otherwise the flag is set and every
+// delay is NaN (nets could overlap, so no net's result could be trusted).
+__global__ void k_static_check_netptr(int64_t N, int64_t V, const int64_t* __restrict__ net_ptr,
+                                      unsigned* __restrict__ flag) {
+  const int64_t n = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (n > N) return;
+  const int64_t x = net_ptr[n];
+  bool bad = x < 0 || x > V;
+  if (n == 0) bad = bad || x != 0;
+  if (n == N) bad = bad || x != V;
+  if (n < N) bad = bad || net_ptr[n + 1] <= x;
+  if (bad) atomicOr(flag, 1u);
+}
+
+// One thread per net; the nodes of a net are visited in id order (parents
+// first) or reverse id order (sons first).  The son lists are built in
+// reverse id order, each son put in front of its parent's list, so every list
+// runs in increasing id: downstream caps are summed over the sons in that
+// order, the order la_elmore and the CPU model use (the results are equal bit
+// for bit).  Junction delays are written to `delay` first and the pin terms
+// added last.  A node whose parent id is out of order, or whose layer, pin or
+// stack is out of range, makes the whole net's delays NaN (no access outside
+// the given arrays is made).
 __global__ void k_elmore_static(int64_t N, const int64_t* __restrict__ net_ptr, const int32_t* __restrict__ parent,
                                 const int8_t* __restrict__ pin, const double* __restrict__ sink_cap,
                                 const double* __restrict__ r_drv, const int8_t* __restrict__ layer,
                                 const int8_t* __restrict__ b, const int8_t* __restrict__ t, const double* __restrict__ R,
                                 const double* __restrict__ C, double* __restrict__ delay, int L, double via_c,
-                                const __grid_constant__ RviaTable tab, double* __restrict__ CdJ,
-                                double* __restrict__ dJ, int64_t V) {
+                                const __grid_constant__ RviaTable tab, const unsigned* __restrict__ flag,
+                                double* __restrict__ CdJ, int32_t* __restrict__ head, int32_t* __restrict__ next,
+                                int64_t V) {
   const double* rv = tab.rv;
-  const int64_t n = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t gtid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (*flag) {  // malformed net_ptr: every delay is NaN
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t i = gtid; i < V; i += stride) delay[i] = nan("");
+    return;
+  }
+  const int64_t n = gtid;
   if (n >= N) return;
-  const int64_t base = net_ptr[n], end = net_ptr[n + 1];
-  if (!(base >= 0 && base < end && end <= V)) return;
-  const int64_t m = end - base;
+  const int64_t base = net_ptr[n], m = net_ptr[n + 1] - base;
   bool bad = false;
   // own capacitance at each junction: C_seg/2 (not at the root), vias, pin
   for (int64_t i = 0; i < m && !bad; ++i) {
     const int64_t v = base + i;
-    const int p = parent[v], l = layer[v], pv = pin[v];
-    bad = (i == 0 ? p != -1 : (p < 0 || p >= i)) || l < 0 || l >= L || pv < -1 || pv >= L || b[v] > t[v];
+    const int p = parent[v], l = layer[v], pv = pin[v], bv = b[v], tv = t[v];
+    bad = (i == 0 ? p != -1 : (p < 0 || p >= i)) || l < 0 || l >= L || pv < -1 || pv >= L || bv < 0 || bv > tv ||
+          tv >= L;
     double s = i == 0 ? 0.0 : 0.5 * C[v];
-    s = s + via_c * double(t[v] - b[v]);
+    s = s + via_c * double(tv - bv);
     CdJ[v] = s + sink_cap[v];
+    head[v] = -1;
   }
-  if (!bad) {
-    // sons before parents: add each son's (C_seg/2 + Cd_J) to its parent
-    for (int64_t i = m - 1; i >= 1; --i) {
-      const int64_t v = base + i, p = base + parent[v];
-      CdJ[p] = CdJ[p] + (0.5 * C[v] + CdJ[v]);
-    }
-    // parents before sons: junction delays, then the pin point
-    for (int64_t i = 0; i < m; ++i) {
-      const int64_t v = base + i;
-      double dj;
-      if (i == 0) {
-        dj = r_drv[n] * CdJ[v];
-      } else {
-        const int64_t p = base + parent[v];
-        dj = dJ[p] + rv[layer[p] * L + layer[v]] * (0.5 * C[v] + CdJ[v]) + R[v] * CdJ[v];
-      }
-      dJ[v] = dj;
-      delay[v] = pin[v] >= 0 ? dj + rv[layer[v] * L + pin[v]] * sink_cap[v] : dj;
-    }
-  } else {
+  if (bad) {
     for (int64_t i = 0; i < m; ++i) delay[base + i] = nan("");
+    return;
+  }
+  // son lists, increasing local id
+  for (int64_t i = m - 1; i >= 1; --i) {
+    const int64_t v = base + i, p = base + parent[v];
+    next[v] = head[p];
+    head[p] = int32_t(i);
+  }
+  // sons before parents: Cd_J(v) += sum over sons c of (C_seg[c]/2 + Cd_J(c))
+  for (int64_t i = m - 1; i >= 0; --i) {
+    const int64_t v = base + i;
+    double s = CdJ[v];
+    for (int32_t c = head[v]; c >= 0; c = next[base + c]) s = s + (0.5 * C[base + c] + CdJ[base + c]);
+    CdJ[v] = s;
+  }
+  // parents before sons: junction delays
+  for (int64_t i = 0; i < m; ++i) {
+    const int64_t v = base + i;
+    double dj;
+    if (i == 0) {
+      dj = r_drv[n] * CdJ[v];
+    } else {
+      const int64_t p = base + parent[v];
+      const double dX = delay[p] + rv[layer[p] * L + layer[v]] * (0.5 * C[v] + CdJ[v]);
+      dj = dX + R[v] * CdJ[v];
+    }
+    delay[v] = dj;
+  }
+  // the pin point of each pin node
+  for (int64_t i = 0; i < m; ++i) {
+    const int64_t v = base + i;
+    if (pin[v] >= 0) delay[v] = delay[v] + rv[layer[v] * L + pin[v]] * sink_cap[v];
   }
 }
 
@@ -118,7 +161,7 @@ extern "C" la_status la_elmore_static(const la_net_desc* nets, const int8_t* lay
     }
     scratch = g_static_ptr[dev];
   }
-  // Rvia(a, b) travels as a kernel parameter; the scratch holds [CdJ V][dJ V]
+  // Rvia(a, b) travels as a kernel parameter
   RviaTable tab;
   for (int a = 0; a < L; ++a)
     for (int c = 0; c < L; ++c) {
@@ -128,11 +171,18 @@ extern "C" la_status la_elmore_static(const la_net_desc* nets, const int8_t* lay
       tab.rv[a * L + c] = s;
     }
   const int64_t V = nets->num_nodes, N = nets->num_nets;
-  double* CdJ = scratch;
-  double* dJ = scratch + V;
-  k_elmore_static<<<(unsigned)((N + 127) / 128), 128, 0, static_cast<cudaStream_t>(stream)>>>(
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  unsigned* flag = reinterpret_cast<unsigned*>(scratch);
+  double* CdJ = scratch + kStaticHeader;
+  int32_t* head = reinterpret_cast<int32_t*>(CdJ + V);
+  int32_t* next = head + V;
+  e = cudaMemsetAsync(flag, 0, sizeof(unsigned), s);  // the flag starts at zero on every call
+  if (e != cudaSuccess)
+    return fail_noctx(LA_ERR_CUDA, std::string("la_elmore_static: clearing the flag failed: ") + cudaGetErrorString(e));
+  k_static_check_netptr<<<(unsigned)((N + 1 + 255) / 256), 256, 0, s>>>(N, V, nets->net_ptr, flag);
+  k_elmore_static<<<(unsigned)((N + 127) / 128), 128, 0, s>>>(
       N, nets->net_ptr, nets->parent, nets->pin_layer, nets->sink_cap, nets->r_drv, layer, b, t, R_seg, C_seg,
-      delay, L, via_c, tab, CdJ, dJ, V);
+      delay, L, via_c, tab, flag, CdJ, head, next, V);
   e = cudaGetLastError();
   if (e != cudaSuccess)
     return fail_noctx(LA_ERR_CUDA, std::string("la_elmore_static: launch failed: ") + cudaGetErrorString(e));

@@ -510,3 +510,210 @@ def test_elmore_of_the_assignment(la):
     ref = a.elmore(R, C).cpu().numpy()
     got = a.elmore_assignment().cpu().numpy()
     assert np.array_equal(got, ref)
+
+
+# ---------------------------------------------------------------------------
+# The headline shapes against the oracle, round by round, with the batched
+# form's own tuned plan; forced splits through the persistent big-net kernels
+# ---------------------------------------------------------------------------
+def _read_round(a, st):
+    got = dict(zip(("layer", "b", "t"), (x.cpu().numpy() for x in a.get_assignment())))
+    got["D"], got["H"] = (x.cpu().numpy() for x in a.get_state())
+    got["J"] = a.get_net_cost().cpu().numpy()
+    got["stats"] = st
+    return got
+
+
+def _rounds_against_oracle(la, a, grid, forest, mode, rounds, label, force_split=0):
+    """Round 0 with the Eq. 4 weights from D = H = 0, then rounds reweighted by
+    the adjoint of the previous assignment; each round's oracle starts from
+    the GPU's previous state (D, H) and the oracle's own adjoint weights of
+    the GPU's previous assignment, which must equal the GPU's bit for bit."""
+    D = H = W = rho = None
+    out = []
+    for r in range(rounds):
+        src = la.LA_WEIGHTS_EQ4 if r == 0 else la.LA_WEIGHTS_ADJOINT
+        st = a.assign_round(mode=mode, reset=(r == 0), weights=src, force_split=force_split, **la.DEFAULT_WEIGHTS)
+        got = _read_round(a, st)
+        ref = ref_round(grid, forest, la.DEFAULT_WEIGHTS, D=D, H=H, W=W, rho=rho)
+        assert_same_round(got, ref, f"{label} round {r}")
+        out.append(got)
+        D, H = got["D"], got["H"]
+        a.reweight_adjoint()
+        W, rho = oracle.adjoint_weights(grid, forest, got["layer"], got["b"], got["t"])
+        Wg, rhog = (x.cpu().numpy() for x in a.get_weights(la.LA_WEIGHTS_ADJOINT))
+        assert np.array_equal(Wg, W) and np.array_equal(rhog, rho), f"{label} adjoint weights after round {r}"
+    return out
+
+
+def test_headline_grid_and_stack_against_oracle(la):
+    """The full-scale workload's own grid and layer stack (2048 x 2048, 12
+    layers with r_l = 8 x 10^(-l/11), capacities U{8..20} with 10% halved) and
+    its net distribution, 1M nets, batched with the tuner's plan: an Eq. 4
+    round and an adjoint-reweighted round, bit for bit against the oracle."""
+    wl = fg.WORKLOADS[5].scaled(1_000_000)
+    grid, forest = fg.make_grid(wl, 0), fg.make_forest(wl, 0)
+    a = _assigner(la, grid, forest)
+    out = _rounds_against_oracle(la, a, grid, forest, la.LA_MODE_BATCHED, 2, "2048x2048x12 1M")
+    st = out[0]["stats"]
+    assert st["batch_trials"] > 0 and st["batch_levels"] > 20
+    a.close()
+
+
+def test_uneven_sizes_against_oracle(la):
+    """The uneven-batching workload (1024 x 1024 x 10, Zipf(1.6) pin counts on
+    [2, 4096]) at 200k nets, batched with the tuner's plan: an Eq. 4 round and
+    an adjoint-reweighted round against the oracle."""
+    wl = fg.WORKLOADS[4].scaled(200_000)
+    grid, forest = fg.make_grid(wl, 0), fg.make_forest(wl, 0)
+    assert np.diff(forest["net_ptr"]).max() > 2000
+    a = _assigner(la, grid, forest)
+    _rounds_against_oracle(la, a, grid, forest, la.LA_MODE_BATCHED, 2, "zipf 200k")
+    a.close()
+
+
+@pytest.mark.parametrize("cfg,nets,split", [(4, 20000, 4), (4, 20000, 7), (5, 100000, 4), (5, 100000, 5)])
+def test_forced_split_runs_the_persistent_kernels(la, cfg, nets, split):
+    """force_split sends every net of more than 2^split nodes through the
+    persistent block-per-net kernels (work queue, a block per net walking its
+    levels): three adjoint rounds against the oracle, and equal to the plain
+    form bit for bit."""
+    wl = fg.WORKLOADS[cfg].scaled(nets)
+    grid, forest = fg.make_grid(wl, 17), fg.make_forest(wl, 17)
+    sizes = np.diff(forest["net_ptr"])
+    a = _assigner(la, grid, forest)
+    out = _rounds_against_oracle(la, a, grid, forest, la.LA_MODE_BATCHED, 3, f"cfg {cfg} split {split}",
+                                 force_split=split)
+    for q in out:
+        assert q["stats"]["batch_split"] == split
+        assert q["stats"]["batch_big_nets"] == int(np.sum(sizes > 2 ** split)) > 0
+    plain = _rounds(a, la, la.LA_MODE_PLAIN, 3, adjoint=True)
+    for r, (p, q) in enumerate(zip(plain, out)):
+        for k in ("layer", "b", "t", "D", "H", "J"):
+            assert np.array_equal(p[k], q[k]), (r, k)
+    # back to the tuner's split on the same context
+    st = a.assign_round(mode=la.LA_MODE_BATCHED, reset=True, **la.DEFAULT_WEIGHTS)
+    assert st["batch_split"] == out[0]["stats"]["batch_split"] or st["batch_split"] != split
+    with pytest.raises(la.LaError) as e:
+        a.assign_round(mode=la.LA_MODE_BATCHED, force_split=3, **la.DEFAULT_WEIGHTS)
+    assert e.value.status == la.LA_ERR_INVALID
+    a.close()
+
+
+@pytest.mark.parametrize("mode", ["plain", "batched"])
+def test_exact_ties_follow_the_documented_rules(la, mode):
+    """The exact-tie nets of the oracle's tie pins: the GPU takes the same
+    documented choice (lowest tied son layer; fewest vias, then lowest bottom)."""
+    from util_inputs import TIE_WEIGHTS, son_tie_case, stack_tie_case
+
+    m = la.LA_MODE_PLAIN if mode == "plain" else la.LA_MODE_BATCHED
+    for grid, forest, layers, stacks in (son_tie_case(), stack_tie_case()):
+        a = _assigner(la, grid, forest)
+        st = a.assign_round(mode=m, reset=True, **TIE_WEIGHTS)
+        got = _read_round(a, st)
+        ref = ref_round(grid, forest, TIE_WEIGHTS)
+        assert_same_round(got, ref, mode)
+        assert list(got["layer"]) == layers
+        assert list(zip(got["b"], got["t"])) == stacks
+        a.close()
+
+
+# ---------------------------------------------------------------------------
+# Failure paths: host-side fault injection (nothing faults on the GPU), input
+# checks of la_set_assignment, and a clean device error word after rounds
+# ---------------------------------------------------------------------------
+def _small(la, seed=1):
+    wl = fg.WORKLOADS[1].scaled(200)
+    grid, forest = fg.make_grid(wl, seed), fg.make_forest(wl, seed)
+    return grid, forest, _assigner(la, grid, forest)
+
+
+@pytest.mark.parametrize("code", ["LA_ERR_DEVICE_CHECK", "LA_ERR_CUDA", "LA_ERR_TIMEOUT"])
+def test_injected_device_failure_poisons_the_context(la, code):
+    grid, forest, a = _small(la)
+    a.assign_round(reset=True, **la.DEFAULT_WEIGHTS)
+    la.la_check(a.ctx)  # clean after a normal round
+    la.la_inject_fault(a.ctx, getattr(la, code))
+    with pytest.raises(la.LaError) as e:
+        a.assign_round(**la.DEFAULT_WEIGHTS)
+    assert e.value.status == getattr(la, code)
+    # poisoned: every later call but la_destroy / la_last_error is LA_ERR_STATE
+    for call in (lambda: a.assign_round(**la.DEFAULT_WEIGHTS), lambda: la.la_check(a.ctx), a.get_assignment,
+                 lambda: a.load_nets(forest), a.rc_from_assignment):
+        with pytest.raises(la.LaError) as e2:
+            call()
+        assert e2.value.status == la.LA_ERR_STATE
+    a.close()
+    # a new context on the same device works and matches the oracle
+    b = _assigner(la, grid, forest)
+    got = gpu_round(b, la.DEFAULT_WEIGHTS, reset=True)
+    assert_same_round(got, ref_round(grid, forest, la.DEFAULT_WEIGHTS))
+    b.close()
+
+
+def test_injected_allocation_failure_keeps_the_loaded_forest(la):
+    """LA_ERR_OOM before the new forest has passed validation: the forest loaded
+    before stays loaded and the context is not poisoned."""
+    grid, forest, a = _small(la)
+    first = gpu_round(a, la.DEFAULT_WEIGHTS, reset=True)
+    other = fg.make_forest(fg.WORKLOADS[1].scaled(300), 2)
+    la.la_inject_fault(a.ctx, la.LA_ERR_OOM)
+    with pytest.raises(la.LaError) as e:
+        a.load_nets(other)
+    assert e.value.status == la.LA_ERR_OOM and "injected" in str(e.value)
+    again = gpu_round(a, la.DEFAULT_WEIGHTS, reset=True)
+    for k in ("layer", "b", "t", "D", "H", "J"):
+        assert np.array_equal(first[k], again[k]), k
+    a.load_nets(other)  # and the next load works
+    got = gpu_round(a, la.DEFAULT_WEIGHTS, reset=True)
+    assert_same_round(got, ref_round(grid, other, la.DEFAULT_WEIGHTS))
+    la.la_inject_fault(a.ctx, la.LA_ERR_OOM)
+    la.la_inject_fault(a.ctx, la.LA_OK)  # cleared: the next load allocates normally
+    a.load_nets(forest)
+    with pytest.raises(la.LaError) as e:
+        la.la_inject_fault(a.ctx, la.LA_ERR_STATE)
+    assert e.value.status == la.LA_ERR_INVALID
+    a.close()
+
+
+def test_set_assignment_checks_its_input(la):
+    """la_set_assignment rejects a layer of the wrong direction, a stack that
+    does not hold a son's layer, and a stack that does not hold the pin, with
+    LA_ERR_INVALID naming the node; the assignment in place is unchanged and
+    the context stays usable."""
+    grid, forest, a = _small(la)
+    a.assign_round(reset=True, **la.DEFAULT_WEIGHTS)
+    layer, b, t = (x.clone() for x in a.get_assignment())
+    lay_np, b_np, t_np = layer.cpu().numpy(), b.cpu().numpy(), t.cpu().numpy()
+    par, ptr, pin = forest["parent"], forest["net_ptr"], forest["pin_layer"]
+    net_of = np.repeat(np.arange(int(forest["num_nets"])), np.diff(ptr))
+    gpar = np.where(par < 0, -1, ptr[net_of] + par)
+    # a non-root node whose layer is moved to the other direction
+    v = int(np.flatnonzero(gpar >= 0)[0])
+    bad = lay_np.copy()
+    bad[v] = lay_np[v] + 1 if lay_np[v] + 1 < grid["L"] else lay_np[v] - 1
+    # a parent whose stack top is lowered below a son's layer (still holding
+    # the parent's own layer and pin)
+    u = next(int(x) for x in np.flatnonzero(gpar >= 0)
+             if lay_np[x] > lay_np[gpar[x]] and pin[gpar[x]] < lay_np[x])
+    p = int(gpar[u])
+    bb, tt = b_np.copy(), t_np.copy()
+    tt[p] = lay_np[u] - 1
+    # a pin node whose stack no longer holds its pin layer
+    w = next(int(x) for x in np.flatnonzero((pin >= 0) & (gpar >= 0)) if pin[x] != lay_np[x])
+    b2, t2 = b_np.copy(), t_np.copy()
+    if pin[w] < lay_np[w]:
+        b2[w] = pin[w] + 1
+    else:
+        t2[w] = pin[w] - 1
+    dev = layer.device
+    for lay_, b_, t_ in ((bad, b_np, t_np), (lay_np, bb, tt), (lay_np, b2, t2)):
+        with pytest.raises(la.LaError) as e:
+            a.set_assignment(*(torch.from_numpy(x).to(dev) for x in (lay_, b_, t_)))
+        assert e.value.status == la.LA_ERR_INVALID and "node" in str(e.value)
+    now = [x.cpu().numpy() for x in a.get_assignment()]
+    for x, y in zip(now, (lay_np, b_np, t_np)):
+        assert np.array_equal(x, y)
+    a.set_assignment(layer, b, t)
+    la.la_check(a.ctx)
+    a.close()
