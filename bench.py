@@ -10,10 +10,12 @@ C ABI from pinned host buffers (host->device copies of the forest, forest
 load + levelisation, the rounds, device->host copy of the assignment).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--workload 5]
-                       [--mode plain|batched] [--impl gapla|reference]
-Under torchrun (N > 1) every rank runs its own replica (seed = rank; no
-collective on the data path); rank 0 prints the JSON line with the max time
-over ranks.
+                       [--mode plain|batched] [--impl gapla|reference] [--shard]
+Under torchrun (N > 1) the workload's nets are split over the ranks by node
+count (one GPU each); every round ends with one all-reduce (sum, int32, NCCL)
+of the demand map, after which every rank commits the same snapshot
+(strong scaling: the job is the one workload).  --shard takes that path at
+N = 1 too.  Rank 0 prints the JSON line with the max time over ranks.
 """
 from __future__ import annotations
 
@@ -150,6 +152,17 @@ def job_rate(world: int, units_per_rank: float, ms: float) -> float:
     return world * units_per_rank / (ms * 1e-3)
 
 
+def sum_over_ranks(x: float, dist, device: str) -> float:
+    """A count summed over the ranks (all-reduce SUM; no-op alone)."""
+    if dist is None:
+        return x
+    import torch
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 # the forest arrays la_load_nets takes, with their element types
 INPUT_KEYS = ("net_ptr", "x", "y", "parent", "pin_layer", "sink_cap", "kappa", "r_drv")
 
@@ -212,17 +225,112 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+def dp_method_bytes(S: int, L_d: float) -> float:
+    """Compulsory HBM bytes of one round's DP + backtrack, counted per segment:
+    the DP reads the segment's geometry (12 B) and CSR (8 B), two prefix values
+    (16 B) and the son table entry (16 B) and writes its own entry (16 B) per
+    legal layer, plus (2 + deg) bytes of stack and choice per legal layer (about
+    2 per layer on a tree): 20 + 50 L_d; the backtrack about 10 B."""
+    return S * (20.0 + 50.0 * L_d) + 10.0 * S
+
+
+def dp_cache_bytes(V: int, S: int, N: int, LD: int) -> float:
+    """The batched form's own per-round bytes with its constant caches, each
+    element once: per node its data (geometry 8 B, the cached w_d W, w_d kappa,
+    w_d r_est, sigma 32 B, pin and caps 17 B, CSR 8 B); per (segment, layer) the
+    two congestion prefixes (16 B), the cached alpha, gamma, C (24 B), the entry
+    written (A, Cc, M, B 32 B, stack 2 B), the parent's read of it (32 B) and
+    the parent's choice byte; a root's stack (2 B)."""
+    return V * (8 + 32 + 17 + 8) + S * LD * (16 + 24 + 32 + 2 + 32 + 1) + N * 2
+
+
+def elmore_method_bytes(S: int) -> dict:
+    """Compulsory bytes of the Elmore passes per RC node (about two per
+    segment: the via end and the junction): forward about 40 B, adjoint about
+    48 B."""
+    return {"rc_nodes": 2 * S, "forward": 40.0 * 2 * S, "adjoint": 48.0 * 2 * S}
+
+
+def rooflines(la, device, forest, wl, N, S, dp_ms, adj_ms, elm_ms):
+    """The DP phase (FP64-bound on GB300) against the FP64 pipe, nominal and
+    measured, with its HBM view beside it; the Elmore passes against HBM."""
+    # GB300 issues FP64 at 2 FMA/clk/SM: 152 SMs x 2 x 2070 MHz x 2 flops
+    fp64_nominal = 152 * 2 * 2070e6 * 2 / 1e12
+    try:
+        fp64_measured = 2.0 * la.la_probe_fp64(device) / 1e12
+    except Exception:  # a failed probe leaves the nominal figure only
+        fp64_measured = None
+    flops = dp_algorithmic_flops(forest, wl.dirs)
+    achieved = flops / (dp_ms * 1e-3) / 1e12
+    hbm_peak, peak_src = measured_peaks()
+    n_h = sum(1 for d in wl.dirs if d == 0)
+    n_v = len(wl.dirs) - n_h
+    LD = max(n_h, n_v)
+    L_d = len(wl.dirs) / 2.0
+    V = int(forest["num_nodes"])
+    method = dp_method_bytes(S, L_d)
+    caches = dp_cache_bytes(V, S, N, LD)
+    rec, traffic_src = dp_capture_record(wl.name)
+    traffic = float(rec["bytes_per_round"]) if rec else None
+    fp64_pipe = None
+    if rec and rec.get("fp64_warp_inst_per_round"):
+        lane_ops = 32.0 * float(rec["fp64_warp_inst_per_round"])
+        pipe_peak = 152 * 2 * 2070e6
+        fp64_pipe = {"issued_lane_ops_per_round": lane_ops, "achieved": round(lane_ops / (dp_ms * 1e-3) / 1e9, 1),
+                     "peak": round(pipe_peak / 1e9, 1), "unit": "G FP64 ops/s",
+                     "frac": round(lane_ops / (dp_ms * 1e-3) / pipe_peak, 4),
+                     "source": "issued FP64 instructions per round from " + traffic_src}
+    gbs = lambda b: b / (dp_ms * 1e-3) / 1e9
+    roofline = {"kernel": "k_dp_level / k_dp_tail / k_dp_bignets + k_backtrack_* (all levels of one round)",
+                "bound": "alu", "achieved": round(achieved, 4), "peak": round(fp64_nominal, 4),
+                "unit": "TFLOP/s", "frac": round(achieved / fp64_nominal, 4),
+                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk/SM x 2070 MHz x 2 flops (nominal FP64 pipe)",
+                "measured_peak": round(fp64_measured, 4) if fp64_measured else None,
+                "frac_of_measured": round(achieved / fp64_measured, 4) if fp64_measured else None,
+                "measured_peak_source": "la_probe_fp64: independent FP64 FMA chains on every SM, CUDA events",
+                "traffic": traffic, "traffic_source": traffic_src,
+                "algorithmic_flops_per_round": flops, "dp_ms_per_round": round(dp_ms, 4),
+                "fp64_pipe": fp64_pipe,
+                "hbm": {"achieved": round(gbs(method), 1), "peak": hbm_peak, "unit": "GB/s",
+                        "frac": round(gbs(method) / hbm_peak, 4), "algorithmic_bytes_per_round": int(method),
+                        "bytes_rule": "S (20 + 50 L_d) + 10 S: the DP's and the backtrack's compulsory bytes",
+                        "peak_source": f"{peak_src} hbm_gbs",
+                        "traffic_over_algorithmic": round(traffic / method, 3) if traffic else None,
+                        "with_batched_caches": {"bytes_per_round": int(caches), "achieved": round(gbs(caches), 1),
+                                                "frac": round(gbs(caches) / hbm_peak, 4),
+                                                "what": "every element the batched form touches once, its "
+                                                        "constant caches included"}}}
+    eb = elmore_method_bytes(S)
+    ge = lambda b, ms: b / (ms * 1e-3) / 1e9 if ms > 0 else None
+    roofline_elmore = {
+        "forward": {"kernel": "la_elmore_assignment: the Elmore forward of the step's final assignment",
+                    "bound": "hbm", "achieved": round(ge(eb["forward"], elm_ms), 1), "peak": hbm_peak,
+                    "unit": "GB/s", "frac": round(ge(eb["forward"], elm_ms) / hbm_peak, 4),
+                    "ms": round(elm_ms, 4), "algorithmic_bytes": int(eb["forward"]),
+                    "bytes_rule": "40 B per RC node, 2 RC nodes per segment"},
+        "adjoint": {"kernel": "la_reweight_adjoint: the adjoint's top-down pass after each round",
+                    "bound": "hbm", "achieved": round(ge(eb["adjoint"], adj_ms), 1), "peak": hbm_peak,
+                    "unit": "GB/s", "frac": round(ge(eb["adjoint"], adj_ms) / hbm_peak, 4),
+                    "ms": round(adj_ms, 4), "algorithmic_bytes": int(eb["adjoint"]),
+                    "bytes_rule": "48 B per RC node, 2 RC nodes per segment"},
+        "peak_source": f"{peak_src} hbm_gbs"}
+    return roofline, roofline_elmore
+
+
 # --------------------------------------------------------------------------
 # one step on the GPU
 # --------------------------------------------------------------------------
-def run_step(a, la, rounds: int, mode: int, weights: dict, want_stats: bool, torch):
+def run_step(a, la, rounds: int, mode: int, weights: dict, want_stats: bool, torch, round_fn=None):
     """The workload's rounds with adjoint reweighting; returns per-round stats
-    (if asked) and the device times of the adjoint passes."""
+    (if asked), the event pairs around the adjoint passes and around the
+    step's Elmore forward, and the delays.  round_fn replaces the context's
+    own round (the sharded round of a job split over GPUs)."""
     out = []
     adj_ms = []
     for r in range(rounds):
         src = la.LA_WEIGHTS_EQ4 if r == 0 else la.LA_WEIGHTS_ADJOINT
-        st = a.assign_round(mode=mode, weights=src, reset=(r == 0), stats=want_stats, **weights)
+        kw = dict(mode=mode, weights=src, reset=(r == 0), stats=want_stats, **weights)
+        st = round_fn(**kw) if round_fn else a.assign_round(**kw)
         if want_stats:
             out.append(st)
         if want_stats:
@@ -233,8 +341,14 @@ def run_step(a, la, rounds: int, mode: int, weights: dict, want_stats: bool, tor
             adj_ms.append((e0, e1))
         else:
             a.reweight_adjoint()
+    elm = None
+    if want_stats:
+        elm = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+        elm[0].record()
     delay = a.elmore_assignment()
-    return out, adj_ms, delay
+    if want_stats:
+        elm[1].record()
+    return out, (adj_ms, elm), delay
 
 
 def bench_gpu(args):
@@ -250,23 +364,36 @@ def bench_gpu(args):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     dist = None
     red_dev = "cuda"
-    if world > 1:
+    shard_mode = world > 1 or args.shard
+    torch.cuda.set_device(local)
+    if world > 1 or args.shard:
         import torch.distributed as dist
         backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if "RANK" not in os.environ:  # --shard without torchrun: a one-rank job
+            os.environ.update(RANK="0", WORLD_SIZE="1", MASTER_ADDR="127.0.0.1", MASTER_PORT="29513")
         dist.init_process_group(backend)
         red_dev = "cuda" if backend == "nccl" else "cpu"
-    torch.cuda.set_device(local)
     __graft_entry__.build()
+    from paper_2507_13375_gb300 import shard as sh
 
     wl = fg.WORKLOADS[args.workload]
     mode = la.LA_MODE_BATCHED if args.mode == "batched" else la.LA_MODE_PLAIN
     weights = dict(la.DEFAULT_WEIGHTS)
     t0 = time.time()
-    grid = fg.make_grid(wl, seed=replica_seed(rank))
-    forest = fg.make_forest(wl, seed=replica_seed(rank))
+    # sharded: every rank builds the one workload and takes its nets; else
+    # (one GPU) the workload itself
+    grid = fg.make_grid(wl, seed=0)
+    full = fg.make_forest(wl, seed=0)
+    lo, hi = sh.shard_ranges(full["net_ptr"], world)[rank] if shard_mode else (0, wl.num_nets)
+    forest = sh.shard_forest(full, lo, hi) if shard_mode else full
     gen_s = time.time() - t0
-    N, V = wl.num_nets, int(forest["num_nodes"])
+    N, V = int(forest["num_nets"]), int(forest["num_nodes"])  # this rank's nets
+    N_job = wl.num_nets
     S = V - N
+    round_fn = None
+    if shard_mode:
+        allreduce = lambda t: dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        round_fn = lambda **kw: sh.sharded_round(a, allreduce, **kw)
 
     a = la.LayerAssigner(local)
     a.load_grid(grid)
@@ -278,7 +405,7 @@ def bench_gpu(args):
     load_ms = ev0.elapsed_time(ev1)
 
     for _ in range(args.warmup):
-        run_step(a, la, wl.rounds, mode, weights, False, torch)
+        run_step(a, la, wl.rounds, mode, weights, False, torch, round_fn)
     torch.cuda.synchronize()
 
     # timed region: K steps, barrier + sync on both sides
@@ -292,21 +419,24 @@ def bench_gpu(args):
         nvtx_push(torch, "bench_timed")
         stats = []
         adj = []
+        elm = []
         for _ in range(args.steps):
-            st, ad, _ = run_step(a, la, wl.rounds, mode, weights, True, torch)
+            st, (ad, el), _ = run_step(a, la, wl.rounds, mode, weights, True, torch, round_fn)
             stats += st
             adj += ad
+            elm.append(el)
         nvtx_pop(torch)
         e_end.record()
         torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    launches = a.launch_count() - launches0
+    launches = sum_over_ranks(a.launch_count() - launches0, dist, red_dev)
     step_ms = max_over_ranks(e_start.elapsed_time(e_end) / args.steps, dist, red_dev)
     adj_ms = sum(e0.elapsed_time(e1) for e0, e1 in adj) / max(len(adj), 1)
+    elm_ms = sum(e0.elapsed_time(e1) for e0, e1 in elm) / max(len(elm), 1)
     dp_ms = statistics.mean(s["ms_dp"] for s in stats)
     rnd_ms = statistics.mean(s["ms"] for s in stats)
-    value = job_rate(world, N * wl.rounds, step_ms)
+    value = N_job * wl.rounds / (step_ms * 1e-3)  # the whole job's nets, over the slowest rank
 
     # ---- end to end through the C ABI, inputs from pinned host memory ----
     keys, dt = INPUT_KEYS, _input_dtypes()
@@ -314,8 +444,8 @@ def bench_gpu(args):
     # two device input sets: step i + 1's inputs are copied while step i runs
     devb = [{k: torch.empty_like(host[k], device="cuda") for k in keys} for _ in range(2)]
     out_host = [torch.empty(V, dtype=torch.int8).pin_memory() for _ in range(3)]
-    h2d = sum(t.numel() * t.element_size() for t in host.values())
-    d2h = 3 * V
+    h2d = sum_over_ranks(sum(t.numel() * t.element_size() for t in host.values()), dist, red_dev)
+    d2h = sum_over_ranks(3 * V, dist, red_dev)
     e2e_steps = max(1, min(args.steps, 3))
     # the host-to-device copies spread over four streams (several copy engines)
     main_s = torch.cuda.current_stream()
@@ -341,7 +471,7 @@ def bench_gpu(args):
         if i + 1 < e2e_steps:
             copy_inputs((i + 1) % 2)
         a.load_nets(devb[i % 2])
-        run_step(a, la, wl.rounds, mode, weights, False, torch)
+        run_step(a, la, wl.rounds, mode, weights, False, torch, round_fn)
         lay, bb, tt_ = a.get_assignment()
         for dst, src in zip(out_host, (lay, bb, tt_)):
             dst.copy_(src, non_blocking=True)
@@ -361,83 +491,53 @@ def bench_gpu(args):
     torch.cuda.synchronize()
     e2e_h2d_ms, e2e_load_ms = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
 
-    # ---- roofline of the dominant kernel (the DP) ----
-    # GB300 issues FP64 at 2 FMA/clk/SM: 152 SMs x 2 x 2070 MHz x 2 flops
-    fp64_peak_tflops = 152 * 2 * 2070e6 * 2 / 1e12
-    flops = dp_algorithmic_flops(forest, wl.dirs)
-    achieved = flops / (dp_ms * 1e-3) / 1e12
-    hbm_peak, peak_src = measured_peaks()
-    LD = max(sum(1 for d in wl.dirs if d == 0), sum(1 for d in wl.dirs if d == 1))
-    # algorithmic bytes of one DP pass of the batched form, each element once:
-    # per node its own data (geometry 8 B, the constant cache w_d W, w_d kappa,
-    # w_d r_est, sigma 32 B, pin and caps 17 B, CSR 8 B); per (segment, layer)
-    # the two congestion prefixes (16 B), the cached alpha, gamma, C (24 B), the
-    # entry written (A, Cc, M, B 32 B, stack 2 B), the parent's read of it
-    # (32 B) and the parent's choice byte; a root's stack (2 B).
-    dp_bytes = V * (8 + 32 + 17 + 8) + S * LD * (16 + 24 + 32 + 2 + 32 + 1) + N * 2
-    rec, traffic_src = dp_capture_record(wl.name)
-    traffic = float(rec["bytes_per_round"]) if rec else None
-    # the FP64 pipe view: issued FP64 lane operations (any of FMA, ADD, MUL,
-    # conversion: one pipe slot each) per second against 2 per clock per SM
-    fp64_pipe = None
-    if rec and rec.get("fp64_warp_inst_per_round"):
-        lane_ops = 32.0 * float(rec["fp64_warp_inst_per_round"])
-        pipe_peak = 152 * 2 * 2070e6
-        fp64_pipe = {"issued_lane_ops_per_round": lane_ops, "achieved": round(lane_ops / (dp_ms * 1e-3) / 1e9, 1),
-                     "peak": round(pipe_peak / 1e9, 1), "unit": "G FP64 ops/s",
-                     "frac": round(lane_ops / (dp_ms * 1e-3) / pipe_peak, 4),
-                     "source": "issued counts from the committed ncu record (profiles/dp_traffic.json)"}
-    hbm_achieved = dp_bytes / (dp_ms * 1e-3) / 1e9
-    roofline = {"kernel": "k_dp_level / k_dp_bignets (all levels of one round; in the batched form the phase "
-                          "also holds the backtrack)",
-                "bound": "alu", "achieved": round(achieved, 4), "peak": round(fp64_peak_tflops, 4),
-                "unit": "TFLOP/s", "frac": round(achieved / fp64_peak_tflops, 4), "traffic": traffic,
-                "traffic_source": traffic_src,
-                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk/SM x 2070 MHz x 2 flops (FP64 pipe)",
-                "algorithmic_flops_per_round": flops, "dp_ms_per_round": round(dp_ms, 4),
-                "fp64_pipe": fp64_pipe,
-                "hbm": {"achieved": round(hbm_achieved, 1), "peak": hbm_peak, "unit": "GB/s",
-                        "frac": round(hbm_achieved / hbm_peak, 4), "algorithmic_bytes_per_round": int(dp_bytes),
-                        "peak_source": f"{peak_src} hbm_gbs"}}
+    # ---- rooflines ----
+    roofline, roofline_elmore = rooflines(la, local, forest, wl, N, S, dp_ms, adj_ms, elm_ms)
 
     # ---- the plain form on the same forest, for comparison ----
     plain = None
     if args.mode == "batched" and not args.no_plain:
         for _ in range(1):
-            run_step(a, la, wl.rounds, la.LA_MODE_PLAIN, weights, False, torch)
+            run_step(a, la, wl.rounds, la.LA_MODE_PLAIN, weights, False, torch, round_fn)
         torch.cuda.synchronize()
         e_start.record()
         pst = []
         for _ in range(max(1, min(args.steps, 3))):
-            st_, _, _ = run_step(a, la, wl.rounds, la.LA_MODE_PLAIN, weights, True, torch)
+            st_, _, _ = run_step(a, la, wl.rounds, la.LA_MODE_PLAIN, weights, True, torch, round_fn)
             pst += st_
         e_end.record()
         torch.cuda.synchronize()
         p_ms = max_over_ranks(e_start.elapsed_time(e_end) / max(1, min(args.steps, 3)), dist, red_dev)
-        plain = {"value": job_rate(world, N * wl.rounds, p_ms), "unit": "nets/s", "ms_per_step": round(p_ms, 3),
+        plain = {"value": N_job * wl.rounds / (p_ms * 1e-3), "unit": "nets/s", "ms_per_step": round(p_ms, 3),
                  "dp_ms_per_round": round(statistics.mean(x["ms_dp"] for x in pst), 4),
                  "round_ms": round(statistics.mean(x["ms"] for x in pst), 4)}
 
     res = {
         "metric": METRIC, "value": value, "unit": "nets/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
+        "scaling": "strong" if shard_mode else "weak",
         "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic: seeded grid + MST/L-split net forest generator (forestgen), seed = rank",
-        "config": {"workload": wl.name, "nets": N, "nodes": V, "segments": S, "rounds_per_step": wl.rounds,
+        "data": "synthetic: seeded grid + MST/L-split net forest generator (forestgen), seed 0",
+        "config": {"workload": wl.name, "nets": N_job, "nodes": int(full["num_nodes"]),
+                   "segments": int(full["num_nodes"]) - N_job, "rounds_per_step": wl.rounds,
                    "grid": f"{wl.X}x{wl.Y}x{wl.L}", "mode": args.mode + ("+adjoint" if wl.rounds > 1 else ""),
                    "weights": "Eq. 4 in round 0, adjoint sensitivities in later rounds",
                    "l2": "inputs larger than L2 (working set %.1f GB)" % (a.device_bytes() / 1e9),
-                   "parallelism": f"replicas x{world}"},
-        "segments_per_s": job_rate(world, S * wl.rounds, step_ms),
+                   "parallelism": (f"nets split over {world} GPU(s) by node count, one int32 demand all-reduce "
+                                   f"per round ({'NCCL' if red_dev == 'cuda' else 'gloo'})") if shard_mode
+                                  else "one GPU"},
+        "segments_per_s": (int(full["num_nodes"]) - N_job) * wl.rounds / (step_ms * 1e-3),
         "phases_ms_per_round": {"round": round(rnd_ms, 4), "dp": round(dp_ms, 4),
                                 "backtrack": round(statistics.mean(s["ms_backtrack"] for s in stats), 4),
                                 "demand_scan": round(statistics.mean(s["ms_demand"] for s in stats), 4),
                                 "adjoint": round(adj_ms, 4)},
+        "elmore_forward_ms_per_step": round(elm_ms, 4),
         "load_ms": round(load_ms, 3), "generate_s": round(gen_s, 2),
         "batched_plan": ({k: stats[-1][k] for k in ("batch_split", "batch_block", "batch_big_nets", "batch_cached", "batch_trials", "batch_tune_ms", "batch_levels", "batch_tail_level")}
                          if args.mode == "batched" else None),
         "roofline": roofline,
-        "e2e": {"value": job_rate(world, N * wl.rounds, e2e_ms), "unit": "nets/s", "h2d_bytes_per_step": int(h2d),
+        "roofline_elmore": roofline_elmore,
+        "e2e": {"value": N_job * wl.rounds / (e2e_ms * 1e-3), "unit": "nets/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "ms_per_step": round(e2e_ms, 3),
                 "h2d_ms": round(e2e_h2d_ms, 3), "load_ms": round(e2e_load_ms, 3),
                 "copies": "step i + 1's inputs copied while step i runs (two device input sets)",
@@ -447,8 +547,9 @@ def bench_gpu(args):
         "clocks": clk.summary(),
         "quality_last_round": {k: _finite(stats[-1][k]) for k in ("total_cost", "tof", "relu_overflow", "vias", "wl")},
     }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        res["cpu_baseline"] = cpu_baseline(wl, grid, forest, args.cpu_seconds)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not shard_mode:
+        res["cpu_baseline"], ref = cpu_baseline(wl, grid, forest, args.cpu_seconds)
+        res["parity"] = round0_parity(a, la, mode, weights, forest, ref, torch)
     a.close()
     if dist:
         dist.destroy_process_group()
@@ -479,20 +580,49 @@ def cpu_baseline(wl, grid, forest, budget_s: float):
     fixed = max(t1 - slope * m1, 0.0)
     M = int(min(wl.num_nets, max(m2, (budget_s - fixed) / slope)))
     sub = fg.subset_forest(forest, np.arange(M))
-    t = _time_oracle_round(grid, sub)
+    t, out = _time_oracle_round(grid, sub, keep=True)
+    out["nets"] = M
     threads = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    return {"value": M / t, "unit": "nets/s", "cores": threads, "kind": "oracle",
-            "sample": f"first {M} of {wl.num_nets} nets, 1 round (penalty + DP + backtrack + demand + adjoint "
-                      f"reweighting) of {wl.name}, {t:.1f} s"}
+    return ({"value": M / t, "unit": "nets/s", "cores": threads, "kind": "oracle",
+             "sample": f"first {M} of {wl.num_nets} nets, 1 round (penalty + DP + backtrack + demand + adjoint "
+                       f"reweighting) of {wl.name}, {t:.1f} s"}, out)
 
 
-def _time_oracle_round(grid, forest):
+def _time_oracle_round(grid, forest, keep=False):
     import oracle
 
     t0 = time.perf_counter()
     out = oracle.assign_round(grid, forest, oracle.DEFAULT_WEIGHTS)
     oracle.adjoint_weights(grid, forest, out["layer"], out["b"], out["t"])
-    return time.perf_counter() - t0
+    t = time.perf_counter() - t0
+    return (t, out) if keep else t
+
+
+def round0_parity(a, la, mode, weights, forest, ref, torch):
+    """The GPU's round 0 (the bench's mode and plan, Eq. 4 weights, D = H = 0)
+    against the oracle's round 0 of the CPU-baseline sample (the first M nets
+    of the same forest): in round 0 every net sees the empty map, so the
+    sample's nets must get the same layers, stacks and costs J bit for bit;
+    with M = N the demand and history maps must be equal too."""
+    import numpy as np
+
+    a.assign_round(mode=mode, weights=la.LA_WEIGHTS_EQ4, reset=True, stats=True, **weights)
+    M = int(ref["nets"])
+    nodes = int(forest["net_ptr"][M])
+    lay, b, t = (x.cpu().numpy()[:nodes] for x in a.get_assignment())
+    J = a.get_net_cost().cpu().numpy()[:M]
+    rel = np.abs(J - ref["J"]) / np.maximum(np.abs(ref["J"]), 1e-300)
+    out = {"nets_compared": M, "nodes_compared": nodes,
+           "layers_mismatch": int(np.count_nonzero(lay != ref["layer"])),
+           "stacks_mismatch": int(np.count_nonzero((b != ref["b"]) | (t != ref["t"]))),
+           "J_equal": bool(np.array_equal(J, ref["J"])), "J_max_rel": float(rel.max()) if M else 0.0,
+           "D_equal": None, "H_equal": None,
+           "what": "GPU round 0 vs the oracle's round 0 on the CPU-baseline sample, same forest"}
+    if M == int(forest["num_nets"]):
+        D, H = (x.cpu().numpy() for x in a.get_state())
+        out["D_equal"] = bool(np.array_equal(D, ref["D"]))
+        out["H_equal"] = bool(np.array_equal(H, ref["H"]))
+    return out
 
 
 def bench_reference(args):
@@ -651,6 +781,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--ref-nets", type=int, default=400000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--shard", action="store_true",
+                    help="split the nets over the ranks with a demand all-reduce per round even at N = 1")
     ap.add_argument("--profile", action="store_true", help="short untimed run for ncu captures")
     ap.add_argument("--rounds", type=int, default=1, help="rounds of the --profile run")
     ap.add_argument("--reloads", type=int, default=0,

@@ -175,6 +175,15 @@ typedef struct {
                             * (the tuned block and caching kept).  Results do
                             * not depend on it; other values are
                             * LA_ERR_INVALID                                     */
+  int32_t local_demand;    /* 1: one shard of a round split over several
+                            * contexts by nets (one per GPU): the round ends
+                            * with D = the demand of this context's nets only
+                            * (H, tof and the overflow statistics untouched);
+                            * the caller sums D over the shards (la_get_state,
+                            * an all-reduce) and hands the sum to
+                            * la_commit_demand before the next round.  0: the
+                            * round ends with D, H and the statistics of the
+                            * whole forest                                      */
 } la_round_params;
 
 typedef struct {
@@ -212,6 +221,17 @@ typedef struct {
  * it; with NULL it only enqueues.  Weights must be >= 0 and finite. */
 la_status la_assign_round(la_ctx* ctx, const la_round_params* params, la_round_stats* stats);
 
+/* Ends a round run with local_demand = 1 once the demand of every shard has
+ * been summed (Alg. 2 over one demand map, the nets split between contexts):
+ * D := demand (device, E entries, public layout, each >= 0), then
+ * H += max(0, D - C), the Eq. 2 / Eq. 3 statistics and the penalty prefix of
+ * the next round, with the round's hist_w.  Every shard calls it with the same
+ * sum, so every shard holds the same snapshot afterwards.  If `stats` is
+ * non-NULL the call synchronises and fills tof and relu_overflow (the other
+ * fields are zero).  LA_ERR_INVALID for a negative entry (the snapshot is then
+ * unchanged); LA_ERR_STATE before any round. */
+la_status la_commit_demand(la_ctx* ctx, const int32_t* demand, la_round_stats* stats);
+
 /* Copy the last round's assignment out (device, V each): layer[v] = layer of
  * v's junction (its segment's layer; the driver pin layer at a root), and the
  * via stack [b[v], t[v]] at v.  Any pointer may be NULL. */
@@ -244,8 +264,8 @@ la_status la_rc_from_assignment(la_ctx* ctx, double* R_seg, double* C_seg);
 /* delay[v] = Elmore delay at v's pin point (pin nodes) or junction (others). */
 la_status la_elmore(la_ctx* ctx, const double* R_seg, const double* C_seg, double* delay);
 /* Adjoint of la_elmore: given g = dL/d delay, writes dL/dR_seg and dL/dC_seg
- * (0 at roots).  Recomputes the downstream caps level by level instead of
- * keeping them from the forward pass. */
+ * (0 at roots).  Recomputes the downstream caps net by net instead of keeping
+ * them from the forward pass. */
 la_status la_elmore_backward(la_ctx* ctx, const double* R_seg, const double* C_seg,
                              const double* grad_delay, double* dR_seg, double* dC_seg);
 

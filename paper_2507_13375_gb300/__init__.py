@@ -36,7 +36,7 @@ EXPORTS = ("la_create", "la_destroy", "la_last_error", "la_set_stream", "la_devi
            "la_load_grid", "la_load_nets", "la_assign_round", "la_get_assignment", "la_set_assignment",
            "la_get_net_cost", "la_get_state", "la_set_state", "la_rc_from_assignment", "la_elmore",
            "la_elmore_backward", "la_elmore_assignment", "la_reweight_adjoint", "la_get_weights",
-           "la_inject_fault", "la_probe_fp64", "la_elmore_static")
+           "la_inject_fault", "la_probe_fp64", "la_commit_demand", "la_elmore_static")
 LA_STATIC_MAX_NODES = 1 << 21
 
 
@@ -64,7 +64,8 @@ class RoundParams(ctypes.Structure):
     _fields_ = [("w_cong", ctypes.c_double), ("w_via", ctypes.c_double), ("w_cap", ctypes.c_double),
                 ("w_d", ctypes.c_double), ("hist_w", ctypes.c_double), ("mode", ctypes.c_int32),
                 ("weights", ctypes.c_int32), ("reset", ctypes.c_int32), ("no_look_ahead", ctypes.c_int32),
-                ("tail_threshold", ctypes.c_int32), ("force_split", ctypes.c_int32)]
+                ("tail_threshold", ctypes.c_int32), ("force_split", ctypes.c_int32),
+                ("local_demand", ctypes.c_int32)]
 
 
 class RoundStats(ctypes.Structure):
@@ -103,6 +104,7 @@ def library() -> ctypes.CDLL:
         "la_reweight_adjoint": [vp],
         "la_get_weights": [vp, i32, vp, vp], "la_inject_fault": [vp, ctypes.c_int],
         "la_probe_fp64": [ctypes.c_int, vp, P(ctypes.c_double)],
+        "la_commit_demand": [vp, vp, P(RoundStats)],
         "la_elmore_static": [P(NetDesc), vp, vp, vp, i32, vp, ctypes.c_double, vp, vp, vp, vp],
     }
     for name, args in sig.items():
@@ -200,11 +202,12 @@ def la_load_nets(ctx, forest: dict, device: int = 0):
 
 def la_assign_round(ctx, mode: int = LA_MODE_PLAIN, weights: int = LA_WEIGHTS_EQ4, reset: bool = False,
                     stats: bool = True, look_ahead: bool = True, tail_threshold: int = 0, force_split: int = 0,
-                    **w):
+                    local_demand: bool = False, **w):
     ww = dict(DEFAULT_WEIGHTS)
     ww.update(w)
     p = RoundParams(ww["w_cong"], ww["w_via"], ww["w_cap"], ww["w_d"], ww["hist_w"], int(mode), int(weights),
-                    1 if reset else 0, 0 if look_ahead else 1, int(tail_threshold), int(force_split))
+                    1 if reset else 0, 0 if look_ahead else 1, int(tail_threshold), int(force_split),
+                    1 if local_demand else 0)
     if not stats:
         _check(ctx, library().la_assign_round(ctx, ctypes.byref(p), None))
         return None
@@ -216,6 +219,16 @@ def la_assign_round(ctx, mode: int = LA_MODE_PLAIN, weights: int = LA_WEIGHTS_EQ
                 batch_big_nets=s.batch_big_nets, batch_cached=s.batch_cached, batch_trials=s.batch_trials,
                 batch_tune_ms=s.batch_tune_ms, batch_levels=s.batch_levels, batch_tail_level=s.batch_tail_level,
                 batch_graph_captured=s.batch_graph_captured)
+
+
+def la_commit_demand(ctx, demand, stats: bool = True):
+    """End a local-demand round with the demand summed over every shard."""
+    if not stats:
+        _check(ctx, library().la_commit_demand(ctx, _ptr(demand), None))
+        return None
+    s = RoundStats()
+    _check(ctx, library().la_commit_demand(ctx, _ptr(demand), ctypes.byref(s)))
+    return dict(tof=s.tof, relu_overflow=s.relu_overflow)
 
 
 def la_get_assignment(ctx, layer, b, t):
@@ -403,9 +416,15 @@ class LayerAssigner:
         self.V = int(len(forest["x"]))
 
     def assign_round(self, mode=LA_MODE_PLAIN, weights=LA_WEIGHTS_EQ4, reset=False, stats=True, look_ahead=True,
-                     tail_threshold=0, force_split=0, **w):
+                     tail_threshold=0, force_split=0, local_demand=False, **w):
         self._sync_stream()
-        return la_assign_round(self.ctx, mode, weights, reset, stats, look_ahead, tail_threshold, force_split, **w)
+        return la_assign_round(self.ctx, mode, weights, reset, stats, look_ahead, tail_threshold, force_split,
+                               local_demand, **w)
+
+    def commit_demand(self, D, stats=True):
+        """D: the demand summed over every shard (public layout, int32, this device)."""
+        self._sync_stream()
+        return la_commit_demand(self.ctx, _dev(D, torch.int32, self.dev), stats)
 
     def get_assignment(self):
         self._sync_stream()

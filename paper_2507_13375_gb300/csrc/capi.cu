@@ -615,7 +615,7 @@ la_status la_load_nets(la_ctx* c, const la_net_desc* nd) {
   GETK(nf.A, V * LD); GETK(nf.Cc, V * LD); GETK(nf.M, V * LD); GETK(nf.B, V * LD); GETK(nf.sb, V * LD);
   GETK(nf.st, V * LD); GETK(nf.ent, V * LD); GETK(nf.Jroot, V); GETK(nf.layer, V); GETK(nf.b, V); GETK(nf.t, V);
   GETK(nf.s0, V); GETK(nf.s1, V); GETK(nf.s2, V); GETK(nf.s3, V); GETK(nf.s4, V); GETK(nf.W_adj, V);
-  GETK(nf.rho_adj, V);
+  GETK(nf.rho_adj, V); GETK(nf.ep, V); GETK(nf.ecap, V);
   const int nred = std::max(scan_blocks(c->grid.li), int((N + 255) / 256)) + 8;
   GETK(nf.red, size_t(nred) * 2);
 #undef GETK
@@ -628,12 +628,13 @@ la_status la_load_nets(la_ctx* c, const la_net_desc* nd) {
                           nf.big_queue, nf.root_of_net, nf.parent_g, nf.net_of, nf.pin, nf.sink_cap, nf.kappa,
                           nf.gk, nf.geo, nf.child_start, nf.nch, nf.child_list, nf.W_eq4, nf.rho_eq4, nf.A, nf.Cc,
                           nf.M, nf.B, nf.sb, nf.st, nf.ent, nf.Jroot, nf.layer, nf.b, nf.t, nf.s0, nf.s1, nf.s2,
-                          nf.s3, nf.s4, nf.W_adj, nf.rho_adj, nf.red, in2int};
+                          nf.s3, nf.s4, nf.W_adj, nf.rho_adj, nf.red, nf.ep, nf.ecap, in2int};
     for (const void* q : need)
       if (!q) return fail(set_err(c, LA_ERR_STATE, "la_load_nets: internal allocation missing"));
   }
   launch_renumber(tf, in2int, key_of, int64_t(nbk), nf, s);
-  ++c->launches;
+  launch_elm_pack(tf, in2int, nf, s);
+  c->launches += 2;
   {
     // the segments by (direction, line), for the demand pass
     const int nl0 = c->grid.li.nlines[0], nkeys = nl0 + c->grid.li.nlines[1];
@@ -719,7 +720,7 @@ static la_status check_loaded(la_ctx* c) {
 // writes, the forest's shape and the plan.  A graph replays only while this
 // is unchanged (a reload of a same-shaped forest gets the same addresses back
 // from the pool and keeps its graphs).
-static uint64_t round_signature(la_ctx* c, int si, const double* W, const double* rho) {
+static uint64_t round_signature(la_ctx* c, int si, const double* W, const double* rho, bool local) {
   const Forest& f = c->forest;
   const Grid& g = c->grid;
   const BatchPlan& bp = c->plan;
@@ -734,7 +735,7 @@ static uint64_t round_signature(la_ctx* c, int si, const double* W, const double
   h = fnv_mix(h, uint64_t(reinterpret_cast<uintptr_t>(W)));
   h = fnv_mix(h, uint64_t(reinterpret_cast<uintptr_t>(rho)));
   const int64_t vals[] = {f.N, f.V, f.Hmax, f.nbatch, f.red_cap, c->LD, bp.k, bp.block, bp.grid, bp.cached ? 1 : 0,
-                          bp.n_big, bp.Hs, bp.tail_h, int64_t(f.key_hash)};
+                          bp.n_big, bp.Hs, bp.tail_h, int64_t(f.key_hash), local ? 1 : 0};
   for (int64_t x : vals) h = fnv_mix(h, uint64_t(x));
   return h;
 }
@@ -948,11 +949,11 @@ static void set_shape(la_ctx* c, int k, int T) {
 // the caller's stream every round; the caller's stream may be the legacy
 // default stream, which cannot be captured).
 static la_status batched_graph(la_ctx* c, const RoundW& w, const double* W, const double* rho, int si,
-                               cudaStream_t s_run, bool* captured) {
+                               cudaStream_t s_run, bool* captured, bool local) {
   BatchPlan& bp = c->plan;
   cudaStream_t s = c->s_cap;
   const double wv[5] = {w.w_cong, w.w_via, w.w_cap, w.w_d, w.hist_w};
-  const uint64_t sig = round_signature(c, si, W, rho);
+  const uint64_t sig = round_signature(c, si, W, rho, local);
   bool same = bp.exec[si] != nullptr && bp.graph_sig[si] == sig;
   for (int i = 0; i < 5 && same; ++i) same = bp.w[si][i] == wv[i];
   *captured = !same;
@@ -974,7 +975,8 @@ static la_status batched_graph(la_ctx* c, const RoundW& w, const double* W, cons
     mark(c->ev[3]);
     Forest& f = c->forest;
     if (st == LA_OK) {
-      launch_demand_scan(c, w.hist_w, f.red, s);
+      if (local) launch_local_demand(c, w.hist_w, f.red, s);
+      else launch_demand_scan(c, w.hist_w, f.red, s);
       launch_sum_roots(c, f.red + f.red_cap, nullptr, s);
     }
     mark(c->ev[4]);
@@ -1014,6 +1016,8 @@ la_status la_assign_round(la_ctx* c, const la_round_params* p, la_round_stats* s
   if (p->no_look_ahead != 0 && p->no_look_ahead != 1)
     return set_err(c, LA_ERR_INVALID, "la_assign_round: no_look_ahead must be 0 or 1");
   if (p->tail_threshold < 0) return set_err(c, LA_ERR_INVALID, "la_assign_round: tail_threshold must be >= 0");
+  if (p->local_demand != 0 && p->local_demand != 1)
+    return set_err(c, LA_ERR_INVALID, "la_assign_round: local_demand must be 0 or 1");
   if (p->force_split != 0 && (p->force_split < kMinBigSc - 1 || p->force_split > kSizeClasses - 1))
     return set_err(c, LA_ERR_INVALID, "la_assign_round: force_split must be 0 or in [%d, %d]", kMinBigSc - 1,
                    kSizeClasses - 1);
@@ -1043,6 +1047,8 @@ la_status la_assign_round(la_ctx* c, const la_round_params* p, la_round_stats* s
   if (!gr.P_valid || gr.P_hist_w != p->hist_w) launch_scan_lines(c, 0, p->hist_w, tof_part, s);
   const bool batched = p->mode == LA_MODE_BATCHED;
   const int si = p->weights == LA_WEIGHTS_ADJOINT ? 1 : 0;
+  if (p->local_demand && f.nbatch > 1)
+    return set_err(c, LA_ERR_INVALID, "la_assign_round: sequential batches cannot be split over shards");
   if (batched && f.nbatch > 1)
     return set_err(c, LA_ERR_INVALID, "la_assign_round: a forest of %d sequential batches needs LA_MODE_PLAIN",
                    f.nbatch);
@@ -1056,14 +1062,15 @@ la_status la_assign_round(la_ctx* c, const la_round_params* p, la_round_stats* s
   bool captured = false;
   CK(cudaEventRecord(c->ev[0], s));
   if (batched) {
-    TRY(batched_graph(c, w, W, rho, si, s, &captured));
+    TRY(batched_graph(c, w, W, rho, si, s, &captured, p->local_demand != 0));
   } else if (f.nbatch == 1) {
     CK(cudaEventRecord(c->ev[1], s));
     for (int h = 0; h <= f.Hmax; ++h) launch_dp_level(c, w, W, rho, h, kSizeClasses - 1, kNoCache, s);
     CK(cudaEventRecord(c->ev[2], s));
     for (int h = f.Hmax; h >= 0; --h) launch_backtrack_level(c, h, kSizeClasses - 1, s);
     CK(cudaEventRecord(c->ev[3], s));
-    launch_demand_scan(c, p->hist_w, tof_part, s);
+    if (p->local_demand) launch_local_demand(c, p->hist_w, tof_part, s);
+    else launch_demand_scan(c, p->hist_w, tof_part, s);
     launch_sum_roots(c, J_part, nullptr, s);
     CK(cudaEventRecord(c->ev[4], s));
   } else {
@@ -1091,13 +1098,15 @@ la_status la_assign_round(la_ctx* c, const la_round_params* p, la_round_stats* s
     }
     CK(cudaEventRecord(c->ev[2], s));
     CK(cudaEventRecord(c->ev[3], s));
-    launch_demand_scan(c, p->hist_w, tof_part, s);
+    if (p->local_demand) launch_local_demand(c, p->hist_w, tof_part, s);
+    else launch_demand_scan(c, p->hist_w, tof_part, s);
     launch_sum_roots(c, J_part, nullptr, s);
     CK(cudaEventRecord(c->ev[4], s));
   }
   CK(cudaGetLastError());
-  gr.P_valid = true;
+  gr.P_valid = p->local_demand == 0;  // a shard's D is not the round's snapshot until la_commit_demand
   gr.P_hist_w = p->hist_w;
+  gr.round_hist_w = p->hist_w;
   f.have_assign = true;
   if (!stats) return LA_OK;
   CK(cudaStreamSynchronize(s));
@@ -1153,6 +1162,49 @@ la_status la_assign_round(la_ctx* c, const la_round_params* p, la_round_stats* s
     stats->batch_tail_level = std::min(c->plan.tail_h, c->plan.Hs + 1);
     stats->batch_graph_captured = captured ? 1 : 0;
   }
+  return LA_OK;
+}
+
+la_status la_commit_demand(la_ctx* c, const int32_t* demand, la_round_stats* stats) {
+  TRY(check_loaded(c));
+  if (!demand) return set_err(c, LA_ERR_INVALID, "la_commit_demand: null pointer");
+  if (!c->forest.have_assign) return set_err(c, LA_ERR_STATE, "la_commit_demand: no round run yet");
+  DeviceGuard g(c->device);
+  Grid& gr = c->grid;
+  Forest& f = c->forest;
+  cudaStream_t s = c->stream;
+  // stage through the difference array (all zero between rounds) so that a
+  // negative entry leaves the snapshot unchanged
+  TRY(reset_dev_err(c));
+  launch_grid_to_internal(gr.li, gr.X, gr.Y, demand, gr.diff, true, c->d_err, s);
+  ++c->launches;
+  CK(cudaGetLastError());
+  int code;
+  long long idx;
+  TRY(read_dev_err(c, &code, &idx));
+  if (code) {
+    CK(cudaMemsetAsync(gr.diff, 0, gr.G * 4, s));
+    return set_err(c, LA_ERR_INVALID, "la_commit_demand: demand at edge %lld is negative", idx);
+  }
+  CK(cudaMemcpyAsync(gr.D, gr.diff, gr.G * 4, cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemsetAsync(gr.diff, 0, gr.G * 4, s));
+  CK(cudaMemsetAsync(c->d_stats, 0, sizeof(Stats), s));
+  launch_scan_lines(c, 3, gr.round_hist_w, f.red, s);
+  CK(cudaGetLastError());
+  gr.P_valid = true;
+  gr.P_hist_w = gr.round_hist_w;
+  if (!stats) return LA_OK;
+  CK(cudaStreamSynchronize(s));
+  Stats hs;
+  CK(cudaMemcpy(&hs, c->d_stats, sizeof hs, cudaMemcpyDeviceToHost));
+  const int nsb = scan_blocks(gr.li);
+  std::vector<double> part(static_cast<size_t>(nsb));
+  CK(cudaMemcpy(part.data(), f.red, sizeof(double) * part.size(), cudaMemcpyDeviceToHost));
+  double tof = 0.0;
+  for (int i = 0; i < nsb; ++i) tof += part[i];
+  memset(stats, 0, sizeof *stats);
+  stats->tof = tof;
+  stats->relu_overflow = (int64_t)hs.relu;
   return LA_OK;
 }
 
@@ -1274,13 +1326,7 @@ la_status la_elmore(la_ctx* c, const double* R, const double* C, double* delay) 
   TRY(check_assigned(c));
   if (!R || !C || !delay) return set_err(c, LA_ERR_INVALID, "la_elmore: null pointer");
   DeviceGuard g(c->device);
-  Forest& f = c->forest;
-  // input order -> internal (s3, s4), the level passes, internal -> input
-  launch_permute64(f.V, f.lvl_nodes, R, f.s3, true, c->stream);
-  launch_permute64(f.V, f.lvl_nodes, C, f.s4, true, c->stream);
-  launch_elmore_fwd(c, f.s3, f.s4, f.s2, c->stream);
-  launch_permute64(f.V, f.lvl_nodes, f.s2, delay, false, c->stream);
-  c->launches += 3;
+  launch_elmore_fwd(c, R, C, delay, c->stream);
   CK(cudaGetLastError());
   return LA_OK;
 }
@@ -1298,19 +1344,7 @@ la_status la_elmore_backward(la_ctx* c, const double* R, const double* C, const 
   TRY(check_assigned(c));
   if (!R || !C || !gd || !dR || !dC) return set_err(c, LA_ERR_INVALID, "la_elmore_backward: null pointer");
   DeviceGuard g(c->device);
-  Forest& f = c->forest;
-  // gather R, C, g into internal order; dR, dC come back through the same
-  // scratch (each input is consumed by the pass that precedes its reuse)
-  double* gi = reinterpret_cast<double*>(f.A);  // V doubles of the DP table are free between rounds
-  launch_permute64(f.V, f.lvl_nodes, R, f.s3, true, c->stream);
-  launch_permute64(f.V, f.lvl_nodes, C, f.s4, true, c->stream);
-  launch_permute64(f.V, f.lvl_nodes, gd, gi, true, c->stream);
-  double* dRi = reinterpret_cast<double*>(f.Cc);
-  double* dCi = reinterpret_cast<double*>(f.M);
-  launch_elmore_bwd(c, f.s3, f.s4, gi, dRi, dCi, nullptr, nullptr, c->stream);
-  launch_permute64(f.V, f.lvl_nodes, dRi, dR, false, c->stream);
-  launch_permute64(f.V, f.lvl_nodes, dCi, dC, false, c->stream);
-  c->launches += 5;
+  launch_elmore_bwd(c, R, C, gd, dR, dC, c->stream);
   CK(cudaGetLastError());
   return LA_OK;
 }
@@ -1322,13 +1356,8 @@ la_status la_reweight_adjoint(la_ctx* c) {
   // The adjoint with g = kappa at pins: W = Ws (the kappa sums below, which
   // depend on the forest only: computed once per forest) and r_est = U (the
   // top-down pass over the current assignment's R).
-  if (!f.wsum_valid) {
-    launch_rc_from_assignment(c, f.s3, f.s4, nullptr, c->stream);
-    launch_elmore_bwd(c, f.s3, f.s4, f.gk, nullptr, nullptr, f.W_adj, f.rho_adj, c->stream);
-    f.wsum_valid = true;
-  } else {
-    launch_elmore_adj_only(c, f.W_adj, f.rho_adj, c->stream);
-  }
+  launch_reweight(c, !f.wsum_valid, c->stream);
+  f.wsum_valid = true;
   CK(cudaGetLastError());
   f.have_adj = true;
   return LA_OK;

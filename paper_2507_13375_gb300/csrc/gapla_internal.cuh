@@ -38,6 +38,7 @@ __host__ __device__ inline int node_class(bool root, int sons, bool has_pin) {
 }
 constexpr int kSizeClasses = 16;
 constexpr int kMinBigSc = 5;  // nets of 17+ nodes get per-net level lists
+constexpr int kElmSmall = 32; // the Elmore passes sweep nets of at most 32 nodes in input order
 __host__ __device__ inline int size_class(int64_t m) {
   int s = 0;
   while ((int64_t(1) << s) < m && s < kSizeClasses - 1) ++s;
@@ -167,6 +168,10 @@ struct Forest {
   int8_t* t = nullptr;
   int8_t* layer_old = nullptr;          // [V] the layers a multi-batch round starts from
   bool have_assign = false;
+  // Elmore passes of the nets of at most kElmSmall nodes, input order:
+  // ep = internal id | len << 32 | (pin + 1) << 48 | (local parent + 1) << 56, ecap = sink cap
+  uint64_t* ep = nullptr;               // [V]
+  double* ecap = nullptr;               // [V]
   // Elmore scratch (internal order)
   double* s0 = nullptr;                 // [V]
   double* s1 = nullptr;
@@ -204,6 +209,7 @@ struct Grid {
   DevTables tab;                        // host copy
   DevTables* tab_dev = nullptr;
   bool P_valid = false;                 // P holds the prefix of the current (D, H, hist_w)
+  double round_hist_w = 1.0;            // hist_w of the last round (la_commit_demand uses it)
   bool fused_scan = false;              // the round's demand update runs inside the line scan
   double P_hist_w = -1.0;
 };
@@ -313,8 +319,10 @@ struct RoundW {
 };
 // from_diff: 0 the prefix of the current D and H; 1 D := the difference
 // array's prefix, then H += max(0, D - C) and the statistics; 2 D += that
-// prefix (between the batches of a round: H and the statistics untouched).
-// The difference array is cleared in modes 1 and 2.
+// prefix (between the batches of a round: H and the statistics untouched);
+// 3 the current D as given (a sharded round's summed demand), then
+// H += max(0, D - C) and the statistics.  The difference array is cleared in
+// modes 1 and 2.
 void launch_scan_lines(la_ctx* c, int from_diff, double hist_w, double* red_tof, cudaStream_t s);
 // the demand update and the line scan of the end of a round (fused when a
 // line's difference array fits in shared memory: prepare_fused_scan at load)
@@ -322,6 +330,9 @@ constexpr size_t kFusedLineMaxBytes = 96 * 1024;
 size_t fused_line_bytes(const LayerInfo& li);
 bool prepare_fused_scan(const LayerInfo& li);
 void launch_demand_scan(la_ctx* c, double hist_w, double* red_tof, cudaStream_t s);
+// the end of a round that is one shard of a round split by nets: D := the
+// demand of this context's nets (global atomics, then a scan); H untouched
+void launch_local_demand(la_ctx* c, double hist_w, double* red_tof, cudaStream_t s);
 // kmax: nodes of nets up to size class kmax (kSizeClasses - 1 = every node)
 // cache: the batched form's constant-cache set to read (0 Eq. 4, 1 adjoint), or
 // kNoCache to recompute the constants in the DP (the plain form)
@@ -347,14 +358,19 @@ int scan_blocks(const LayerInfo& li);
 // k_elmore.cu
 // R, C in internal order, or scattered to input order when perm != nullptr
 void launch_rc_from_assignment(la_ctx* c, double* R, double* C, const int32_t* perm, cudaStream_t s);
+// the input-order pack (ep, ecap) of `out` from the input-order forest `in`
+void launch_elm_pack(const Forest& in, const int32_t* in2int, Forest& out, cudaStream_t s);
+// delays from given R_seg, C_seg; every array in input order
 void launch_elmore_fwd(la_ctx* c, const double* R, const double* C, double* delay, cudaStream_t s);
 // the delays of the current assignment (R_seg, C_seg from its layers), input order
 void launch_elmore_assignment(la_ctx* c, double* delay_input_order, cudaStream_t s);
-void launch_elmore_bwd(la_ctx* c, const double* R, const double* C, const double* g, double* dR,
-                       double* dC, double* Wsum_out, double* UJ_out, cudaStream_t s);
-// Top-down pass only: U from Ws (given) and R_seg = len x unit R of the
-// assignment's layer (the expression of la_rc_from_assignment), into UJ_out.
-void launch_elmore_adj_only(la_ctx* c, const double* Ws, double* UJ_out, cudaStream_t s);
+// dL/dR_seg, dL/dC_seg of L = sum g delay from given R_seg, C_seg, g; input order
+void launch_elmore_bwd(la_ctx* c, const double* R, const double* C, const double* g, double* dR, double* dC,
+                       cudaStream_t s);
+// The DP's adjoint weights on the current assignment (R_seg = len x unit R of
+// the layer): with_wsum, W_adj = the sums of g = kappa below each node, then
+// rho_adj = U_J; else rho_adj = U_J from the W_adj already there.
+void launch_reweight(la_ctx* c, bool with_wsum, cudaStream_t s);
 
 // error message of calls that have no context (read by la_last_error(NULL))
 void set_noctx_error(const std::string& msg);

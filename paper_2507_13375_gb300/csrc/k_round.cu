@@ -147,12 +147,12 @@ __global__ void __launch_bounds__(kScanT, (NLD <= 8 ? 3 : 1)) k_scan_lines(const
     for (int q = 0; q < NLD; ++q) {
       if (q < nld) {
         if constexpr (FUSED) Dv[q] = valid ? s_line[pos * nld + q] : 0;
-        else Dv[q] = a.from_diff ? (valid ? a.diff[row + q] : 0) : (edge ? a.D[row + q] : 0);
+        else Dv[q] = (a.from_diff == 1 || a.from_diff == 2) ? (valid ? a.diff[row + q] : 0) : (edge ? a.D[row + q] : 0);
         cv[q] = edge ? a.cap[row + q] : 0;
         hv[q] = edge ? a.H[row + q] : 0;
       }
     }
-    if (a.from_diff) {
+    if (a.from_diff == 1 || a.from_diff == 2) {
 #pragma unroll
       for (int q = 0; q < NLD; ++q) {
         if (q < nld) {
@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(kScanT, (NLD <= 8 ? 3 : 1)) k_scan_lines(const
           const int32_t c = cv[q];
           int32_t h = hv[q];
           const int si = c > 0 ? 0 : 1;
-          if (a.from_diff == 1) {
+          if (a.from_diff == 1 || a.from_diff == 3) {
             const int32_t over = Dv[q] - c;
             const int l = s_lay[q];
             if (over > 0) { h += over; a.H[row + q] = h; relu += (unsigned long long)over; }
@@ -361,6 +361,13 @@ void launch_demand_scan(la_ctx* c, double hist_w, double* tof_part, cudaStream_t
     launch_demand(c, s);
     launch_scan_lines(c, 1, hist_w, tof_part, s);
   }
+}
+
+void launch_local_demand(la_ctx* c, double hist_w, double* tof_part, cudaStream_t s) {
+  Grid& g = c->grid;
+  cudaMemsetAsync(g.D, 0, size_t(g.G) * sizeof(int32_t), s);
+  launch_demand(c, s);
+  launch_scan_lines(c, 2, hist_w, tof_part, s);
 }
 
 // ---------------------------------------------------------------------------

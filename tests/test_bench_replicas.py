@@ -1,8 +1,9 @@
-"""The multi-GPU form of the bench is N independent replicas (one process per
-GPU, seed = rank, no data-path collective): its host logic on 2 gloo ranks on
-the CPU - max-over-ranks timing, whole-job throughput, one forest per rank -
-and the reference arm: its ranks other than 0 exit without work, rank 0
-prints the bench line."""
+"""The multi-GPU form of the bench splits the workload's nets over the ranks
+(one process per GPU) with one demand all-reduce per round: its host logic
+on 2 gloo ranks on the CPU - max-over-ranks timing, counts summed over the
+ranks, each rank's node-balanced net range of the one forest - and the
+reference arm: its ranks other than 0 exit without work, rank 0 prints the
+bench line."""
 import json
 import os
 import socket
@@ -28,31 +29,35 @@ def _worker(rank, world, port, out):
 
     import bench
     import forestgen as fg
+    from paper_2507_13375_gb300 import shard as sh
 
     dist.init_process_group("gloo", rank=rank, world_size=world)
     local_ms = 100.0 + 50.0 * rank
     m = bench.max_over_ranks(local_ms, dist, "cpu")
-    value = bench.job_rate(world, 1000.0, m)
+    total = bench.sum_over_ranks(10.0 + rank, dist, "cpu")
     wl = fg.WORKLOADS[1].scaled(40)
-    f = fg.make_forest(wl, bench.replica_seed(rank))
-    sig = [int(f["num_nodes"]), int(np.sum(f["x"].astype(np.int64) * 31 + f["y"]))]
-    sigs = [None] * world
-    dist.all_gather_object(sigs, sig)
+    f = fg.make_forest(wl, 0)
+    lo, hi = sh.shard_ranges(f["net_ptr"], world)[rank]
+    mine = sh.shard_forest(f, lo, hi)
+    parts = [None] * world
+    dist.all_gather_object(parts, (lo, hi, int(mine["num_nodes"])))
     if rank == 0:
         with open(out, "w") as fh:
-            json.dump({"max_ms": m, "value": value, "sigs": sigs}, fh)
+            json.dump({"max_ms": m, "total": total, "parts": parts, "V": int(f["num_nodes"]),
+                       "N": int(f["num_nets"])}, fh)
     dist.barrier()
     dist.destroy_process_group()
 
 
-def test_replicas_on_two_gloo_ranks(tmp_path):
+def test_ranks_on_two_gloo_ranks(tmp_path):
     out = str(tmp_path / "r.json")
     mp.spawn(_worker, args=(2, _free_port(), out), nprocs=2, join=True)
     with open(out) as fh:
         r = json.load(fh)
     assert r["max_ms"] == 150.0                     # the slower rank's time
-    assert r["value"] == 2 * 1000.0 / 0.150         # units of both ranks over it
-    assert r["sigs"][0] != r["sigs"][1]             # each replica its own forest
+    assert r["total"] == 21.0                       # a count of both ranks
+    (lo0, hi0, v0), (lo1, hi1, v1) = r["parts"]     # one forest, split by nets
+    assert lo0 == 0 and hi0 == lo1 and hi1 == r["N"] and v0 + v1 == r["V"]
 
 
 def test_reference_arm_other_ranks_exit_without_work():

@@ -36,3 +36,16 @@ def test_dp_flops_by_hand():
     dirs = (0, 1, 0, 1)
     assert bench.dp_algorithmic_flops(_forest([_net(0)]), dirs) == 118.0
     assert bench.dp_algorithmic_flops(_forest([_net(0), _net(20)]), dirs) == 236.0
+
+
+def test_roofline_byte_rules():
+    """The DP's compulsory bytes per segment, S (20 + 50 L_d) + 10 S: 320 B per
+    segment at 12 layers (L_d = 6) and 270 B at 10, plus 10 B of backtrack; the
+    Elmore passes 40 B (forward) and 48 B (adjoint) per RC node, two per
+    segment."""
+    assert bench.dp_method_bytes(1, 6.0) == 330.0
+    assert bench.dp_method_bytes(1000, 5.0) == 280_000.0
+    e = bench.elmore_method_bytes(10)
+    assert e == {"rc_nodes": 20, "forward": 800.0, "adjoint": 960.0}
+    # the batched form's own count (its constant caches included) is larger
+    assert bench.dp_cache_bytes(V=7, S=6, N=1, LD=6) > bench.dp_method_bytes(6, 6.0)

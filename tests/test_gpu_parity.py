@@ -717,3 +717,35 @@ def test_set_assignment_checks_its_input(la):
     a.set_assignment(layer, b, t)
     la.la_check(a.ctx)
     a.close()
+
+
+def test_elmore_small_and_large_nets(la):
+    """The Elmore passes on the uneven workload (Zipf pin counts: nets from 2
+    to thousands of nodes, so both the per-net kernel of small nets and the
+    block-per-net kernel of large ones run): delays, gradients and the
+    adjoint weights against the oracle, and la_elmore_assignment equal to
+    la_elmore of la_rc_from_assignment bit for bit."""
+    wl = fg.WORKLOADS[4].scaled(20000)
+    grid, forest = fg.make_grid(wl, 23), fg.make_forest(wl, 23)
+    sizes = np.diff(forest["net_ptr"])
+    assert (sizes <= 32).sum() > 1000 and (sizes > 32).sum() > 100 and sizes.max() > 2000
+    a = _assigner(la, grid, forest)
+    a.assign_round(reset=True, **la.DEFAULT_WEIGHTS)
+    layer, b, t = (x.cpu().numpy() for x in a.get_assignment())
+    R, C = a.rc_from_assignment()
+    Rn, Cn = R.cpu().numpy(), C.cpu().numpy()
+    d = a.elmore(R, C)
+    assert torch.equal(a.elmore_assignment(), d)
+    np.testing.assert_allclose(d.cpu().numpy(), oracle.elmore(grid, forest, layer, b, t, Rn, Cn), rtol=1e-10, atol=0)
+    rng = np.random.default_rng(5)
+    g = rng.uniform(0.0, 1.0, len(Rn))
+    dR, dC = a.elmore_backward(R, C, torch.from_numpy(g).cuda())
+    dR_ref, dC_ref, _, _ = oracle.elmore_backward(grid, forest, layer, b, t, Rn, Cn, g)
+    np.testing.assert_allclose(dR.cpu().numpy(), dR_ref, rtol=1e-10, atol=0)
+    np.testing.assert_allclose(dC.cpu().numpy(), dC_ref, rtol=1e-10, atol=0)
+    for _ in range(2):  # the first reweighting sums W, the second reuses it
+        a.reweight_adjoint()
+        W, rho = (x.cpu().numpy() for x in a.get_weights(la.LA_WEIGHTS_ADJOINT))
+        Wr, rhor = oracle.adjoint_weights(grid, forest, layer, b, t)
+        assert np.array_equal(W, Wr) and np.array_equal(rho, rhor)
+    a.close()
