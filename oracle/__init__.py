@@ -31,6 +31,12 @@ Parity status of each function (what pins it, see tests/test_oracle_pins.py):
                form, and the d_34 = R_34 (C4+C5+C6+C7) example of Sec. III-D.
   elmore_backward  pinned to the closed forms dT/dR = Wsum Cdown and
                dT/dC = sum of R Wsum above, and to central differences.
+  logistic_pin_weight  pinned to the logistic's fixed points: 1/2 at
+               slack / WNS = b, about 1 at the worst slack, symmetry
+               w(b + d) + w(b - d) = 1, monotone in the slack ratio.
+  partition_batches  pinned by hand-built nets on every interval edge of
+               Alg. 1 (criticality halvings, slack edges 1 - j^2/100) and by
+               the interval rule checked net by net in exact arithmetic.
 """
 from __future__ import annotations
 
@@ -103,8 +109,12 @@ def _load():
         lib.or_rc_from_assignment.argtypes = [P(_Grid), P(_Forest), vp, vp, vp]
         lib.or_elmore.argtypes = [P(_Grid), P(_Forest)] + [vp] * 8
         lib.or_elmore_backward.argtypes = [P(_Grid), P(_Forest)] + [vp] * 11
+        lib.or_logistic_pin_weight.argtypes = [ctypes.c_int64, vp, vp, ctypes.c_double, ctypes.c_double,
+                                               ctypes.c_double, vp]
+        lib.or_partition_batches.restype = ctypes.c_int32
+        lib.or_partition_batches.argtypes = [ctypes.c_int64, vp, vp, ctypes.c_double, ctypes.c_double, vp]
         for fn in ("or_penalty_table", "or_penalty", "or_weights_eq4", "or_demand",
-                   "or_rc_from_assignment", "or_elmore", "or_elmore_backward"):
+                   "or_rc_from_assignment", "or_elmore", "or_elmore_backward", "or_logistic_pin_weight"):
             getattr(lib, fn).restype = None
         _lib = lib
     return _lib
@@ -350,3 +360,24 @@ def adjoint_weights(grid, forest, layer, b, t):
     g = np.where(np.asarray(forest["pin_layer"]) >= 0, forest["kappa"], 0.0)
     _, _, Ws, UJ = elmore_backward(grid, forest, layer, b, t, R, C, g)
     return Ws, UJ
+
+
+def logistic_pin_weight(pin_layer, slack, wns: float, k: float = 10.0, b: float = 0.3):
+    """Sec. III-C pin weights: 1 / (1 + e^{-k (slack / WNS - b)}) at pins, 0 elsewhere."""
+    keep = _Keep()
+    V = len(pin_layer)
+    w = np.empty(V)
+    _load().or_logistic_pin_weight(V, keep.ptr(pin_layer, np.int8), keep.ptr(slack, np.float64), float(wns),
+                                   float(k), float(b), w.ctypes.data)
+    return w
+
+
+def partition_batches(crit, slack=None, critical_frac: float = 0.5, slack_ratio: float = 0.7):
+    """Alg. 1's partition of the nets into batches: (batch ids, number of batches)."""
+    keep = _Keep()
+    N = len(crit)
+    out = np.empty(N, np.int32)
+    nb = _load().or_partition_batches(N, keep.ptr(crit, np.float64),
+                                      None if slack is None else keep.ptr(slack, np.float64),
+                                      float(critical_frac), float(slack_ratio), out.ctypes.data)
+    return out, int(nb)

@@ -568,3 +568,62 @@ void or_elmore_backward(const or_grid* g, const or_forest* f, const int8_t* laye
   }
   free(S.ptr); free(S.list); free(S.fill);
 }
+
+/* ------------------------------------------------------------------------ */
+/* Net ordering (Sec. III-A, Alg. 1) and pin weights (Sec. III-C)            */
+/* ------------------------------------------------------------------------ */
+/* Pin weight of Sec. III-C, read as the logistic of the slack ratio (the
+ * printed form is garbled; the text says the weight is about 1 for a pin at
+ * the worst slack): x = slack / WNS with WNS < 0 the worst slack,
+ * w = 1 / (1 + e^{-k (x - b)}); 0 at a node without a pin. */
+void or_logistic_pin_weight(int64_t V, const int8_t* pin_layer, const double* slack, double wns, double k,
+                            double b, double* w) {
+  for (int64_t v = 0; v < V; v++) {
+    if (pin_layer[v] < 0) { w[v] = 0.0; continue; }
+    double x = slack[v] / wns;
+    w[v] = 1.0 / (1.0 + exp(-k * (x - b)));
+  }
+}
+
+/* Alg. 1's partition of the nets into batches (Divide, then Partition):
+ *   C = the largest criticality; the critical nets (crit >= critical_frac C,
+ *   C > 0) go by criticality interval: [C, C] first, then [C/2, C),
+ *   [C/4, C/2), ... (interval k >= 1 holds C 2^-k <= crit < C 2^-(k-1));
+ *   then, with slack given and WNS = the least slack < 0, the other nets with
+ *   slack <= slack_ratio WNS by slack interval: slack = WNS first, then the
+ *   edges e_j = WNS (1 - j^2 / 100) (interval j >= 1 holds
+ *   e_(j-1) < slack <= e_j: 0.99 WNS, 0.96 WNS, ...);
+ *   every other net last.
+ * Batch ids number the non-empty intervals in that order from 0.  Returns
+ * the number of batches. */
+int32_t or_partition_batches(int64_t N, const double* crit, const double* slack, double critical_frac,
+                             double slack_ratio, int32_t* batch) {
+  double C = 0.0, wns = 0.0;
+  for (int64_t n = 0; n < N; n++) if (crit[n] > C) C = crit[n];
+  if (slack) for (int64_t n = 0; n < N; n++) if (slack[n] < wns) wns = slack[n];
+  int used[256] = {0};
+  for (int64_t n = 0; n < N; n++) {
+    int id = 255;  /* the rest */
+    if (C > 0.0 && crit[n] >= critical_frac * C) {
+      int k = 0;
+      if (crit[n] != C) {
+        k = 1;
+        while (crit[n] < ldexp(C, -k)) k++;
+      }
+      id = k < 127 ? k : 127;
+    } else if (slack && wns < 0.0 && slack[n] <= slack_ratio * wns) {
+      int j = 0;
+      if (slack[n] != wns) {
+        j = 1;
+        while (!(slack[n] <= wns * (1.0 - (double)(j * j) / 100.0))) j++;
+      }
+      id = 128 + (j < 126 ? j : 126);
+    }
+    batch[n] = id;
+    used[id] = 1;
+  }
+  int32_t map[256], nb = 0;
+  for (int i = 0; i < 256; i++) map[i] = used[i] ? nb++ : -1;
+  for (int64_t n = 0; n < N; n++) batch[n] = map[batch[n]];
+  return nb;
+}

@@ -455,3 +455,73 @@ def test_stack_tie_fewest_vias_then_lowest_bottom():
 
     arg = _tie_check(stack_tie_case())
     assert [0, 2, 3] in arg
+
+
+# ---------------------------------------------------------------------------
+# Pin weights (Sec. III-C) and Alg. 1's partition (Sec. III-A)
+# ---------------------------------------------------------------------------
+def test_logistic_pin_weight_fixed_points():
+    """The logistic of the slack ratio x = slack / WNS: exactly 1/2 at x = b,
+    close to 1 at the worst slack (x = 1: the paper's "nearly 1"), small for
+    positive slack, symmetric about b, increasing in x, 0 off the pins."""
+    k, b = 10.0, 0.3
+    x = np.array([0.3, 1.0, -0.5, 0.0, 0.3 + 0.125, 0.3 - 0.125, 0.3 + 0.25, 0.3 - 0.25, 0.15, 0.8, 0.99])
+    pin = np.zeros(len(x) + 1, np.int8)
+    pin[-1] = -1
+    slack = np.append(x, 5.0)          # WNS = -1: the slack ratio is -slack
+    w = oracle.logistic_pin_weight(pin, -slack, -1.0, k, b)
+    assert w[0] == 0.5
+    assert 0.999 < w[1] < 1.0
+    assert w[2] < 1e-3 and w[3] < 0.05
+    for i in (4, 6):
+        assert abs(w[i] + w[i + 1] - 1.0) <= 2.0 ** -52
+    xs, first = np.unique(x, return_index=True)
+    assert np.all(np.diff(w[first]) > 0)
+    assert w[-1] == 0.0
+
+
+def test_partition_on_interval_edges():
+    """Nets placed on every interval edge of Alg. 1: criticality C = 8 with
+    critical_frac 1/4 gives [8, 8], [4, 8), [2, 4); slack with WNS = -100 and
+    slack_ratio 0.7 gives slack = WNS, (WNS, 0.99 WNS], (0.99 WNS, 0.96 WNS],
+    ..., (0.75 WNS, 0.64 WNS]; the rest last; ids without gaps."""
+    crit = np.array([8, 4, 6, 2, 3.9999, 0.5, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 1.0])
+    slack = np.array([-1, -1, -1, -1, -1, -100, -99, -99.5, -98.9, -96, -71, -69, 0.0, -100.0])
+    got, nb = oracle.partition_batches(crit, slack, critical_frac=0.25, slack_ratio=0.7)
+    # net by net: critical interval k, semi-critical interval j, or the rest
+    keys = [("c", 0), ("c", 1), ("c", 1), ("c", 2), ("c", 2),  # 8, 4, 6, 2, 3.9999
+            ("s", 0), ("s", 1), ("s", 1), ("s", 2), ("s", 2),  # -100, -99, -99.5, -98.9, -96
+            ("s", 6), ("r", 0), ("r", 0), ("s", 0)]             # -71, -69 (> 0.7 WNS), 0, -100
+    rank = {"c": 0, "s": 1, "r": 2}
+    order = sorted(set(keys), key=lambda t: (rank[t[0]], t[1]))
+    want = [order.index(t) for t in keys]
+    assert list(got) == want and nb == len(order) == 8
+    # without slack: critical nets, then one batch
+    got2, nb2 = oracle.partition_batches(crit, None, critical_frac=0.25)
+    assert list(got2) == [0, 1, 1, 2, 2, 3, 3, 3, 3, 3, 3, 3, 3, 3] and nb2 == 4
+
+
+def test_partition_matches_exact_intervals():
+    """Random criticalities and slacks: each net's batch follows from its
+    interval computed in exact rational arithmetic, and the batch ids are
+    those intervals in Alg. 1's order."""
+    rng = np.random.default_rng(4)
+    N = 3000
+    crit = rng.uniform(0, 10, N) ** 2
+    slack = rng.uniform(-50, 20, N)
+    got, nb = oracle.partition_batches(crit, slack, critical_frac=0.1, slack_ratio=0.7)
+    C, W = Fr(float(crit.max())), Fr(float(slack.min()))
+    keys = []
+    for c, s in zip(crit, slack):
+        c, s = Fr(float(c)), Fr(float(s))
+        if c >= Fr(1, 10) * C:
+            k = 0 if c == C else next(k for k in range(1, 200) if c >= C / 2 ** k)
+            keys.append((0, k))
+        elif s <= Fr(7, 10) * W:
+            j = 0 if s == W else next(j for j in range(1, 200) if s <= W * (1 - Fr(j * j, 100)))
+            keys.append((1, j))
+        else:
+            keys.append((2, 0))
+    order = sorted(set(keys))
+    assert nb == len(order)
+    assert list(got) == [order.index(t) for t in keys]
