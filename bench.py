@@ -658,9 +658,11 @@ def bench_reference(args):
 
 
 def profile_case(args):
-    """A short run for ncu: load the workload, `--rounds` rounds and one adjoint
-    reweighting plus an Elmore forward, no timing, no CPU baseline; with
-    `--reloads K`, K reloads of the forest before the rounds."""
+    """A short run for ncu: load the workload, `--rounds` rounds, each with its
+    adjoint reweighting, and an Elmore forward, no timing, no CPU baseline; the
+    last round, its reweighting and the Elmore forward inside the NVTX range
+    profile_round; with `--reloads K`, K reloads of the forest before the
+    rounds."""
     import numpy as np
     import torch
 
@@ -694,9 +696,16 @@ def profile_case(args):
             load_ms.append(round((time.perf_counter() - t0) * 1e3, 3))
     mode = la.LA_MODE_BATCHED if args.mode == "batched" else la.LA_MODE_PLAIN
     for r in range(args.rounds):
+        last = r == args.rounds - 1
+        if last:  # the steady-state round (after the tuner's trials), for ncu --nvtx-include profile_round/
+            torch.cuda.synchronize()
+            nvtx_push(torch, "profile_round")
         st = a.assign_round(mode=mode, reset=(r == 0), weights=la.LA_WEIGHTS_EQ4 if r == 0 else la.LA_WEIGHTS_ADJOINT)
         a.reweight_adjoint()
-    a.elmore_assignment()
+        if last:
+            a.elmore_assignment()
+            torch.cuda.synchronize()
+            nvtx_pop(torch)
     torch.cuda.synchronize()
     print(json.dumps({"profile_case": wl.name, "nets": wl.num_nets, "nodes": int(forest["num_nodes"]),
                       "rounds": args.rounds, "last_round_ms": st["ms"], "device_bytes": a.device_bytes(),
@@ -753,7 +762,8 @@ def ablation(args):
     net_of = np.repeat(np.arange(N), np.diff(forest["net_ptr"]))
     crit = np.zeros(N)
     np.maximum.at(crit, net_of, forest["kappa"])
-    batch = la.batches_by_criticality(crit, critical_frac=0.5)
+    batch_t, _ = la.la_partition_batches(torch.from_numpy(crit).cuda(), critical_frac=0.5)
+    batch = batch_t.cpu().numpy()
     for name, fb in (("one batch", forest), ("criticality batches", dict(forest, batch=batch))):
         a.load_nets(fb)
         st = None

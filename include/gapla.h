@@ -126,8 +126,11 @@ typedef struct {
                               after the other in increasing id; each sees the
                               demand the batches before it committed (the
                               sequential batches of Sec. III-A).  Null: one batch,
-                              every net against one snapshot.  Several batches
-                              need LA_MODE_PLAIN.                                    */
+                              every net against one snapshot.  In LA_MODE_BATCHED
+                              the batches run as level waves of the class kernels
+                              with the constant caches, the whole round in one
+                              CUDA graph (no persistent kernels, no tuning:
+                              tail_threshold and force_split are not used).      */
 } la_net_desc;
 #define LA_MAX_BATCHES 4096
 
@@ -283,6 +286,42 @@ la_status la_reweight_adjoint(la_ctx* ctx);
 /* Copy the DP weights out (device, V each): W[v] and r_est[v] of the given
  * source (LA_WEIGHTS_EQ4 or LA_WEIGHTS_ADJOINT). */
 la_status la_get_weights(la_ctx* ctx, int32_t source, double* W, double* rho);
+
+/* ---------------------------------------------------------------------------
+ * Net ordering (Sec. III-A) and pin weights (Sec. III-C).  Context-free: they
+ * run on the calling thread's current CUDA device, on `stream`.
+ * ------------------------------------------------------------------------- */
+/* Pin weights of Sec. III-C: weight[v] = 1 / (1 + e^{-k (slack[v] / wns - b)})
+ * at pin nodes (pin_layer[v] >= 0), 0 elsewhere; the paper's k = 10, b = 0.3.
+ * The printed formula is garbled (1 / (1 + k (x - b)) would not be near 1 at
+ * the worst slack, as the text says the weight is); the logistic is the
+ * reading taken.  Passed as la_net_desc.kappa, Eq. 4 then takes the largest
+ * weight below each node as its edge weight.
+ *   pin_layer: device, V; slack: device, V (the pins' slack; others unread);
+ *   wns: the worst negative slack, finite and < 0 (else LA_ERR_INVALID);
+ *   weight: device, V, written.  Enqueues only. */
+la_status la_logistic_pin_weight(const int8_t* pin_layer, const double* slack, int64_t V, double wns, double k,
+                                 double b, double* weight, void* stream);
+/* Alg. 1's partition of the nets into batches (Divide, then Partition):
+ *   C = the largest criticality; the critical nets (crit >= critical_frac C,
+ *   C > 0) first, by criticality interval: [C, C], then [C/2, C), [C/4, C/2),
+ *   ... (interval k >= 1 holds C 2^-k <= crit < C 2^-(k-1));
+ *   then, with slack given and WNS = the least slack < 0, the other nets with
+ *   slack <= slack_ratio WNS, by slack interval: slack = WNS, then
+ *   e_(j-1) < slack <= e_j for the edges e_j = WNS (1 - j^2 / 100)
+ *   (0.99 WNS, 0.96 WNS, ...);
+ *   every other net last.
+ * The batch ids number the non-empty intervals in that order from 0 (a
+ * forest's la_net_desc.batch).  The paper counts critical paths through a net
+ * as its criticality and takes its worst pin slack as its slack; both come
+ * from the caller (static timing analysis is outside this library).
+ *   crit: device, N, finite and >= 0; slack: device, N, finite, or NULL;
+ *   critical_frac, slack_ratio in (0, 1] (the paper's 0.7 for the slack);
+ *   batch: device, N, written; num_batches: host, written.
+ * Synchronises the stream; allocates and frees a small scratch buffer.
+ * LA_ERR_INVALID for a negative or non-finite input (batch is then undefined). */
+la_status la_partition_batches(const double* crit, const double* slack, int64_t N, double critical_frac,
+                               double slack_ratio, int32_t* batch, int32_t* num_batches, void* stream);
 
 /* Measurement helper (the paper has no counterpart): the rate of FP64 fused
  * multiply-adds this GPU sustains, from a kernel of independent FMA chains on

@@ -36,7 +36,8 @@ EXPORTS = ("la_create", "la_destroy", "la_last_error", "la_set_stream", "la_devi
            "la_load_grid", "la_load_nets", "la_assign_round", "la_get_assignment", "la_set_assignment",
            "la_get_net_cost", "la_get_state", "la_set_state", "la_rc_from_assignment", "la_elmore",
            "la_elmore_backward", "la_elmore_assignment", "la_reweight_adjoint", "la_get_weights",
-           "la_inject_fault", "la_probe_fp64", "la_commit_demand", "la_elmore_static")
+           "la_inject_fault", "la_probe_fp64", "la_commit_demand", "la_logistic_pin_weight",
+           "la_partition_batches", "la_elmore_static")
 LA_STATIC_MAX_NODES = 1 << 21
 
 
@@ -105,6 +106,10 @@ def library() -> ctypes.CDLL:
         "la_get_weights": [vp, i32, vp, vp], "la_inject_fault": [vp, ctypes.c_int],
         "la_probe_fp64": [ctypes.c_int, vp, P(ctypes.c_double)],
         "la_commit_demand": [vp, vp, P(RoundStats)],
+        "la_logistic_pin_weight": [vp, vp, ctypes.c_int64, ctypes.c_double, ctypes.c_double, ctypes.c_double, vp,
+                                   vp],
+        "la_partition_batches": [vp, vp, ctypes.c_int64, ctypes.c_double, ctypes.c_double, vp,
+                                 P(ctypes.c_int32), vp],
         "la_elmore_static": [P(NetDesc), vp, vp, vp, i32, vp, ctypes.c_double, vp, vp, vp, vp],
     }
     for name, args in sig.items():
@@ -281,49 +286,42 @@ def la_inject_fault(ctx, code: int):
     _check(ctx, library().la_inject_fault(ctx, int(code)))
 
 
-def batches_by_criticality(crit, slack=None, critical_frac: float = 0.5, slack_ratio: float = 0.7):
-    """Net batches after Alg. 1 (Sec. III-A), from per-net criticality `crit`
-    (>= 0; the paper counts critical paths through the net) and optionally
-    per-net slack (<= 0 is bad; the paper's net slack is its worst pin slack):
+def la_logistic_pin_weight(pin_layer, slack, wns: float, k: float = 10.0, b: float = 0.3, stream=None):
+    """Sec. III-C pin weights (CUDA tensors in, a new float64 tensor out): the
+    logistic of slack / WNS at pins, 0 elsewhere (see include/gapla.h)."""
+    lib = library()
+    pin_layer, slack = pin_layer.contiguous(), slack.contiguous()
+    if pin_layer.dtype != torch.int8 or slack.dtype != torch.float64 or pin_layer.numel() != slack.numel():
+        raise LaError(LA_ERR_INVALID, "la_logistic_pin_weight: int8 pin_layer and float64 slack of one length")
+    w = torch.empty_like(slack)
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    st = lib.la_logistic_pin_weight(_ptr(pin_layer), _ptr(slack), int(slack.numel()), float(wns), float(k), float(b),
+                                    _ptr(w), ctypes.c_void_p(stream))
+    if st != LA_OK:
+        raise LaError(st, lib.la_last_error(None).decode())
+    return w
 
-      critical nets (crit >= critical_frac x C, C = max crit): one batch per
-        criticality interval [C, C], [C/2, C), [C/4, C/2), ...;
-      then the nets with slack worse than slack_ratio x WNS (WNS = min slack):
-        [WNS, WNS], [0.99 WNS, WNS), [0.96 WNS, 0.99 WNS), ... (edges 1 - k^2/100);
-      then every other net, in one batch.
 
-    Returns int32 batch ids, 0 first, with no empty batch in between."""
-    crit = np.asarray(crit, np.float64)
-    N = len(crit)
-    out = np.full(N, -1, np.int64)
-    C = float(crit.max()) if N else 0.0
-    nxt = 0
-    if C > 0:
-        is_crit = crit >= critical_frac * C
-        k = np.zeros(N, np.int64)
-        pos = is_crit & (crit < C)
-        k[pos] = np.ceil(np.log2(C / crit[pos]) - 1e-12).astype(np.int64)  # [C/2^k, C/2^(k-1))
-        ids = np.unique(k[is_crit])
-        for i, kk in enumerate(ids):
-            out[is_crit & (k == kk)] = nxt + i
-        nxt += len(ids)
-    if slack is not None:
-        slack = np.asarray(slack, np.float64)
-        wns = float(slack.min()) if N else 0.0
-        semi = (out < 0) & (slack <= slack_ratio * wns) if wns < 0 else np.zeros(N, bool)
-        if semi.any():
-            r = slack[semi] / wns  # in [slack_ratio, 1]
-            j = np.zeros(int(semi.sum()), np.int64)
-            below = r < 1.0
-            j[below] = np.maximum(1, np.ceil(np.sqrt(np.maximum(0.0, 1.0 - r[below]) * 100.0) - 1e-9)).astype(np.int64)
-            ids = np.unique(j)
-            sub = np.full(len(j), -1, np.int64)
-            for i, jj in enumerate(ids):
-                sub[j == jj] = nxt + i
-            out[semi] = sub
-            nxt += len(ids)
-    out[out < 0] = nxt
-    return out.astype(np.int32)
+def la_partition_batches(crit, slack=None, critical_frac: float = 0.5, slack_ratio: float = 0.7, stream=None):
+    """Alg. 1's partition of the nets into batches on the GPU (see
+    include/gapla.h): per-net criticality and optional slack (CUDA float64
+    tensors) -> (int32 batch ids, number of batches)."""
+    lib = library()
+    crit = crit.contiguous()
+    if crit.dtype != torch.float64 or (slack is not None and (slack.dtype != torch.float64
+                                                              or slack.numel() != crit.numel())):
+        raise LaError(LA_ERR_INVALID, "la_partition_batches: float64 crit and slack of one length")
+    slack = None if slack is None else slack.contiguous()
+    out = torch.empty(crit.numel(), dtype=torch.int32, device=crit.device)
+    nb = ctypes.c_int32()
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    st = lib.la_partition_batches(_ptr(crit), _ptr(slack), int(crit.numel()), float(critical_frac),
+                                  float(slack_ratio), _ptr(out), ctypes.byref(nb), ctypes.c_void_p(stream))
+    if st != LA_OK:
+        raise LaError(st, lib.la_last_error(None).decode())
+    return out, int(nb.value)
 
 
 def la_probe_fp64(device: int = 0, stream=None) -> float:

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 SO = os.path.join(LIBDIR, "libgapla.so")
-SOURCES = ["capi.cu", "k_load.cu", "k_round.cu", "k_elmore.cu", "k_static.cu", "k_probe.cu"]
+SOURCES = ["capi.cu", "k_load.cu", "k_round.cu", "k_elmore.cu", "k_static.cu", "k_probe.cu", "k_order.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "--fmad=false", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off"]
 

@@ -615,7 +615,7 @@ la_status la_load_nets(la_ctx* c, const la_net_desc* nd) {
   GETK(nf.A, V * LD); GETK(nf.Cc, V * LD); GETK(nf.M, V * LD); GETK(nf.B, V * LD); GETK(nf.sb, V * LD);
   GETK(nf.st, V * LD); GETK(nf.ent, V * LD); GETK(nf.Jroot, V); GETK(nf.layer, V); GETK(nf.b, V); GETK(nf.t, V);
   GETK(nf.s0, V); GETK(nf.s1, V); GETK(nf.s2, V); GETK(nf.s3, V); GETK(nf.s4, V); GETK(nf.W_adj, V);
-  GETK(nf.rho_adj, V); GETK(nf.ep, V); GETK(nf.ecap, V);
+  GETK(nf.rho_adj, V);
   const int nred = std::max(scan_blocks(c->grid.li), int((N + 255) / 256)) + 8;
   GETK(nf.red, size_t(nred) * 2);
 #undef GETK
@@ -628,13 +628,12 @@ la_status la_load_nets(la_ctx* c, const la_net_desc* nd) {
                           nf.big_queue, nf.root_of_net, nf.parent_g, nf.net_of, nf.pin, nf.sink_cap, nf.kappa,
                           nf.gk, nf.geo, nf.child_start, nf.nch, nf.child_list, nf.W_eq4, nf.rho_eq4, nf.A, nf.Cc,
                           nf.M, nf.B, nf.sb, nf.st, nf.ent, nf.Jroot, nf.layer, nf.b, nf.t, nf.s0, nf.s1, nf.s2,
-                          nf.s3, nf.s4, nf.W_adj, nf.rho_adj, nf.red, nf.ep, nf.ecap, in2int};
+                          nf.s3, nf.s4, nf.W_adj, nf.rho_adj, nf.red, in2int};
     for (const void* q : need)
       if (!q) return fail(set_err(c, LA_ERR_STATE, "la_load_nets: internal allocation missing"));
   }
   launch_renumber(tf, in2int, key_of, int64_t(nbk), nf, s);
-  launch_elm_pack(tf, in2int, nf, s);
-  c->launches += 2;
+  ++c->launches;
   {
     // the segments by (direction, line), for the demand pass
     const int nl0 = c->grid.li.nlines[0], nkeys = nl0 + c->grid.li.nlines[1];
@@ -728,7 +727,7 @@ static uint64_t round_signature(la_ctx* c, int si, const double* W, const double
                         f.parent_g, f.net_of, f.pin, f.sink_cap, f.kappa, f.gk, f.r_drv, f.geo, f.child_start,
                         f.nch, f.child_list, f.W_eq4, f.rho_eq4, f.W_adj, f.rho_adj, f.A, f.Cc, f.M, f.B,
                         f.ncache[si], f.scache[si], f.sb, f.st, f.ent, f.Jroot, f.layer, f.b, f.t, f.red,
-                        f.seg_node, f.seg_geo, f.seg_off, f.range_tab,
+                        f.seg_node, f.seg_geo, f.seg_off, f.range_tab, f.layer_old,
                         g.cap, g.D, g.H, g.diff, g.P, g.T_dev, g.tofT_dev, g.tab_dev, c->d_stats, c->d_err};
   uint64_t h = 1469598103934665603ull;
   for (const void* q : ptrs) h = fnv_mix(h, uint64_t(reinterpret_cast<uintptr_t>(q)));
@@ -798,6 +797,29 @@ static la_status enqueue_batched(la_ctx* c, const BatchPlan& bp, const RoundW& w
   }
   for (int h = hw; h >= 0; --h) launch_backtrack_level(c, h, bp.k, s);
   if (bp.n_big > 0) CK(cudaStreamWaitEvent(s, c->ev_join, 0));
+  CK(cudaGetLastError());
+  return LA_OK;
+}
+
+// The batched form of a forest in sequential batches (Sec. III-A): every net
+// in the level waves of the class kernels with the constant caches; after
+// batch k's DP and backtrack its nets' demand moves from their layers at the
+// round's start (layer_old; -1: none) to the new ones and the penalty prefix
+// is refreshed, so batch k + 1 sees it.  No persistent kernels and no tuning.
+static la_status enqueue_batched_multi(la_ctx* c, const RoundW& w, const double* W, const double* rho, int si,
+                                       cudaStream_t s) {
+  Forest& f = c->forest;
+  const int H1 = f.Hmax + 1;
+  for (int k = 0; k < f.nbatch; ++k) {
+    const int g0 = k * H1;
+    if (f.lvl_off[g0 + H1] == f.lvl_off[g0]) continue;  // an empty batch
+    for (int h = 0; h < H1; ++h) launch_dp_level(c, w, W, rho, g0 + h, kSizeClasses - 1, si, s);
+    for (int h = H1 - 1; h >= 0; --h) launch_backtrack_level(c, g0 + h, kSizeClasses - 1, s);
+    if (k + 1 < f.nbatch) {
+      launch_demand_delta(c, f.lvl_off[g0], f.lvl_off[g0 + H1], f.layer_old, s);
+      launch_scan_lines(c, 2, w.hist_w, f.red, s);
+    }
+  }
   CK(cudaGetLastError());
   return LA_OK;
 }
@@ -971,7 +993,8 @@ static la_status batched_graph(la_ctx* c, const RoundW& w, const double* W, cons
     };
     launch_node_round(c, w, rho, si, s);
     mark(c->ev[1]);
-    if (st == LA_OK) st = enqueue_batched(c, bp, w, W, rho, si, s);
+    if (st == LA_OK)
+      st = c->forest.nbatch > 1 ? enqueue_batched_multi(c, w, W, rho, si, s) : enqueue_batched(c, bp, w, W, rho, si, s);
     mark(c->ev[3]);
     Forest& f = c->forest;
     if (st == LA_OK) {
@@ -1049,10 +1072,27 @@ la_status la_assign_round(la_ctx* c, const la_round_params* p, la_round_stats* s
   const int si = p->weights == LA_WEIGHTS_ADJOINT ? 1 : 0;
   if (p->local_demand && f.nbatch > 1)
     return set_err(c, LA_ERR_INVALID, "la_assign_round: sequential batches cannot be split over shards");
-  if (batched && f.nbatch > 1)
-    return set_err(c, LA_ERR_INVALID, "la_assign_round: a forest of %d sequential batches needs LA_MODE_PLAIN",
-                   f.nbatch);
-  if (batched) {
+  if (batched && f.nbatch > 1) {
+    TRY(batched_caches(c, w, W, si, s));
+    BatchPlan& bp = c->plan;
+    if (!bp.tuned) {  // every net in level waves, caches on; nothing to tune
+      bp.k = kSizeClasses - 1;
+      bp.block = 256;
+      bp.grid = 1;
+      bp.cached = true;
+      bp.n_big = 0;
+      bp.Hs = f.nlev - 1;
+      bp.tail_h = 1 << 30;
+      bp.tail_T = 0;
+      bp.tuned = true;
+      bp.trials = 0;
+      bp.best_ms = 0.0;
+    }
+    // the batches' start layers: the previous assignment, or none after a reset
+    if (!f.layer_old) TRY(allocs_of(c)->forest.get(c, &f.layer_old, size_t(f.V)));
+    if (!p->reset && f.have_assign) CK(cudaMemcpyAsync(f.layer_old, f.layer, size_t(f.V), cudaMemcpyDeviceToDevice, s));
+    else CK(cudaMemsetAsync(f.layer_old, 0xFF, size_t(f.V), s));
+  } else if (batched) {
     TRY(batched_caches(c, w, W, si, s));
     if (!c->plan.tuned) TRY(autotune(c, w, W, rho, si, s));
     const int T = p->tail_threshold > 0 ? p->tail_threshold : c->memo.tail_T;

@@ -38,7 +38,6 @@ __host__ __device__ inline int node_class(bool root, int sons, bool has_pin) {
 }
 constexpr int kSizeClasses = 16;
 constexpr int kMinBigSc = 5;  // nets of 17+ nodes get per-net level lists
-constexpr int kElmSmall = 32; // the Elmore passes sweep nets of at most 32 nodes in input order
 __host__ __device__ inline int size_class(int64_t m) {
   int s = 0;
   while ((int64_t(1) << s) < m && s < kSizeClasses - 1) ++s;
@@ -157,7 +156,7 @@ struct Forest {
   double* Cc = nullptr;
   double* M = nullptr;
   double* B = nullptr;                  // look-ahead base fma(w_d r_est(parent), Cc, A)
-  double* ncache[2] = {nullptr, nullptr};  // batched form, per weight source: [V][4] per-node constants
+  double* ncache[2] = {nullptr, nullptr};  // batched form, per weight source: [V][2] per weight set, then [V][2] per round
   double* scache[2] = {nullptr, nullptr};  // and [V][LD][3] per (node, layer) constants
   int8_t* sb = nullptr;                 // [V][LD] chosen stack bottom
   int8_t* st = nullptr;                 // [V][LD] chosen stack top
@@ -168,10 +167,6 @@ struct Forest {
   int8_t* t = nullptr;
   int8_t* layer_old = nullptr;          // [V] the layers a multi-batch round starts from
   bool have_assign = false;
-  // Elmore passes of the nets of at most kElmSmall nodes, input order:
-  // ep = internal id | len << 32 | (pin + 1) << 48 | (local parent + 1) << 56, ecap = sink cap
-  uint64_t* ep = nullptr;               // [V]
-  double* ecap = nullptr;               // [V]
   // Elmore scratch (internal order)
   double* s0 = nullptr;                 // [V]
   double* s1 = nullptr;
@@ -358,8 +353,6 @@ int scan_blocks(const LayerInfo& li);
 // k_elmore.cu
 // R, C in internal order, or scattered to input order when perm != nullptr
 void launch_rc_from_assignment(la_ctx* c, double* R, double* C, const int32_t* perm, cudaStream_t s);
-// the input-order pack (ep, ecap) of `out` from the input-order forest `in`
-void launch_elm_pack(const Forest& in, const int32_t* in2int, Forest& out, cudaStream_t s);
 // delays from given R_seg, C_seg; every array in input order
 void launch_elmore_fwd(la_ctx* c, const double* R, const double* C, double* delay, cudaStream_t s);
 // the delays of the current assignment (R_seg, C_seg from its layers), input order

@@ -314,7 +314,7 @@ __global__ void __launch_bounds__(256) k_demand_delta(int64_t lo, int64_t hi, co
   const int ln = tab->ld_of[layer[v]];
   atomicAdd(diff + at + ln, 1);
   atomicAdd(diff + at + span + ln, -1);
-  if (layer_old) {
+  if (layer_old && layer_old[v] >= 0) {  // -1: the node had no layer before this round
     const int lold = tab->ld_of[layer_old[v]];
     atomicAdd(diff + at + lold, -1);
     atomicAdd(diff + at + span + lold, 1);
@@ -397,9 +397,11 @@ struct DPArgs {
   int8_t *sb, *st, *ent;
   double w_cong_s, w_cap, w_d, sigma0;
   unsigned long long* err;
-  // batched form only (else null): per node {w_d W, w_d kappa, w_d r_est, sigma}
-  // and per (node, layer) {alpha = w_d W R, gamma = fma(alpha, C/2, w_cap C), C}
+  // batched form only (else null): per node {w_d W, w_d kappa} (per weight
+  // set) and {w_d r_est, sigma} (per round), and per (node, layer)
+  // {alpha = w_d W R, gamma = fma(alpha, C/2, w_cap C), C}
   const double* ncache;
+  const double* nround;
   const double* scache;
 };
 
@@ -447,9 +449,9 @@ __device__ __forceinline__ void dp_node(const DPArgs& a, const DevTables& s, con
     l = s.lay[d][ldi];
   }
   const double* rvl = &s.rv[l * kMaxL];
-  const double* nc = CACHED ? a.ncache + 4 * int64_t(v) : nullptr;
-  const double wd_rho = CACHED ? nc[2] : a.w_d * a.rho[v];
-  const double sigma_v = CACHED ? nc[3] : fma(wd_rho, s.via_c, a.sigma0);
+  const double* nc = CACHED ? a.ncache + 2 * int64_t(v) : nullptr;
+  const double wd_rho = CACHED ? a.nround[2 * int64_t(v)] : a.w_d * a.rho[v];
+  const double sigma_v = CACHED ? a.nround[2 * int64_t(v) + 1] : fma(wd_rho, s.via_c, a.sigma0);
   double Cs = 0.0, sinkf = 0.0, z = 0.0;  // a node without a pin: all exactly 0
   if (PINK == 1 || (PINK == 2 && pin >= 0)) {
     Cs = a.sink_cap[v];
@@ -532,71 +534,8 @@ __device__ __forceinline__ void dp_node(const DPArgs& a, const DevTables& s, con
     a.ent[int64_t(c) * LD + ldi] = int8_t(lc);
     sg = fma(Mc[bj], rvl[lc], Ac[bj]);
     sc = Ccc[bj];
-  } else if (a.nch[v] == 2) {
-    // Two sons (most several-son nodes): every stack [b, t] with b <= lo_req
-    // <= hi_req <= t.  Each son's key for every layer of its direction is
-    // computed once per (node, l) and held by layer (LLONG_MAX at the other
-    // direction's layers); the tail costs T(k) = fma(k, sigma_v, z), k < L,
-    // once per thread in shared memory ([k][thread], conflict-free; keybuf's
-    // LMAX x 256 entries).  f'(b, t) = (key0 + key1) + T(t - b) with each
-    // son's least key in [b, t], the oracle's sum in son order.
-    const int c0 = a.child_list[cs], c1 = a.child_list[cs + 1];
-    const int d0 = geo_dir(a.geo[c0]), d1 = geo_dir(a.geo[c1]);
-    const double* B0 = a.B + int64_t(c0) * LD;
-    const double* M0 = a.M + int64_t(c0) * LD;
-    const double* B1 = a.B + int64_t(c1) * LD;
-    const double* M1 = a.M + int64_t(c1) * LD;
-    long long k0[LMAX], k1[LMAX];
-#pragma unroll
-    for (int t = 0; t < LMAX; ++t) {
-      k0[t] = LLONG_MAX;
-      k1[t] = LLONG_MAX;
-      if (t < L) {
-        const int jt = s.ld_of[t];
-        if (s.dir[t] == d0) k0[t] = dbits(fma(M0[jt], rvl[t], B0[jt]));
-        if (s.dir[t] == d1) k1[t] = dbits(fma(M1[jt], rvl[t], B1[jt]));
-      }
-    }
-    double* tl = reinterpret_cast<double*>(keybuf) + threadIdx.x;
-    for (int k = 0; k < L; ++k) tl[k * 256] = fma(s.kd[k], sigma_v, z);
-    int bk = INT_MAX;
-    for (int b = 0; b <= lo_req; ++b) {
-      long long r0 = LLONG_MAX, r1 = LLONG_MAX;
-#pragma unroll
-      for (int t = 0; t < LMAX; ++t) {
-        if (t < L && t >= b) {
-          r0 = min(r0, k0[t]);
-          r1 = min(r1, k1[t]);
-          if (t >= hi_req && r0 != LLONG_MAX && r1 != LLONG_MAX) {
-            const double S = __longlong_as_double(r0) + __longlong_as_double(r1);
-            const long long f = dbits(S + tl[(t - b) * 256]);
-            if (stack_better(f, t - b, b, bfp, bk, bb)) { bfp = f; bk = t - b; bb = b; bt = t; }
-          }
-        }
-      }
-    }
-    if (bfp == LLONG_MAX) {  // cannot happen for a valid forest; report it
-      dev_error(a.err, DE_NOSTACK, v);
-      return;
-    }
-    // each son's least key inside the winning stack (ascending layers: the
-    // lowest layer wins ties), and its g = fma(M, Rvia(l, lc), A)
-    long long m0 = LLONG_MAX, m1 = LLONG_MAX;
-    int l0 = -1, l1 = -1;
-#pragma unroll
-    for (int t = 0; t < LMAX; ++t) {
-      if (t >= bb && t <= bt) {
-        if (k0[t] < m0) { m0 = k0[t]; l0 = t; }
-        if (k1[t] < m1) { m1 = k1[t]; l1 = t; }
-      }
-    }
-    const int j0 = s.ld_of[l0], j1 = s.ld_of[l1];
-    a.ent[int64_t(c0) * LD + ldi] = int8_t(l0);
-    a.ent[int64_t(c1) * LD + ldi] = int8_t(l1);
-    sg = fma(M0[j0], rvl[l0], a.A[int64_t(c0) * LD + j0]) + fma(M1[j1], rvl[l1], a.A[int64_t(c1) * LD + j1]);
-    sc = a.Cc[int64_t(c0) * LD + j0] + a.Cc[int64_t(c1) * LD + j1];
   } else {
-    // Three or more sons: every stack [b, t] with b <= lo_req <= hi_req <= t;
+    // Two or more sons: every stack [b, t] with b <= lo_req <= hi_req <= t;
     // S[t] accumulates, son by son in order, the son's least key in [b, t].
     // A son's keys are computed on its own direction's layers only and put
     // in shared memory by layer, [t][thread] (conflict-free), for the scan
@@ -718,7 +657,7 @@ __device__ __forceinline__ void dp_node(const DPArgs& a, const DevTables& s, con
     a.Cc[o] = ccv;
     a.M[o] = wdW * ccv;
     const int p = a.parent_g[v];
-    a.B[o] = fma(CACHED ? a.ncache[4 * int64_t(p) + 2] : a.w_d * a.rho[p], ccv, Av);
+    a.B[o] = fma(CACHED ? a.nround[2 * int64_t(p)] : a.w_d * a.rho[p], ccv, Av);
   }
 }
 
@@ -752,7 +691,7 @@ __global__ void __launch_bounds__(256, (DEG == 1 && !ROOT && PINK == 0 ? 5 : (DE
       s_son[3][threadIdx.x] = a.Cc[o];
       so.B = &s_son[0][gi * LD]; so.M = &s_son[1][gi * LD]; so.A = &s_son[2][gi * LD]; so.Cc = &s_son[3][gi * LD];
       if constexpr (PINK == 0) {
-        const double sig = CACHED ? a.ncache[4 * int64_t(v) + 3] : fma(a.w_d * a.rho[v], li.via_c, a.sigma0);
+        const double sig = CACHED ? a.nround[2 * int64_t(v) + 1] : fma(a.w_d * a.rho[v], li.via_c, a.sigma0);
         double* T = &s_T[gi * li.L];
         for (int k2 = ldi; k2 < li.L; k2 += LD) T[k2] = fma(double(k2), sig, 0.0);
         so.T = T;
@@ -981,6 +920,7 @@ static DPArgs dp_args(la_ctx* c, const RoundW& w, const double* W, const double*
   a.base = 0;
   a.count = 0;
   a.ncache = nullptr;
+  a.nround = nullptr;
   a.scache = nullptr;
   return a;
 }
@@ -991,6 +931,7 @@ void launch_dp_level(la_ctx* c, const RoundW& w, const double* W, const double* 
   DPArgs a = dp_args(c, w, W, rho);
   if (cache >= 0) {
     a.ncache = f.ncache[cache];
+    a.nround = f.ncache[cache] + 2 * f.V;
     a.scache = f.scache[cache];
   }
   for (int cls = 0; cls < kClasses; ++cls) {
@@ -1092,6 +1033,7 @@ void launch_dp_tail(la_ctx* c, const RoundW& w, const double* W, const double* r
   const bool cached = cache >= 0;
   if (cached) {
     a.ncache = f.ncache[cache];
+    a.nround = f.ncache[cache] + 2 * f.V;
     a.scache = f.scache[cache];
   }
   const int64_t* ranges = f.range_tab + int64_t(k) * (f.Hmax + 1) * kClasses * 2;
@@ -1122,6 +1064,7 @@ void launch_dp_bignets(la_ctx* c, const RoundW& w, const double* W, const double
   const bool cached = cache >= 0;
   if (cached) {
     a.ncache = c->forest.ncache[cache];
+    a.nround = c->forest.ncache[cache] + 2 * c->forest.V;
     a.scache = c->forest.scache[cache];
   }
   const int L = c->grid.li.L, LD = c->LD;
@@ -1159,8 +1102,8 @@ __global__ void k_seg_consts(int64_t V, int LD, const DevTables* __restrict__ ta
   if (v >= V) return;
   const double wdW = w_d * W[v];
   if (ldi == 0) {
-    ncache[4 * v] = wdW;
-    ncache[4 * v + 1] = pin[v] >= 0 ? w_d * kappa[v] : 0.0;
+    ncache[2 * v] = wdW;
+    ncache[2 * v + 1] = pin[v] >= 0 ? w_d * kappa[v] : 0.0;
   }
   const uint64_t g = geo[v];
   const int d = geo_dir(g);
@@ -1179,12 +1122,12 @@ __global__ void k_seg_consts(int64_t V, int LD, const DevTables* __restrict__ ta
 
 // Batched form, every round: w_d r_est and sigma = fma(w_d r_est, vc, w_via + w_cap vc) per node.
 __global__ void k_node_round(int64_t V, const double* __restrict__ rho, double w_d, double via_c, double sigma0,
-                             double* __restrict__ ncache) {
+                             double* __restrict__ nround) {
   const int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (v >= V) return;
   const double wd_rho = w_d * rho[v];
-  ncache[4 * v + 2] = wd_rho;
-  ncache[4 * v + 3] = fma(wd_rho, via_c, sigma0);
+  nround[2 * v] = wd_rho;
+  nround[2 * v + 1] = fma(wd_rho, via_c, sigma0);
 }
 
 void launch_seg_consts(la_ctx* c, const RoundW& w, const double* W, int cache, cudaStream_t s) {
@@ -1199,7 +1142,8 @@ void launch_seg_consts(la_ctx* c, const RoundW& w, const double* W, int cache, c
 void launch_node_round(la_ctx* c, const RoundW& w, const double* rho, int cache, cudaStream_t s) {
   Forest& f = c->forest;
   k_node_round<<<(unsigned)((f.V + 255) / 256), 256, 0, s>>>(f.V, rho, w.w_d, c->grid.li.via_c,
-                                                             w.w_via + w.w_cap * c->grid.li.via_c, f.ncache[cache]);
+                                                             w.w_via + w.w_cap * c->grid.li.via_c,
+                                                             f.ncache[cache] + 2 * f.V);
   ++c->launches;
 }
 

@@ -424,39 +424,44 @@ def test_nangate45_stack_against_oracle(la):
             D, H = got["D"], got["H"]
 
 
-def test_sequential_batches_against_oracle(la):
+@pytest.mark.parametrize("mode", ["plain", "batched"])
+def test_sequential_batches_against_oracle(la, mode):
     """Sequential batches (Sec. III-A): batch k sees the demand of batches < k
     with their new layers and every other net with its previous ones.  Two
-    plain rounds against the oracle, batches from the Alg. 1 partition of the
-    nets' criticality; the batched form refuses several batches; the Elmore
-    passes walk every batch's levels."""
+    rounds against the oracle, plain and batched (level waves with the
+    constant caches in one CUDA graph), batches from the GPU's Alg. 1
+    partition of the nets' criticality, which must equal the oracle's; the
+    Elmore passes walk every batch's levels."""
     wl = fg.WORKLOADS[2].scaled(12000)
     grid, forest = fg.make_grid(wl, 13), fg.make_forest(wl, 13)
     N = int(forest["num_nets"])
     net_of = np.repeat(np.arange(N), np.diff(forest["net_ptr"]))
     crit = np.zeros(N)
     np.maximum.at(crit, net_of, forest["kappa"])
-    batch = la.batches_by_criticality(crit, critical_frac=0.6)
-    assert len(np.unique(batch)) >= 3
+    bt, nb = la.la_partition_batches(torch.from_numpy(crit).cuda(), critical_frac=0.6)
+    batch = bt.cpu().numpy()
+    ref_b, ref_nb = oracle.partition_batches(crit, None, critical_frac=0.6)
+    assert np.array_equal(batch, ref_b) and nb == ref_nb >= 3
+    m = la.LA_MODE_PLAIN if mode == "plain" else la.LA_MODE_BATCHED
     fb = dict(forest, batch=batch)
     a = _assigner(la, grid, fb)
     D = H = prev = None
     for r in range(2):
-        st = a.assign_round(mode=la.LA_MODE_PLAIN, reset=(r == 0), **la.DEFAULT_WEIGHTS)
-        got = dict(zip(("layer", "b", "t"), (x.cpu().numpy() for x in a.get_assignment())))
-        got["D"], got["H"] = (x.cpu().numpy() for x in a.get_state())
-        got["J"] = a.get_net_cost().cpu().numpy()
-        got["stats"] = st
+        st = a.assign_round(mode=m, reset=(r == 0), **la.DEFAULT_WEIGHTS)
+        got = _read_round(a, st)
         ref = oracle.assign_round_batches(grid, forest, batch, la.DEFAULT_WEIGHTS, D=D, H=H, layer_prev=prev)
-        assert_same_round(got, ref, f"round {r}")
+        assert_same_round(got, ref, f"{mode} round {r}")
         D, H, prev = got["D"], got["H"], got["layer"]
-    with pytest.raises(la.LaError) as e:
-        a.assign_round(mode=la.LA_MODE_BATCHED, **la.DEFAULT_WEIGHTS)
-    assert e.value.status == la.LA_ERR_INVALID
+    if mode == "batched":
+        assert st["batch_graph_captured"] == 0  # the second round replayed the first one's graph
+        with pytest.raises(la.LaError) as e:
+            a.assign_round(mode=m, local_demand=True, **la.DEFAULT_WEIGHTS)
+        assert e.value.status == la.LA_ERR_INVALID
     R, C = a.rc_from_assignment()
     d = a.elmore(R, C).cpu().numpy()
     ref_d = oracle.elmore(grid, forest, prev, got["b"], got["t"], R.cpu().numpy(), C.cpu().numpy())
     assert np.allclose(d, ref_d, rtol=1e-10, atol=0.0)
+    a.close()
 
 
 def _chains(n, depth, X, Y, seed):
@@ -749,3 +754,92 @@ def test_elmore_small_and_large_nets(la):
         Wr, rhor = oracle.adjoint_weights(grid, forest, layer, b, t)
         assert np.array_equal(W, Wr) and np.array_equal(rho, rhor)
     a.close()
+
+
+# ---------------------------------------------------------------------------
+# Net ordering and pin weights (Sec. III-A, Sec. III-C)
+# ---------------------------------------------------------------------------
+def test_logistic_pin_weight_against_oracle(la):
+    """The GPU's logistic pin weights equal the oracle's within a few units in
+    the last place (the two sides' exp() may round differently), exactly 1/2
+    at slack / WNS = b, and 0 off the pins."""
+    rng = np.random.default_rng(3)
+    V = 300_000
+    pin = np.where(rng.uniform(size=V) < 0.4, 0, -1).astype(np.int8)
+    slack = rng.uniform(-200.0, 60.0, V)
+    slack[:3] = [-60.0, -200.0, 0.0]  # x = b (WNS = -200), the worst slack, zero slack
+    pin[:3] = 0
+    wns = float(slack.min())
+    got = la.la_logistic_pin_weight(torch.from_numpy(pin).cuda(), torch.from_numpy(slack).cuda(), wns).cpu().numpy()
+    ref = oracle.logistic_pin_weight(pin, slack, wns)
+    np.testing.assert_allclose(got, ref, rtol=4 * 2.0 ** -52, atol=0)
+    assert got[0] == 0.5 and got[1] > 0.999 and np.all(got[pin < 0] == 0.0)
+    with pytest.raises(la.LaError):
+        la.la_logistic_pin_weight(torch.from_numpy(pin).cuda(), torch.from_numpy(slack).cuda(), 1.0)
+
+
+def test_partition_against_oracle(la):
+    """Alg. 1's partition on the GPU equals the oracle's net by net: random
+    criticalities and slacks at several ratios, the interval-edge nets of the
+    oracle's pin, and no slack at all; bad inputs are refused."""
+    rng = np.random.default_rng(8)
+    N = 500_000
+    crit = rng.uniform(0, 10, N) ** 3
+    slack = rng.uniform(-80, 30, N)
+    for frac, ratio, sl in ((0.5, 0.7, slack), (0.05, 0.9, slack), (0.3, 0.7, None), (1.0, 1.0, slack)):
+        g, nb = la.la_partition_batches(torch.from_numpy(crit).cuda(),
+                                        None if sl is None else torch.from_numpy(sl).cuda(), frac, ratio)
+        r, rnb = oracle.partition_batches(crit, sl, frac, ratio)
+        assert np.array_equal(g.cpu().numpy(), r) and nb == rnb, (frac, ratio)
+    ce = np.array([8, 4, 6, 2, 3.9999, 0.5, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 1.0])
+    se = np.array([-1, -1, -1, -1, -1, -100, -99, -99.5, -98.9, -96, -71, -69, 0.0, -100.0])
+    g, nb = la.la_partition_batches(torch.from_numpy(ce).cuda(), torch.from_numpy(se).cuda(), 0.25, 0.7)
+    r, rnb = oracle.partition_batches(ce, se, 0.25, 0.7)
+    assert np.array_equal(g.cpu().numpy(), r) and nb == rnb == 8
+    bad = crit.copy()
+    bad[7] = -1.0
+    with pytest.raises(la.LaError) as e:
+        la.la_partition_batches(torch.from_numpy(bad).cuda())
+    assert e.value.status == la.LA_ERR_INVALID
+
+
+def test_slack_driven_ordering_end_to_end(la):
+    """The paper's ordering on synthetic timing: per-pin slack from the
+    Elmore delays of a first round against a required time, the logistic pin
+    weights as the sinks' criticality (so Eq. 4 takes their maximum below
+    each node), the nets partitioned by their largest weight and their worst
+    slack, and two rounds in those sequential batches, batched, against the
+    oracle given the same weights and batches."""
+    wl = fg.WORKLOADS[2].scaled(20000)
+    grid, forest = fg.make_grid(wl, 31), fg.make_forest(wl, 31)
+    a = _assigner(la, grid, forest)
+    a.assign_round(reset=True, **la.DEFAULT_WEIGHTS)
+    delay = a.elmore_assignment().cpu().numpy()
+    pin = forest["pin_layer"]
+    sinks = pin >= 0
+    req = np.quantile(delay[sinks], 0.8)
+    slack = np.where(sinks, req - delay, 0.0)
+    wns = float(slack[sinks].min())
+    w = la.la_logistic_pin_weight(torch.from_numpy(pin).cuda(), torch.from_numpy(slack).cuda(), wns).cpu().numpy()
+    N = int(forest["num_nets"])
+    net_of = np.repeat(np.arange(N), np.diff(forest["net_ptr"]))
+    crit = np.zeros(N)
+    np.maximum.at(crit, net_of, w)
+    nslack = np.full(N, np.inf)
+    np.minimum.at(nslack, net_of[sinks], slack[sinks])
+    nslack[~np.isfinite(nslack)] = 0.0
+    bt, nb = la.la_partition_batches(torch.from_numpy(crit).cuda(), torch.from_numpy(nslack).cuda(), 0.9, 0.7)
+    batch = bt.cpu().numpy()
+    assert nb >= 3 and np.array_equal(batch, oracle.partition_batches(crit, nslack, 0.9, 0.7)[0])
+    f2 = dict(forest, kappa=w, batch=batch)
+    b = _assigner(la, grid, f2)
+    ref_in = dict(forest, kappa=w)
+    D = H = prev = None
+    for r in range(2):
+        st = b.assign_round(mode=la.LA_MODE_BATCHED, reset=(r == 0), **la.DEFAULT_WEIGHTS)
+        got = _read_round(b, st)
+        ref = oracle.assign_round_batches(grid, ref_in, batch, la.DEFAULT_WEIGHTS, D=D, H=H, layer_prev=prev)
+        assert_same_round(got, ref, f"round {r}")
+        D, H, prev = got["D"], got["H"], got["layer"]
+    a.close()
+    b.close()
