@@ -200,10 +200,28 @@ def dp_source_hash():
     return h.hexdigest()
 
 
-def dp_capture_record(workload_name):
-    """The committed ncu record of one round's DP phase (DRAM bytes, issued
-    FP64 warp instructions), if it was taken on the current kernel sources for
-    this workload; else (None, why)."""
+def node_class_counts(forest):
+    """Nodes per DP node class (the library's bucketing: class = min(sons, 2)
+    + 0 for a non-root node with a pin, 3 for a root, 6 for a node without a
+    pin), from the forest arrays."""
+    import numpy as np
+
+    par, ptr = forest["parent"], forest["net_ptr"]
+    V, N = int(forest["num_nodes"]), int(forest["num_nets"])
+    net_of = np.repeat(np.arange(N), np.diff(ptr))
+    root = par < 0
+    gp = np.where(root, -1, ptr[net_of] + par)
+    sons = np.bincount(gp[~root], minlength=V)
+    cls = np.minimum(sons, 2) + np.where(root, 3, np.where(forest["pin_layer"] >= 0, 0, 6))
+    return np.bincount(cls, minlength=9)
+
+
+def dp_capture_record(workload_name, forest=None):
+    """The committed ncu record of the DP kernels (DRAM bytes and issued FP64
+    warp instructions per node of each node class, captured launch by launch
+    on a scaled-down case of the same grid and net distribution) if it was
+    taken on the current kernel sources for this workload's shape, scaled to
+    one round of `forest` by its nodes per class; else (None, why)."""
     p = os.path.join(ROOT, "profiles", "dp_traffic.json")
     if not os.path.exists(p):
         return None, "no capture record"
@@ -213,7 +231,16 @@ def dp_capture_record(workload_name):
         return None, "capture record is for another workload"
     if rec.get("source_sha256") != dp_source_hash():
         return None, "kernels changed since the capture"
-    return rec, rec.get("how", "")
+    if forest is None:
+        return None, "no forest to scale to"
+    cnt = node_class_counts(forest)
+    bpn, ipn = rec["bytes_per_node"], rec["fp64_warp_inst_per_node"]
+    covered = sum(int(cnt[int(c)]) for c in bpn)
+    out = {"bytes_per_round": sum(float(bpn[c]) * int(cnt[int(c)]) for c in bpn),
+           "fp64_warp_inst_per_round": sum(float(ipn[c]) * int(cnt[int(c)]) for c in ipn),
+           "nodes_covered": covered, "nodes": int(forest["num_nodes"])}
+    return out, (f"{rec.get('how', '')}; scaled to this forest's nodes per class "
+                 f"({covered} of {int(forest['num_nodes'])} nodes in the captured classes)")
 
 
 def measured_peaks():
@@ -270,7 +297,7 @@ def rooflines(la, device, forest, wl, N, S, dp_ms, adj_ms, elm_ms):
     V = int(forest["num_nodes"])
     method = dp_method_bytes(S, L_d)
     caches = dp_cache_bytes(V, S, N, LD)
-    rec, traffic_src = dp_capture_record(wl.name)
+    rec, traffic_src = dp_capture_record(wl.name, forest)
     traffic = float(rec["bytes_per_round"]) if rec else None
     fp64_pipe = None
     if rec and rec.get("fp64_warp_inst_per_round"):

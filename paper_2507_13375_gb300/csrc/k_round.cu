@@ -405,6 +405,9 @@ struct DPArgs {
   const double* scache;
 };
 
+// Sons of a several-son node whose choices per stack top are recorded.
+constexpr int kRecSons = 4;
+
 // (fp, k, b) lexicographic order of Kernel 2 (least f', fewest vias, lowest b).
 __device__ __forceinline__ bool stack_better(long long f, int k, int b, long long bf, int bk, int bb) {
   return f < bf || (f == bf && (k < bk || (k == bk && b < bb)));
@@ -435,7 +438,8 @@ struct Son1 {
 };
 template <int LMAX, int LDM, int DEG, bool ROOT, bool CACHED, int PINK, bool STAGED = false>
 __device__ __forceinline__ void dp_node(const DPArgs& a, const DevTables& s, const RoundTabs& rt, int L, int v,
-                                        int ldi, const Son1& so = Son1{}, long long* keybuf = nullptr) {
+                                        int ldi, const Son1& so = Son1{}, long long* keybuf = nullptr,
+                                        int8_t* chbuf = nullptr) {
   static_assert(!STAGED || (DEG == 1 && !ROOT), "staged son rows are for one-son non-root nodes");
   const int LD = a.LD;
   const int pin = PINK == 0 ? -1 : a.pin[v];
@@ -539,9 +543,14 @@ __device__ __forceinline__ void dp_node(const DPArgs& a, const DevTables& s, con
     // S[t] accumulates, son by son in order, the son's least key in [b, t].
     // A son's keys are computed on its own direction's layers only and put
     // in shared memory by layer, [t][thread] (conflict-free), for the scan
-    // over t (keybuf: LMAX x 256 entries, from the kernel).
+    // over t (keybuf: LMAX x 256 entries, from the kernel).  With one stack
+    // bottom only (lo_req = 0: a pin on layer 0, or a root on it) and at most
+    // kRecSons sons, each son's least layer for every top t is recorded
+    // (chbuf: kRecSons x LMAX x 256 bytes) and read back for the winner.
     long long* keyL = keybuf + threadIdx.x;
     const int nc = a.nch[v];
+    int8_t* chL = chbuf ? chbuf + threadIdx.x : nullptr;
+    const bool rec = chL != nullptr && lo_req == 0 && nc <= kRecSons;
     int bk = INT_MAX;
     for (int b = 0; b <= lo_req; ++b) {
       double S[LMAX];
@@ -564,13 +573,19 @@ __device__ __forceinline__ void dp_node(const DPArgs& a, const DevTables& s, con
           }
         }
         long long rbits = LLONG_MAX;
+        int rlay = 0;
 #pragma unroll
         for (int lc = 0; lc < LMAX; ++lc) {
           if (lc < L && lc >= b) {
-            rbits = min(rbits, keyL[lc * 256]);
+            const long long kk = keyL[lc * 256];
+            if (kk < rbits) {  // ascending layers: the lowest layer keeps a tie
+              rbits = kk;
+              rlay = lc;
+            }
             if (lc >= hi_req) {
               if (rbits == LLONG_MAX) ok[lc] = false;
               else S[lc] = j == 0 ? __longlong_as_double(rbits) : S[lc] + __longlong_as_double(rbits);
+              if (rec) chL[(j * LMAX + lc) * 256] = int8_t(rlay);
             }
           }
         }
@@ -593,13 +608,17 @@ __device__ __forceinline__ void dp_node(const DPArgs& a, const DevTables& s, con
       const double* Mc = a.M + int64_t(c) * LD;
       long long rbits = LLONG_MAX;
       int rj = -1;
+      if (rec) {
+        rj = s.ld_of[chL[(j * LMAX + bt) * 256]];
+      } else {
 #pragma unroll
-      for (int jj = 0; jj < LDM; ++jj) {
-        if (jj < nldc) {
-          const int lc = s.lay[dc][jj];
-          if (lc >= bb && lc <= bt) {
-            const long long kb = dbits(fma(Mc[jj], rvl[lc], Bc[jj]));
-            if (rj < 0 || kb < rbits) { rj = jj; rbits = kb; }
+        for (int jj = 0; jj < LDM; ++jj) {
+          if (jj < nldc) {
+            const int lc = s.lay[dc][jj];
+            if (lc >= bb && lc <= bt) {
+              const long long kb = dbits(fma(Mc[jj], rvl[lc], Bc[jj]));
+              if (rj < 0 || kb < rbits) { rj = jj; rbits = kb; }
+            }
           }
         }
       }
@@ -707,7 +726,8 @@ __global__ void __launch_bounds__(256, (DEG == 1 && !ROOT && PINK == 0 ? 5 : (DE
     const int ldi = ROOT ? 0 : int(k - node_i * a.LD);
     if (node_i >= a.count) return;
     __shared__ long long s_keyL[DEG == 2 ? LMAX * 256 : 1];
-    dp_node<LMAX, LDM, DEG, ROOT, CACHED, PINK>(a, s, rt, li.L, int(a.base + node_i), ldi, Son1{}, s_keyL);
+    __shared__ int8_t s_ch[DEG == 2 ? kRecSons * LMAX * 256 : 1];
+    dp_node<LMAX, LDM, DEG, ROOT, CACHED, PINK>(a, s, rt, li.L, int(a.base + node_i), ldi, Son1{}, s_keyL, s_ch);
   }
 }
 

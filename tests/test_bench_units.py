@@ -49,3 +49,13 @@ def test_roofline_byte_rules():
     assert e == {"rc_nodes": 20, "forward": 800.0, "adjoint": 960.0}
     # the batched form's own count (its constant caches included) is larger
     assert bench.dp_cache_bytes(V=7, S=6, N=1, LD=6) > bench.dp_method_bytes(6, 6.0)
+
+
+def test_node_class_counts():
+    """The DP's node classes of the hand-made net: the root (a pin, one son)
+    is class 4, the bend (no pin, one son) class 7, the sink (a pin, no son)
+    class 0; a second net doubles every count."""
+    f = _forest([_net(0), _net(20)])
+    f["pin_layer"] = f["pin_layer"].astype(np.int8)
+    c = bench.node_class_counts(f)
+    assert list(c) == [2, 0, 0, 0, 2, 0, 0, 2, 0]
