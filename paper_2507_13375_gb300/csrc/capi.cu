@@ -256,6 +256,9 @@ la_status la_create(la_ctx** out, int device, void* stream) {
   for (auto& e2 : c->ev) ok = ok && cudaEventCreate(&e2) == cudaSuccess;
   ok = ok && cudaStreamCreateWithFlags(&c->s2, cudaStreamNonBlocking) == cudaSuccess &&
        cudaStreamCreateWithFlags(&c->s_cap, cudaStreamNonBlocking) == cudaSuccess &&
+       cudaStreamCreateWithFlags(&c->s3, cudaStreamNonBlocking) == cudaSuccess &&
+       cudaEventCreateWithFlags(&c->ev_lfork, cudaEventDisableTiming) == cudaSuccess &&
+       cudaEventCreateWithFlags(&c->ev_ljoin, cudaEventDisableTiming) == cudaSuccess &&
        cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) == cudaSuccess;
   if (!ok) {
@@ -288,6 +291,9 @@ la_status la_destroy(la_ctx* c) {
   if (c->ev_join) cudaEventDestroy(c->ev_join);
   if (c->s2) cudaStreamDestroy(c->s2);
   if (c->s_cap) cudaStreamDestroy(c->s_cap);
+  if (c->s3) cudaStreamDestroy(c->s3);
+  if (c->ev_lfork) cudaEventDestroy(c->ev_lfork);
+  if (c->ev_ljoin) cudaEventDestroy(c->ev_ljoin);
   delete c;
   return LA_OK;
 }
@@ -790,7 +796,26 @@ static la_status enqueue_batched(la_ctx* c, const BatchPlan& bp, const RoundW& w
   }
   const bool tail = bp.tail_h <= bp.Hs;
   const int hw = tail ? bp.tail_h - 1 : bp.Hs;  // the last level-wave level
-  for (int h = 0; h <= hw; ++h) launch_dp_level(c, w, W, rho, h, bp.k, cache, s);
+  // A level's classes are independent: the several-son, root and no-pin
+  // classes (latency-bound, small) run on a side branch beside the leaves,
+  // one-son and bend classes (FP64-bound, large), joined before the next level.
+  constexpr unsigned kSide = (1u << 2) | (1u << 3) | (1u << 4) | (1u << 5) | (1u << 6) | (1u << 8);
+  for (int h = 0; h <= hw; ++h) {
+    bool side = false;
+    for (int cls = 0; cls < kClasses && !side; ++cls)
+      side = ((kSide >> cls) & 1u) &&
+             f.key_off[size_t(bucket_key(h, cls, bp.k + 1))] > f.key_off[size_t(bucket_key(h, cls, 0))];
+    if (!side) {
+      launch_dp_level(c, w, W, rho, h, bp.k, cache, s);
+      continue;
+    }
+    CK(cudaEventRecord(c->ev_lfork, s));
+    CK(cudaStreamWaitEvent(c->s3, c->ev_lfork, 0));
+    launch_dp_level(c, w, W, rho, h, bp.k, cache, c->s3, kSide);
+    launch_dp_level(c, w, W, rho, h, bp.k, cache, s, kAllClasses & ~kSide);
+    CK(cudaEventRecord(c->ev_ljoin, c->s3));
+    CK(cudaStreamWaitEvent(s, c->ev_ljoin, 0));
+  }
   if (tail) {
     launch_dp_tail(c, w, W, rho, bp.tail_h, bp.Hs, bp.k, cache, s);
     launch_backtrack_tail(c, bp.tail_h, bp.Hs, bp.k, s);
@@ -1062,7 +1087,6 @@ la_status la_assign_round(la_ctx* c, const la_round_params* p, la_round_stats* s
     CK(cudaMemsetAsync(gr.diff, 0, gr.G * 4, s));
     gr.P_valid = false;
   }
-  CK(cudaMemsetAsync(c->d_stats, 0, sizeof(Stats), s));
   TRY(reset_dev_err(c));
   const long long launches0 = c->launches;
   double* tof_part = f.red;
@@ -1099,6 +1123,8 @@ la_status la_assign_round(la_ctx* c, const la_round_params* p, la_round_stats* s
     const int k = p->force_split > 0 ? p->force_split : c->memo.k;
     if (T != c->plan.tail_T || k != c->plan.k) set_shape(c, k, T);
   }
+  // the statistics count this round only (not the tuner's trial rounds)
+  CK(cudaMemsetAsync(c->d_stats, 0, sizeof(Stats), s));
   bool captured = false;
   CK(cudaEventRecord(c->ev[0], s));
   if (batched) {

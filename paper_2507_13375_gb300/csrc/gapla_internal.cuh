@@ -266,6 +266,8 @@ struct la_ctx {
   int LD = 0;
   long long launches = 0;               // kernels launched (host-side count)
   cudaStream_t s2 = nullptr;            // second stream (big-net bucket)
+  cudaStream_t s3 = nullptr;            // third stream (a level's several-son, root and no-pin classes)
+  cudaEvent_t ev_lfork = nullptr, ev_ljoin = nullptr;
   cudaStream_t s_cap = nullptr;         // stream the batched round is captured on
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   gapla::BatchPlan plan;
@@ -332,8 +334,10 @@ void launch_local_demand(la_ctx* c, double hist_w, double* red_tof, cudaStream_t
 // cache: the batched form's constant-cache set to read (0 Eq. 4, 1 adjoint), or
 // kNoCache to recompute the constants in the DP (the plain form)
 constexpr int kNoCache = -1;
+// class_mask: the node classes to launch (bit cls)
+constexpr unsigned kAllClasses = (1u << kClasses) - 1u;
 void launch_dp_level(la_ctx* c, const RoundW& w, const double* W, const double* rho, int level, int kmax,
-                     int cache, cudaStream_t s);
+                     int cache, cudaStream_t s, unsigned class_mask = kAllClasses);
 void launch_backtrack_level(la_ctx* c, int level, int kmax, cudaStream_t s);
 // the first n_big nets of the big-net queue, persistent grid
 void launch_dp_bignets(la_ctx* c, const RoundW& w, const double* W, const double* rho, int64_t n_big, int grid,

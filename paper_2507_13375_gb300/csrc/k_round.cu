@@ -329,33 +329,12 @@ void launch_demand_delta(la_ctx* c, int64_t lo, int64_t hi, const int8_t* layer_
   ++c->launches;
 }
 
-// Vias: the sum over nodes of t - b (warp, then block, then one atomic).
-__global__ void __launch_bounds__(256) k_vias(int64_t V, const int8_t* __restrict__ b, const int8_t* __restrict__ t,
-                                              Stats* stats) {
-  __shared__ unsigned s_v[8];
-  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  unsigned x = 0;
-  if (i < V) x = unsigned(__ldcs(reinterpret_cast<const signed char*>(t) + i) -
-                          __ldcs(reinterpret_cast<const signed char*>(b) + i));
-  x = __reduce_add_sync(0xffffffffu, x);
-  if ((threadIdx.x & 31) == 0) s_v[threadIdx.x >> 5] = x;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned long long sv = 0;
-    for (int w = 0; w < int(blockDim.x >> 5); ++w) sv += s_v[w];
-    if (sv) atomicAdd(&stats->vias, sv);
-  }
-}
-
 // After the backtrack: demand, D, H += max(0, D - C), the statistics and the
 // next penalty prefix.  Fused into the line scan when a line fits in shared
 // memory; otherwise global atomics into the difference array, then the scan.
 void launch_demand_scan(la_ctx* c, double hist_w, double* tof_part, cudaStream_t s) {
   Grid& g = c->grid;
-  Forest& f = c->forest;
   if (g.fused_scan) {
-    k_vias<<<(unsigned)((f.V + 255) / 256), 256, 0, s>>>(f.V, f.b, f.t, c->d_stats);
-    ++c->launches;
     scan_launch<true>(c, scan_args(c, 1, hist_w, tof_part), fused_line_bytes(g.li), s);
   } else {
     launch_demand(c, s);
@@ -435,7 +414,50 @@ struct Son1 {
   int c, dc;
   const double *B, *M, *A, *Cc;
   const double* T;  // no pin: the node's tail costs T(k) = fma(k, sigma_v, 0.0), k < L
+  long long* K;     // the thread's son keys by son layer index, stride 256 (shared memory)
 };
+// One son of a several-son node in the scan of the stacks with bottom b: its
+// keys on its own direction's layers go to keyL by layer ([t][thread], the
+// other layers hold LLONG_MAX), then for every top t = hi_req + i (i < nt) its
+// least key in [b, t] is added to S[i] (FIRST: the first son sets S[i]) and
+// its layer recorded in chj[t] (chj non-null).  Ascending layers: the lowest
+// layer keeps a tie.  The loop over tops ends at the last one, so threads
+// with the same hi_req run it the same number of times.
+template <int LMAX, int LDM, bool FIRST>
+__device__ __forceinline__ void son_scan(const DPArgs& a, const DevTables& s, const double* rvl, int c, int b,
+                                         int hi_req, int nt, long long* keyL, int8_t* chj, double (&S)[LMAX],
+                                         unsigned& okm) {
+  const int dc = geo_dir(a.geo[c]);
+  const int nldc = s.nld[dc];
+  const double* Bc = a.B + int64_t(c) * a.LD;
+  const double* Mc = a.M + int64_t(c) * a.LD;
+#pragma unroll
+  for (int t = 0; t < LMAX; ++t) keyL[t * 256] = LLONG_MAX;
+#pragma unroll
+  for (int jj = 0; jj < LDM; ++jj) {
+    if (jj < nldc) {
+      const int lc = s.lay[dc][jj];
+      keyL[lc * 256] = dbits(fma(Mc[jj], rvl[lc], Bc[jj]));
+    }
+  }
+  long long rbits = LLONG_MAX;
+  int rlay = 0;
+  for (int lc = b; lc < hi_req; ++lc) {
+    const long long kk = keyL[lc * 256];
+    if (kk < rbits) { rbits = kk; rlay = lc; }
+  }
+#pragma unroll
+  for (int i = 0; i < LMAX; ++i) {
+    if (i >= nt) break;
+    const int t = hi_req + i;
+    const long long kk = keyL[t * 256];
+    if (kk < rbits) { rbits = kk; rlay = t; }
+    if (rbits == LLONG_MAX) okm &= ~(1u << i);
+    else S[i] = FIRST ? __longlong_as_double(rbits) : S[i] + __longlong_as_double(rbits);
+    if (chj) chj[t * 256] = int8_t(rlay);
+  }
+}
+
 template <int LMAX, int LDM, int DEG, bool ROOT, bool CACHED, int PINK, bool STAGED = false>
 __device__ __forceinline__ void dp_node(const DPArgs& a, const DevTables& s, const RoundTabs& rt, int L, int v,
                                         int ldi, const Son1& so = Son1{}, long long* keybuf = nullptr,
@@ -494,40 +516,59 @@ __device__ __forceinline__ void dp_node(const DPArgs& a, const DevTables& s, con
     }
     const int nldc = s.nld[dc];
     long long key[LDM];
-    int lcs[LDM];
+    int p = 0, q = 0;  // son layer indices [p, q) lie in [lo_req, hi_req]
 #pragma unroll
     for (int j = 0; j < LDM; ++j) {
-      lcs[j] = s.lay[dc][j];
-      if (j < nldc) key[j] = dbits(fma(Mc[j], rvl[lcs[j]], Bc[j]));
+      if (j < nldc) {
+        const int lc = s.lay[dc][j];
+        p += lc < lo_req;
+        q += lc <= hi_req;
+        key[j] = dbits(fma(Mc[j], rvl[lc], Bc[j]));
+        if constexpr (STAGED && PINK == 0) so.K[j * 256] = key[j];
+      }
     }
     long long inmin = LLONG_MAX;
     int m = -1;
 #pragma unroll
     for (int j = 0; j < LDM; ++j)
-      if (j < nldc && lcs[j] >= lo_req && lcs[j] <= hi_req && key[j] < inmin) { inmin = key[j]; m = j; }
+      if (j >= p && j < q && key[j] < inmin) { inmin = key[j]; m = j; }
     unsigned cons = m >= 0 ? 1u << m : 0u;
     long long run = inmin;
 #pragma unroll
     for (int j = LDM - 1; j >= 0; --j)
-      if (j < nldc && lcs[j] < lo_req) {
+      if (j < p) {
         if (key[j] <= run) cons |= 1u << j;
         run = min(run, key[j]);
       }
     run = inmin;
 #pragma unroll
     for (int j = 0; j < LDM; ++j)
-      if (j < nldc && lcs[j] > hi_req) {
+      if (j >= q && j < nldc) {
         if (key[j] < run) cons |= 1u << j;
         run = min(run, key[j]);
       }
     int bj = 0, bk = INT_MAX;
-#pragma unroll
-    for (int j = 0; j < LDM; ++j) {
-      if ((cons >> j) & 1u) {
-        const int b0 = min(lo_req, lcs[j]), t0 = max(hi_req, lcs[j]);
-        const double tail = (STAGED && PINK == 0) ? so.T[t0 - b0] : fma(s.kd[t0 - b0], sigma_v, z);
-        const long long f = dbits(__longlong_as_double(key[j]) + tail);
+    if constexpr (STAGED && PINK == 0) {
+      // the consistent candidates only, lowest index first (a warp issues the
+      // most any of its threads has, not the union of theirs; the tail costs
+      // come from the node's table)
+      for (unsigned mm = cons; mm; mm &= mm - 1u) {
+        const int j = __ffs(mm) - 1;
+        const int lcj = s.lay[dc][j];
+        const int b0 = min(lo_req, lcj), t0 = max(hi_req, lcj);
+        const long long f = dbits(__longlong_as_double(so.K[j * 256]) + so.T[t0 - b0]);
         if (stack_better(f, t0 - b0, b0, bfp, bk, bb)) { bfp = f; bk = t0 - b0; bb = b0; bt = t0; bj = j; }
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < LDM; ++j) {
+        if ((cons >> j) & 1u) {
+          const int lcj = s.lay[dc][j];
+          const int b0 = min(lo_req, lcj), t0 = max(hi_req, lcj);
+          const double tail = (STAGED && PINK == 0) ? so.T[t0 - b0] : fma(s.kd[t0 - b0], sigma_v, z);
+          const long long f = dbits(__longlong_as_double(key[j]) + tail);
+          if (stack_better(f, t0 - b0, b0, bfp, bk, bb)) { bfp = f; bk = t0 - b0; bb = b0; bt = t0; bj = j; }
+        }
       }
     }
     if (bfp == LLONG_MAX) {  // cannot happen (the least key overall is consistent); report it
@@ -551,49 +592,23 @@ __device__ __forceinline__ void dp_node(const DPArgs& a, const DevTables& s, con
     const int nc = a.nch[v];
     int8_t* chL = chbuf ? chbuf + threadIdx.x : nullptr;
     const bool rec = chL != nullptr && lo_req == 0 && nc <= kRecSons;
+    const int nt = L - hi_req;  // stack tops hi_req + i, i < nt
     int bk = INT_MAX;
     for (int b = 0; b <= lo_req; ++b) {
       double S[LMAX];
-      bool ok[LMAX];
+      unsigned okm = ~0u;  // bit i: every son has a layer in [b, hi_req + i]
 #pragma unroll
-      for (int t = 0; t < LMAX; ++t) { S[t] = 0.0; ok[t] = true; }
-      for (int j = 0; j < nc; ++j) {
-        const int c = a.child_list[cs + j];
-        const int dc = geo_dir(a.geo[c]);
-        const int nldc = s.nld[dc];
-        const double* Bc = a.B + int64_t(c) * LD;
-        const double* Mc = a.M + int64_t(c) * LD;
+      for (int i = 0; i < LMAX; ++i) S[i] = 0.0;
+      son_scan<LMAX, LDM, true>(a, s, rvl, a.child_list[cs], b, hi_req, nt, keyL, rec ? chL : nullptr, S, okm);
+      for (int j = 1; j < nc; ++j)
+        son_scan<LMAX, LDM, false>(a, s, rvl, a.child_list[cs + j], b, hi_req, nt, keyL,
+                                   rec ? chL + j * LMAX * 256 : nullptr, S, okm);
 #pragma unroll
-        for (int t = 0; t < LMAX; ++t) keyL[t * 256] = LLONG_MAX;
-#pragma unroll
-        for (int jj = 0; jj < LDM; ++jj) {
-          if (jj < nldc) {
-            const int lc = s.lay[dc][jj];
-            keyL[lc * 256] = dbits(fma(Mc[jj], rvl[lc], Bc[jj]));
-          }
-        }
-        long long rbits = LLONG_MAX;
-        int rlay = 0;
-#pragma unroll
-        for (int lc = 0; lc < LMAX; ++lc) {
-          if (lc < L && lc >= b) {
-            const long long kk = keyL[lc * 256];
-            if (kk < rbits) {  // ascending layers: the lowest layer keeps a tie
-              rbits = kk;
-              rlay = lc;
-            }
-            if (lc >= hi_req) {
-              if (rbits == LLONG_MAX) ok[lc] = false;
-              else S[lc] = j == 0 ? __longlong_as_double(rbits) : S[lc] + __longlong_as_double(rbits);
-              if (rec) chL[(j * LMAX + lc) * 256] = int8_t(rlay);
-            }
-          }
-        }
-      }
-#pragma unroll
-      for (int t = 0; t < LMAX; ++t) {
-        if (t < L && t >= hi_req && ok[t]) {
-          const long long f = dbits(S[t] + fma(s.kd[t - b], sigma_v, z));
+      for (int i = 0; i < LMAX; ++i) {
+        if (i >= nt) break;
+        if ((okm >> i) & 1u) {
+          const int t = hi_req + i;
+          const long long f = dbits(S[i] + fma(s.kd[t - b], sigma_v, z));
           if (stack_better(f, t - b, b, bfp, bk, bb)) { bfp = f; bk = t - b; bb = b; bt = t; }
         }
       }
@@ -694,12 +709,14 @@ __global__ void __launch_bounds__(256, (DEG == 1 && !ROOT && PINK == 0 ? 5 : (DE
     // (a node without a pin also tabulates its tail costs T(k), k < L, once)
     __shared__ double s_son[4][256];
     __shared__ double s_T[PINK == 0 ? 512 : 1];  // (256 / LD) nodes x L <= 512 since LD >= L / 2
+    __shared__ long long s_key[PINK == 0 ? LDM : 1][256];
     const int LD = a.LD, npb = 256 / LD;
     const int gi = int(threadIdx.x) / LD, ldi = int(threadIdx.x) - gi * LD;
     const int64_t node_i = int64_t(blockIdx.x) * npb + gi;
     const bool in = gi < npb && node_i < a.count;
     const int v = int(a.base + (in ? node_i : 0));
     Son1 so{};
+    so.K = &s_key[0][threadIdx.x];
     if (in) {
       so.c = a.child_list[a.child_start[v]];
       so.dc = geo_dir(a.geo[so.c]);
@@ -712,13 +729,23 @@ __global__ void __launch_bounds__(256, (DEG == 1 && !ROOT && PINK == 0 ? 5 : (DE
       if constexpr (PINK == 0) {
         const double sig = CACHED ? a.nround[2 * int64_t(v) + 1] : fma(a.w_d * a.rho[v], li.via_c, a.sigma0);
         double* T = &s_T[gi * li.L];
-        for (int k2 = ldi; k2 < li.L; k2 += LD) T[k2] = fma(double(k2), sig, 0.0);
+        for (int k2 = ldi; k2 < li.L; k2 += LD) T[k2] = fma(s.kd[k2], sig, 0.0);
         so.T = T;
       }
     }
     __syncthreads();
     if (!in) return;
     dp_node<LMAX, LDM, DEG, ROOT, CACHED, PINK, true>(a, s, rt, li.L, v, ldi, so);
+  } else if constexpr (DEG == 2 && !ROOT && LDM <= 8) {
+    // 32 nodes per block of 32 x LD threads, warp w evaluating candidate
+    // index w of each: a warp's threads share l, so the scans over the stack
+    // tops above it have one length per warp
+    const int ldi = int(threadIdx.x >> 5);
+    const int64_t node_i = int64_t(blockIdx.x) * 32 + (threadIdx.x & 31);
+    if (node_i >= a.count) return;
+    __shared__ long long s_keyL[LMAX * 256];
+    __shared__ int8_t s_ch[kRecSons * LMAX * 256];
+    dp_node<LMAX, LDM, DEG, ROOT, CACHED, PINK>(a, s, rt, li.L, int(a.base + node_i), ldi, Son1{}, s_keyL, s_ch);
   } else {
     // a node's candidate layers side by side (they share its sons' rows)
     const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -749,9 +776,11 @@ __device__ void dp_node_any(const DPArgs& a, const DevTables& s, const RoundTabs
   }
 }
 
-__device__ __forceinline__ void backtrack_node(int v, int LD, const int8_t* ld_of, const int32_t* parent_g,
-                                               const int8_t* pin, const int8_t* ent, const int8_t* sb,
-                                               const int8_t* st, int8_t* layer, int8_t* b, int8_t* t) {
+// Alg. 4 at node v: its layer from its parent's choice, its stack; returns
+// the stack's via count t - b (the round's via statistic).
+__device__ __forceinline__ int backtrack_node(int v, int LD, const int8_t* ld_of, const int32_t* parent_g,
+                                              const int8_t* pin, const int8_t* ent, const int8_t* sb,
+                                              const int8_t* st, int8_t* layer, int8_t* b, int8_t* t) {
   const int gp = parent_g[v];
   int l, idx;
   if (gp < 0) {
@@ -764,8 +793,25 @@ __device__ __forceinline__ void backtrack_node(int v, int LD, const int8_t* ld_o
     idx = ld_of[l];
   }
   layer[v] = int8_t(l);
-  b[v] = sb[int64_t(v) * LD + idx];
-  t[v] = st[int64_t(v) * LD + idx];
+  const int bv = sb[int64_t(v) * LD + idx], tv = st[int64_t(v) * LD + idx];
+  b[v] = int8_t(bv);
+  t[v] = int8_t(tv);
+  return tv - bv;
+}
+
+// The block's via counts into the round's statistics: warp sums, then one
+// atomic per block (every thread of the block calls it; blockDim a multiple
+// of 32, at most 1024).
+__device__ __forceinline__ void add_vias(Stats* stats, unsigned vias) {
+  __shared__ unsigned s_w[32];
+  const unsigned w = __reduce_add_sync(0xffffffffu, vias);
+  if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = w;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long sum = 0;
+    for (int i = 0; i < int(blockDim.x >> 5); ++i) sum += s_w[i];
+    if (sum) atomicAdd(&stats->vias, sum);
+  }
 }
 
 // Large nets (batched form): a persistent grid takes nets from a work queue
@@ -851,12 +897,14 @@ struct BtArgs {
   const int32_t* parent_g;
   const int8_t *pin, *ent, *sb, *st;
   int8_t *layer, *b, *t;
+  Stats* stats;
 };
 
 __global__ void __launch_bounds__(256) k_backtrack_bignets(BtArgs a, BigArgs g) {
   __shared__ int s_q;
   __shared__ int8_t s_ld[kMaxL];
   if (threadIdx.x < kMaxL) s_ld[threadIdx.x] = a.tab->ld_of[threadIdx.x];
+  unsigned vias = 0;
   for (;;) {
     if (threadIdx.x == 0) s_q = atomicAdd(g.ctr, 1);
     __syncthreads();
@@ -869,20 +917,24 @@ __global__ void __launch_bounds__(256) k_backtrack_bignets(BtArgs a, BigArgs g) 
     for (int h = g.net_H[n]; h >= 0; --h) {
       const int lo = ho[h], cnt = ho[h + 1] - lo;
       for (int t = threadIdx.x; t < cnt; t += blockDim.x)
-        backtrack_node(g.bl_nodes[base + lo + t], a.LD, s_ld, a.parent_g, a.pin, a.ent, a.sb, a.st, a.layer, a.b,
-                       a.t);
+        vias += backtrack_node(g.bl_nodes[base + lo + t], a.LD, s_ld, a.parent_g, a.pin, a.ent, a.sb, a.st, a.layer,
+                               a.b, a.t);
       __syncthreads();
     }
   }
+  add_vias(a.stats, vias);
 }
 
 template <int LMAX, int LDM, int DEG, bool ROOT, int PINK>
 static void dp_launch(la_ctx* c, const DPArgs& a, cudaStream_t s) {
-  const int T = 256;
+  int T = 256;
   unsigned B;
   if (DEG == 1 && !ROOT) {
     const int64_t npb = T / a.LD;  // whole nodes per block
     B = (unsigned)((a.count + npb - 1) / npb);
+  } else if (DEG == 2 && !ROOT && LDM <= 8) {  // 32 nodes per block, a warp per candidate index
+    T = 32 * a.LD;
+    B = (unsigned)((a.count + 31) / 32);
   } else {
     const int64_t threads = ROOT ? a.count : a.count * a.LD;
     B = (unsigned)((threads + T - 1) / T);
@@ -946,7 +998,7 @@ static DPArgs dp_args(la_ctx* c, const RoundW& w, const double* W, const double*
 }
 
 void launch_dp_level(la_ctx* c, const RoundW& w, const double* W, const double* rho, int level, int kmax,
-                     int cache, cudaStream_t s) {
+                     int cache, cudaStream_t s, unsigned class_mask) {
   Forest& f = c->forest;
   DPArgs a = dp_args(c, w, W, rho);
   if (cache >= 0) {
@@ -955,6 +1007,7 @@ void launch_dp_level(la_ctx* c, const RoundW& w, const double* W, const double* 
     a.scache = f.scache[cache];
   }
   for (int cls = 0; cls < kClasses; ++cls) {
+    if (!((class_mask >> cls) & 1u)) continue;
     const int64_t lo = f.key_off[size_t(bucket_key(level, cls, 0))];
     const int64_t hi = f.key_off[size_t(bucket_key(level, cls, kmax + 1))];
     const int64_t n = hi - lo;
@@ -980,10 +1033,13 @@ __global__ void __launch_bounds__(256) k_backtrack_level(Ranges r, BtArgs a) {
   if (threadIdx.x < kMaxL) s_ld[threadIdx.x] = a.tab->ld_of[threadIdx.x];
   __syncthreads();
   int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (j >= r.total) return;
-  int k = 0;
-  while (k < kClasses - 1 && j >= r.cnt[k]) j -= r.cnt[k++];
-  backtrack_node(int(r.lo[k] + j), a.LD, s_ld, a.parent_g, a.pin, a.ent, a.sb, a.st, a.layer, a.b, a.t);
+  unsigned vias = 0;
+  if (j < r.total) {
+    int k = 0;
+    while (k < kClasses - 1 && j >= r.cnt[k]) j -= r.cnt[k++];
+    vias = backtrack_node(int(r.lo[k] + j), a.LD, s_ld, a.parent_g, a.pin, a.ent, a.sb, a.st, a.layer, a.b, a.t);
+  }
+  add_vias(a.stats, vias);
 }
 
 __global__ void __launch_bounds__(256) k_backtrack_tail(BtArgs a, const int64_t* __restrict__ ranges, int h0,
@@ -991,6 +1047,7 @@ __global__ void __launch_bounds__(256) k_backtrack_tail(BtArgs a, const int64_t*
   __shared__ int8_t s_ld[kMaxL];
   __shared__ int64_t s_lo[kClasses], s_n[kClasses];
   if (threadIdx.x < kMaxL) s_ld[threadIdx.x] = a.tab->ld_of[threadIdx.x];
+  unsigned vias = 0;
   for (int h = h1; h >= h0; --h) {
     if (threadIdx.x < kClasses) {
       s_lo[threadIdx.x] = ranges[(int64_t(h) * kClasses + threadIdx.x) * 2];
@@ -1004,15 +1061,17 @@ __global__ void __launch_bounds__(256) k_backtrack_tail(BtArgs a, const int64_t*
       int64_t r = t;
       int cls = 0;
       while (cls < kClasses - 1 && r >= s_n[cls]) r -= s_n[cls++];
-      backtrack_node(int(s_lo[cls] + r), a.LD, s_ld, a.parent_g, a.pin, a.ent, a.sb, a.st, a.layer, a.b, a.t);
+      vias += backtrack_node(int(s_lo[cls] + r), a.LD, s_ld, a.parent_g, a.pin, a.ent, a.sb, a.st, a.layer, a.b,
+                             a.t);
     }
     __syncthreads();
   }
+  add_vias(a.stats, vias);
 }
 
 static BtArgs bt_args(la_ctx* c) {
   Forest& f = c->forest;
-  return BtArgs{c->LD, c->grid.tab_dev, f.parent_g, f.pin, f.ent, f.sb, f.st, f.layer, f.b, f.t};
+  return BtArgs{c->LD, c->grid.tab_dev, f.parent_g, f.pin, f.ent, f.sb, f.st, f.layer, f.b, f.t, c->d_stats};
 }
 
 void launch_backtrack_level(la_ctx* c, int level, int kmax, cudaStream_t s) {
@@ -1180,21 +1239,19 @@ int bignet_blocks_per_sm(int L, int LD, int block) {
 // ---------------------------------------------------------------------------
 // Demand: +1 at the segment's first edge and -1 past its last edge in the
 // difference array of its line and layer (the line scan folds it into D),
-// plus vias and wirelength per layer.  Integer atomics: exact in any order.
+// plus wirelength per layer (the vias are counted by the backtrack).  Integer
+// atomics: exact in any order.
 // ---------------------------------------------------------------------------
-// Thread i: the vias of node i (t - b), and the i-th segment in (direction,
-// line) order: +1 at its first edge and -1 past its last edge, in the
-// difference array of its line and layer.  A warp's segments lie on one or
-// two lines, so its atomics land in a few L2 sectors.  The node data is read
-// with streaming loads (each byte once).
-__global__ void __launch_bounds__(256) k_demand(int64_t V, int64_t S, int L, const DevTables* __restrict__ tab,
+// Thread i: the i-th segment in (direction, line) order: +1 at its first edge
+// and -1 past its last edge, in the difference array of its line and layer.
+// A warp's segments lie on one or two lines, so its atomics land in a few L2
+// sectors.  The segment data is read with streaming loads (each byte once).
+__global__ void __launch_bounds__(256) k_demand(int64_t S, int L, const DevTables* __restrict__ tab,
                                                 const int32_t* __restrict__ seg_node,
                                                 const uint64_t* __restrict__ seg_geo,
-                                                const int8_t* __restrict__ layer, const int8_t* __restrict__ b,
-                                                const int8_t* __restrict__ t, int32_t* __restrict__ diff,
+                                                const int8_t* __restrict__ layer, int32_t* __restrict__ diff,
                                                 Stats* stats) {
   __shared__ unsigned long long s_wl[kMaxL];
-  __shared__ unsigned long long s_v[8];
   __shared__ int64_t s_off[2];
   __shared__ int32_t s_npos[2], s_nld[2];
   __shared__ int8_t s_ld[kMaxL];
@@ -1209,11 +1266,8 @@ __global__ void __launch_bounds__(256) k_demand(int64_t V, int64_t S, int L, con
   }
   __syncthreads();
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  unsigned vias = 0, len = 0;
+  unsigned len = 0;
   int l = -1;
-  if (i < V)
-    vias = unsigned(__ldcs(reinterpret_cast<const signed char*>(t) + i) -
-                    __ldcs(reinterpret_cast<const signed char*>(b) + i));
   if (i < S) {
     const int v = __ldcs(seg_node + i);
     const uint64_t g = __ldcs(reinterpret_cast<const unsigned long long*>(seg_geo) + i);
@@ -1226,17 +1280,10 @@ __global__ void __launch_bounds__(256) k_demand(int64_t V, int64_t S, int L, con
     atomicAdd(diff + base + int64_t(len) * nld, -1);
   }
   // warp sums first: one shared atomic per warp and layer
-  const unsigned wv = __reduce_add_sync(0xffffffffu, vias);
-  if ((threadIdx.x & 31) == 0) s_v[threadIdx.x >> 5] = wv;
   const unsigned peers = __match_any_sync(0xffffffffu, l);
   const unsigned wl = __reduce_add_sync(peers, len);
   if (l >= 0 && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&s_wl[l], (unsigned long long)wl);
   __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned long long sv = 0;
-    for (int w = 0; w < int(blockDim.x >> 5); ++w) sv += s_v[w];
-    if (sv) atomicAdd(&stats->vias, sv);
-  }
   if (threadIdx.x < L && s_wl[threadIdx.x]) {
     atomicAdd(&stats->wl_layer[threadIdx.x], s_wl[threadIdx.x]);
     atomicAdd(&stats->wl, s_wl[threadIdx.x]);
@@ -1246,8 +1293,9 @@ __global__ void __launch_bounds__(256) k_demand(int64_t V, int64_t S, int L, con
 void launch_demand(la_ctx* c, cudaStream_t s) {
   Forest& f = c->forest;
   const int T = 256;
-  k_demand<<<(unsigned)((f.V + T - 1) / T), T, 0, s>>>(f.V, f.S, c->grid.li.L, c->grid.tab_dev, f.seg_node,
-                                                     f.seg_geo, f.layer, f.b, f.t, c->grid.diff, c->d_stats);
+  if (f.S == 0) return;
+  k_demand<<<(unsigned)((f.S + T - 1) / T), T, 0, s>>>(f.S, c->grid.li.L, c->grid.tab_dev, f.seg_node, f.seg_geo,
+                                                     f.layer, c->grid.diff, c->d_stats);
   ++c->launches;
 }
 
