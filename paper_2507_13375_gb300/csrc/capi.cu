@@ -413,7 +413,8 @@ la_status la_load_grid(la_ctx* c, const la_grid_desc* gd) {
     }
   DevTables& t = ng.tab;
   memset(&t, 0, sizeof t);
-  memcpy(t.rv, ng.rvia, sizeof t.rv);
+  for (int a = 0; a < kMaxL; ++a)
+    for (int b = 0; b < kMaxL; ++b) t.rv[a * kRvStride + b] = ng.rvia[a * kMaxL + b];
   for (int k = 0; k < kMaxL; ++k) t.kd[k] = double(k);
   for (int l = 0; l < kMaxL; ++l) {
     t.unit_r[l] = li.unit_r[l];
@@ -871,6 +872,44 @@ static la_status batched_caches(la_ctx* c, const RoundW& w, const double* W, int
 // Autotuner: time the DP + backtrack of every distinct split (size-class
 // threshold) and block shape on the loaded forest, keep the fastest.  The
 // trials compute the same tables the round computes next.
+// One trial of plan b timed the way the round runs it: the DP and backtrack
+// captured into a graph, then one untimed replay and the best of three timed
+// ones (launched one by one, the same kernels would be timed with the host's
+// launch overhead of every small level in them).
+static la_status time_plan(la_ctx* c, const BatchPlan& b, const RoundW& w, const double* W, const double* rho,
+                           int si, cudaStream_t s, double* ms_out) {
+  cudaStream_t cs = c->s_cap;
+  const long long l0 = c->launches;
+  CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  const la_status st = enqueue_batched(c, b, w, W, rho, si, cs);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(cs, &g);
+  c->launches = l0;
+  if (st != LA_OK || e != cudaSuccess || !g) {
+    if (g) cudaGraphDestroy(g);
+    if (st != LA_OK) return st;
+    return set_err(c, LA_ERR_CUDA, "la_assign_round: tuner capture failed: %s", cudaGetErrorString(e));
+  }
+  cudaGraphExec_t x = nullptr;
+  const cudaError_t ei = cudaGraphInstantiate(&x, g, 0);
+  cudaGraphDestroy(g);
+  if (ei != cudaSuccess) return set_err(c, LA_ERR_CUDA, "la_assign_round: tuner instantiate: %s", cudaGetErrorString(ei));
+  double t = 1e30;
+  cudaError_t er = cudaSuccess;
+  for (int rep = 0; rep < 4 && er == cudaSuccess; ++rep) {
+    float ms = 0.f;
+    if ((er = cudaEventRecord(c->ev[1], s)) != cudaSuccess || (er = cudaGraphLaunch(x, s)) != cudaSuccess ||
+        (er = cudaEventRecord(c->ev[2], s)) != cudaSuccess || (er = cudaEventSynchronize(c->ev[2])) != cudaSuccess ||
+        (er = cudaEventElapsedTime(&ms, c->ev[1], c->ev[2])) != cudaSuccess)
+      break;
+    if (rep > 0) t = std::min(t, double(ms));
+  }
+  cudaGraphExecDestroy(x);
+  if (er != cudaSuccess) return set_err(c, LA_ERR_CUDA, "la_assign_round: tuner trial: %s", cudaGetErrorString(er));
+  *ms_out = t;
+  return LA_OK;
+}
+
 static la_status autotune(la_ctx* c, const RoundW& w, const double* W, const double* rho, int si, cudaStream_t s) {
   Forest& f = c->forest;
   TRY(batched_caches(c, w, W, si, s));
@@ -898,15 +937,7 @@ static la_status autotune(la_ctx* c, const RoundW& w, const double* W, const dou
   BatchPlan chosen = cand.front();
   for (auto& b : cand) {
     double t = 1e30;
-    for (int rep = 0; rep < 2; ++rep) {
-      CK(cudaEventRecord(c->ev[1], s));
-      TRY(enqueue_batched(c, b, w, W, rho, si, s));
-      CK(cudaEventRecord(c->ev[2], s));
-      CK(cudaEventSynchronize(c->ev[2]));
-      float ms = 0.f;
-      CK(cudaEventElapsedTime(&ms, c->ev[1], c->ev[2]));
-      t = std::min(t, double(ms));
-    }
+    TRY(time_plan(c, b, w, W, rho, si, s, &t));
     if (t < best) { best = t; chosen = b; }
   }
   (void)f;
@@ -918,15 +949,7 @@ static la_status autotune(la_ctx* c, const RoundW& w, const double* W, const dou
     b.grid = chosen.grid;
     b.cached = chosen.cached;
     double t = 1e30;
-    for (int rep = 0; rep < 2; ++rep) {
-      CK(cudaEventRecord(c->ev[1], s));
-      TRY(enqueue_batched(c, b, w, W, rho, si, s));
-      CK(cudaEventRecord(c->ev[2], s));
-      CK(cudaEventSynchronize(c->ev[2]));
-      float ms = 0.f;
-      CK(cudaEventElapsedTime(&ms, c->ev[1], c->ev[2]));
-      t = std::min(t, double(ms));
-    }
+    TRY(time_plan(c, b, w, W, rho, si, s, &t));
     ++trials;
     if (t < best) { best = t; chosen = b; }
   }

@@ -81,8 +81,12 @@ struct LayerInfo {
 
 // Small per-grid tables every DP/backtrack/demand kernel reads with
 // thread-varying indices; kernels copy them to shared memory (load_tables).
+// Row stride of the Rvia table: odd, so that the threads of a node, each on
+// its own row l, reading column lc hit different shared-memory banks (a
+// stride of 16 doubles = 128 bytes would put them all on one bank).
+constexpr int kRvStride = kMaxL + 1;
 struct DevTables {
-  double rv[kMaxL * kMaxL];   // Rvia(a, b) = sum of via R between layers a and b
+  double rv[kMaxL * kRvStride];  // Rvia(a, b) at [a * kRvStride + b]: sum of via R between layers a and b
   double kd[kMaxL];           // 0.0, 1.0, ..., 15.0 (via counts as doubles)
   double unit_r[kMaxL], unit_c[kMaxL], half_c[kMaxL];
   double via_c;
@@ -380,6 +384,18 @@ __device__ __forceinline__ void dev_error(unsigned long long* err, int code, int
 // Order of non-negative doubles through their bit patterns (integer compare,
 // no FP64 pipe): a < b  <=>  bits(a) < bits(b) for a, b >= +0, not NaN.
 __device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
+
+// double(x) for an integer 0 <= x < 2^53, built from its bits (IEEE 754
+// binary64): the leading one, at bit p, shifted to the hidden bit 52, which
+// carries into the biased exponent 1022 + p written above it.  Exact, and no
+// FP64 instruction: GB300 issues FP64 (conversions included) at 1/64 of the
+// FP32 rate, so the kernels bound by it convert integers this way.
+__device__ __forceinline__ double exact_int_to_double(unsigned long long x) {
+  if (x == 0) return 0.0;
+  const int p = 63 - __clzll(static_cast<long long>(x));
+  return __longlong_as_double(
+      static_cast<long long>((x << (52 - p)) + (static_cast<unsigned long long>(1022 + p) << 52)));
+}
 
 // Copy the tables to shared memory; every thread of the block must call it.
 __device__ __forceinline__ void load_tables(DevTables& s, const DevTables* g) {

@@ -29,7 +29,7 @@ __global__ void k_rc(int64_t V, const DevTables* __restrict__ tab, const int32_t
     return;
   }
   const int l = layer[v];
-  const double len = double(geo_len(geo[v]));
+  const double len = exact_int_to_double(unsigned(geo_len(geo[v])));
   R[o] = len * tab->unit_r[l];
   C[o] = len * tab->unit_c[l];
 }
@@ -56,11 +56,11 @@ struct ElmArgs {
 // R / unit C of v's layer (the expressions of k_rc; 0 at roots).
 __device__ __forceinline__ double seg_r(const ElmArgs& a, int v) {
   if (a.R) return a.R[v];
-  return a.parent_g[v] < 0 ? 0.0 : double(geo_len(a.geo[v])) * a.tab->unit_r[a.layer[v]];
+  return a.parent_g[v] < 0 ? 0.0 : exact_int_to_double(unsigned(geo_len(a.geo[v]))) * a.tab->unit_r[a.layer[v]];
 }
 __device__ __forceinline__ double seg_c(const ElmArgs& a, int v) {
   if (a.C) return a.C[v];
-  return a.parent_g[v] < 0 ? 0.0 : double(geo_len(a.geo[v])) * a.tab->unit_c[a.layer[v]];
+  return a.parent_g[v] < 0 ? 0.0 : exact_int_to_double(unsigned(geo_len(a.geo[v]))) * a.tab->unit_c[a.layer[v]];
 }
 
 // Bottom-up: Cd_J(v) = C_seg[v]/2 + vc (t - b) + Cs_v + sum over sons of
@@ -103,12 +103,12 @@ __global__ void k_elm_delay(ElmArgs a) {
     dj = a.r_drv[a.net_of[v]] * a.CdJ[v];
   } else {
     const double hcv = a.HC ? a.HC[v] : 0.5 * seg_c(a, v);
-    const double dX = a.dJ[p] + a.tab->rv[a.layer[p] * kMaxL + lv] * (hcv + a.CdJ[v]);
+    const double dX = a.dJ[p] + a.tab->rv[a.layer[p] * kRvStride + lv] * (hcv + a.CdJ[v]);
     dj = dX + (a.RS ? a.RS[v] : seg_r(a, v)) * a.CdJ[v];
   }
   a.dJ[v] = dj;
   const int pin = a.pin[v];
-  a.delay[a.out_perm ? a.out_perm[v] : v] = pin >= 0 ? dj + a.tab->rv[lv * kMaxL + pin] * a.sink_cap[v] : dj;
+  a.delay[a.out_perm ? a.out_perm[v] : v] = pin >= 0 ? dj + a.tab->rv[lv * kRvStride + pin] * a.sink_cap[v] : dj;
 }
 
 // Top-down adjoint: U_J(root) = R_drv Ws(root); U_X(v) = U_J(p) + Rvia Ws(v);
@@ -126,7 +126,7 @@ __global__ void k_elm_adj(ElmArgs a) {
   const double w = a.Ws[v];
   const int lv = a.layer[v];
   const double Rv = seg_r(a, v);
-  const double UX = a.UJ[p] + a.tab->rv[a.layer[p] * kMaxL + lv] * w;
+  const double UX = a.UJ[p] + a.tab->rv[a.layer[p] * kRvStride + lv] * w;
   const double uj = UX + Rv * w;
   a.UJ[v] = uj;
   if (a.dR) {

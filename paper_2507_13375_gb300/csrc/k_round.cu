@@ -384,6 +384,14 @@ struct DPArgs {
   const double* scache;
 };
 
+// double(K) for the penalty sum K of a segment: built from K's bits where
+// that is exact (0 <= K < 2^53, which every sum of the non-negative penalties
+// below 2^53 is), else the conversion.
+__device__ __forceinline__ double penalty_to_double(long long K) {
+  if (K >= 0 && K < (1LL << 53)) return exact_int_to_double(static_cast<unsigned long long>(K));
+  return double(K);
+}
+
 // Sons of a several-son node whose choices per stack top are recorded.
 constexpr int kRecSons = 4;
 
@@ -474,7 +482,7 @@ __device__ __forceinline__ void dp_node(const DPArgs& a, const DevTables& s, con
     if (ldi >= s.nld[d]) return;
     l = s.lay[d][ldi];
   }
-  const double* rvl = &s.rv[l * kMaxL];
+  const double* rvl = &s.rv[l * kRvStride];
   const double* nc = CACHED ? a.ncache + 2 * int64_t(v) : nullptr;
   const double wd_rho = CACHED ? a.nround[2 * int64_t(v)] : a.w_d * a.rho[v];
   const double sigma_v = CACHED ? a.nround[2 * int64_t(v) + 1] : fma(wd_rho, s.via_c, a.sigma0);
@@ -674,9 +682,10 @@ __device__ __forceinline__ void dp_node(const DPArgs& a, const DevTables& s, con
       C = sc3[2];
       wdW = nc[0];
     } else {
-      const double R = double(len) * s.unit_r[l];
-      C = double(len) * s.unit_c[l];
-      const double Ch = double(len) * s.half_c[l];
+      const double lenf = exact_int_to_double(unsigned(len));
+      const double R = lenf * s.unit_r[l];
+      C = lenf * s.unit_c[l];
+      const double Ch = lenf * s.half_c[l];
       wdW = a.w_d * a.W[v];
       alpha = wdW * R;
       gamma = fma(alpha, Ch, a.w_cap * C);
@@ -684,7 +693,7 @@ __device__ __forceinline__ void dp_node(const DPArgs& a, const DevTables& s, con
     const int nldd = s.nld[d];
     const int64_t pb = s.grid_off[d] + int64_t(line) * s.npos[d] * nldd + ldi;
     const int64_t K = a.P[pb + int64_t(lo + len) * nldd] - a.P[pb + int64_t(lo) * nldd];
-    const double seg = fma(a.w_cong_s, double(K), gamma);
+    const double seg = fma(a.w_cong_s, penalty_to_double(K), gamma);
     const double Av = fma(alpha, cv, fv + seg);
     const double ccv = C + cv;
     a.A[o] = Av;
