@@ -187,6 +187,13 @@ typedef struct {
                             * la_commit_demand before the next round.  0: the
                             * round ends with D, H and the statistics of the
                             * whole forest                                      */
+  int32_t reweight_adjoint;/* 1: the round also leaves the adjoint weights of
+                            * its new assignment, as la_reweight_adjoint called
+                            * after it would (bit for bit; the top-down pass is
+                            * done by the backtrack kernels), so that the next
+                            * round can take LA_WEIGHTS_ADJOINT.  0: it leaves
+                            * the weights as they were.  Other values are
+                            * LA_ERR_INVALID                                     */
 } la_round_params;
 
 typedef struct {

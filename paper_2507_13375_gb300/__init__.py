@@ -66,7 +66,7 @@ class RoundParams(ctypes.Structure):
                 ("w_d", ctypes.c_double), ("hist_w", ctypes.c_double), ("mode", ctypes.c_int32),
                 ("weights", ctypes.c_int32), ("reset", ctypes.c_int32), ("no_look_ahead", ctypes.c_int32),
                 ("tail_threshold", ctypes.c_int32), ("force_split", ctypes.c_int32),
-                ("local_demand", ctypes.c_int32)]
+                ("local_demand", ctypes.c_int32), ("reweight_adjoint", ctypes.c_int32)]
 
 
 class RoundStats(ctypes.Structure):
@@ -207,12 +207,12 @@ def la_load_nets(ctx, forest: dict, device: int = 0):
 
 def la_assign_round(ctx, mode: int = LA_MODE_PLAIN, weights: int = LA_WEIGHTS_EQ4, reset: bool = False,
                     stats: bool = True, look_ahead: bool = True, tail_threshold: int = 0, force_split: int = 0,
-                    local_demand: bool = False, **w):
+                    local_demand: bool = False, reweight_adjoint: bool = False, **w):
     ww = dict(DEFAULT_WEIGHTS)
     ww.update(w)
     p = RoundParams(ww["w_cong"], ww["w_via"], ww["w_cap"], ww["w_d"], ww["hist_w"], int(mode), int(weights),
                     1 if reset else 0, 0 if look_ahead else 1, int(tail_threshold), int(force_split),
-                    1 if local_demand else 0)
+                    1 if local_demand else 0, int(reweight_adjoint))
     if not stats:
         _check(ctx, library().la_assign_round(ctx, ctypes.byref(p), None))
         return None
@@ -414,10 +414,10 @@ class LayerAssigner:
         self.V = int(len(forest["x"]))
 
     def assign_round(self, mode=LA_MODE_PLAIN, weights=LA_WEIGHTS_EQ4, reset=False, stats=True, look_ahead=True,
-                     tail_threshold=0, force_split=0, local_demand=False, **w):
+                     tail_threshold=0, force_split=0, local_demand=False, reweight_adjoint=False, **w):
         self._sync_stream()
         return la_assign_round(self.ctx, mode, weights, reset, stats, look_ahead, tail_threshold, force_split,
-                               local_demand, **w)
+                               local_demand, reweight_adjoint, **w)
 
     def commit_demand(self, D, stats=True):
         """D: the demand summed over every shard (public layout, int32, this device)."""

@@ -741,7 +741,7 @@ static uint64_t round_signature(la_ctx* c, int si, const double* W, const double
   h = fnv_mix(h, uint64_t(reinterpret_cast<uintptr_t>(W)));
   h = fnv_mix(h, uint64_t(reinterpret_cast<uintptr_t>(rho)));
   const int64_t vals[] = {f.N, f.V, f.Hmax, f.nbatch, f.red_cap, c->LD, bp.k, bp.block, bp.grid, bp.cached ? 1 : 0,
-                          bp.n_big, bp.Hs, bp.tail_h, int64_t(f.key_hash), local ? 1 : 0};
+                          bp.n_big, bp.Hs, bp.tail_h, int64_t(f.key_hash), local ? 1 : 0, c->fuse_adjoint ? 1 : 0};
   for (int64_t x : vals) h = fnv_mix(h, uint64_t(x));
   return h;
 }
@@ -1089,6 +1089,8 @@ la_status la_assign_round(la_ctx* c, const la_round_params* p, la_round_stats* s
   if (p->tail_threshold < 0) return set_err(c, LA_ERR_INVALID, "la_assign_round: tail_threshold must be >= 0");
   if (p->local_demand != 0 && p->local_demand != 1)
     return set_err(c, LA_ERR_INVALID, "la_assign_round: local_demand must be 0 or 1");
+  if (p->reweight_adjoint != 0 && p->reweight_adjoint != 1)
+    return set_err(c, LA_ERR_INVALID, "la_assign_round: reweight_adjoint must be 0 or 1");
   if (p->force_split != 0 && (p->force_split < kMinBigSc - 1 || p->force_split > kSizeClasses - 1))
     return set_err(c, LA_ERR_INVALID, "la_assign_round: force_split must be 0 or in [%d, %d]", kMinBigSc - 1,
                    kSizeClasses - 1);
@@ -1148,6 +1150,21 @@ la_status la_assign_round(la_ctx* c, const la_round_params* p, la_round_stats* s
   }
   // the statistics count this round only (not the tuner's trial rounds)
   CK(cudaMemsetAsync(c->d_stats, 0, sizeof(Stats), s));
+  // The adjoint reweighting of the new assignment in the backtrack (never in
+  // the tuner's trials above: their backtracks would overwrite the adjoint
+  // weights this round reads).  Its W, the kappa sums, depend on the forest
+  // only and are computed once.
+  struct FuseOff {
+    la_ctx* c;
+    ~FuseOff() { c->fuse_adjoint = false; }
+  } fuse_off{c};
+  if (p->reweight_adjoint) {
+    if (!f.wsum_valid) {
+      launch_wsum(c, s);
+      f.wsum_valid = true;
+    }
+    c->fuse_adjoint = true;
+  }
   bool captured = false;
   CK(cudaEventRecord(c->ev[0], s));
   if (batched) {
@@ -1197,6 +1214,7 @@ la_status la_assign_round(la_ctx* c, const la_round_params* p, la_round_stats* s
   gr.P_hist_w = p->hist_w;
   gr.round_hist_w = p->hist_w;
   f.have_assign = true;
+  if (p->reweight_adjoint) f.have_adj = true;
   if (!stats) return LA_OK;
   CK(cudaStreamSynchronize(s));
   int code;

@@ -260,6 +260,7 @@ struct la_ctx {
   cudaStream_t stream = nullptr;
   bool poisoned = false;
   la_status inject = LA_OK;             // la_inject_fault: the failure the next matching step reports
+  bool fuse_adjoint = false;            // the backtrack kernels also do the adjoint's top-down step
   std::string err;
   size_t bytes = 0;
   gapla::Grid grid;
@@ -372,6 +373,8 @@ void launch_elmore_bwd(la_ctx* c, const double* R, const double* C, const double
 // the layer): with_wsum, W_adj = the sums of g = kappa below each node, then
 // rho_adj = U_J; else rho_adj = U_J from the W_adj already there.
 void launch_reweight(la_ctx* c, bool with_wsum, cudaStream_t s);
+// W_adj = the sums of kappa below each node (they depend on the forest only)
+void launch_wsum(la_ctx* c, cudaStream_t s);
 
 // error message of calls that have no context (read by la_last_error(NULL))
 void set_noctx_error(const std::string& msg);

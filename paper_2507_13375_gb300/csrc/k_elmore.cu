@@ -91,6 +91,18 @@ __global__ void k_elm_up(ElmArgs a) {
   }
 }
 
+// Bottom-up sums of g alone: Ws(v) = g_v + sum over sons of Ws(c) (the
+// expression of k_elm_up, without the caps, which need an assignment).
+__global__ void k_wsum(ElmArgs a) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= a.count) return;
+  const int v = int(a.base + i);
+  const int cs = a.child_start[v], nc = a.nch[v];
+  double w = a.g[v];
+  for (int j = 0; j < nc; ++j) w = w + a.Ws[a.child_list[cs + j]];
+  a.Ws[v] = w;
+}
+
 // Top-down forward: delay at junctions, then at the pin point.
 __global__ void k_elm_delay(ElmArgs a) {
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -230,6 +242,14 @@ void launch_reweight(la_ctx* c, bool with_wsum, cudaStream_t s) {
     per_level(c, a, k_elm_up, true, s);
   }
   per_level(c, a, k_elm_adj, false, s);
+}
+
+void launch_wsum(la_ctx* c, cudaStream_t s) {
+  Forest& f = c->forest;
+  ElmArgs a = elm_args(c, nullptr, nullptr);
+  a.g = f.gk;
+  a.Ws = f.W_adj;
+  per_level(c, a, k_wsum, true, s);
 }
 
 }  // namespace gapla

@@ -785,26 +785,52 @@ __device__ void dp_node_any(const DPArgs& a, const DevTables& s, const RoundTabs
   }
 }
 
+struct BtArgs {
+  int LD;
+  const DevTables* tab;
+  const int32_t* parent_g;
+  const int8_t *pin, *ent, *sb, *st;
+  int8_t *layer, *b, *t;
+  Stats* stats;
+  // the adjoint reweighting fused into the backtrack (UJ null: not fused)
+  const uint64_t* geo;
+  const int32_t* net_of;
+  const double *r_drv, *Ws;
+  double* UJ;
+};
+
 // Alg. 4 at node v: its layer from its parent's choice, its stack; returns
-// the stack's via count t - b (the round's via statistic).
-__device__ __forceinline__ int backtrack_node(int v, int LD, const int8_t* ld_of, const int32_t* parent_g,
-                                              const int8_t* pin, const int8_t* ent, const int8_t* sb,
-                                              const int8_t* st, int8_t* layer, int8_t* b, int8_t* t) {
-  const int gp = parent_g[v];
-  int l, idx;
+// the stack's via count t - b (the round's via statistic).  With a.UJ, also
+// the top-down step of the adjoint reweighting on the new layers, in the
+// expressions of the separate pass (k_elm_adj with g = kappa):
+// U_J(root) = R_drv Ws; U_J(v) = (U_J(p) + Rvia(l_p, l_v) Ws(v)) + R_seg(v) Ws(v),
+// the parent's U_J written by the level (or barrier step) before.
+__device__ __forceinline__ int backtrack_node(const BtArgs& a, const int8_t* ld_of, int v) {
+  const int gp = a.parent_g[v];
+  int l, idx, lp = 0;
   if (gp < 0) {
-    l = pin[v];
+    l = a.pin[v];
     idx = 0;
   } else {
-    const int lp = layer[gp];
-    const int pidx = parent_g[gp] < 0 ? 0 : ld_of[lp];
-    l = ent[int64_t(v) * LD + pidx];
+    lp = a.layer[gp];
+    const int pidx = a.parent_g[gp] < 0 ? 0 : ld_of[lp];
+    l = a.ent[int64_t(v) * a.LD + pidx];
     idx = ld_of[l];
   }
-  layer[v] = int8_t(l);
-  const int bv = sb[int64_t(v) * LD + idx], tv = st[int64_t(v) * LD + idx];
-  b[v] = int8_t(bv);
-  t[v] = int8_t(tv);
+  a.layer[v] = int8_t(l);
+  const int bv = a.sb[int64_t(v) * a.LD + idx], tv = a.st[int64_t(v) * a.LD + idx];
+  a.b[v] = int8_t(bv);
+  a.t[v] = int8_t(tv);
+  if (a.UJ != nullptr) {
+    const double w = a.Ws[v];
+    if (gp < 0) {
+      a.UJ[v] = a.r_drv[a.net_of[v]] * w;
+    } else {
+      const double Rv = exact_int_to_double(unsigned(geo_len(a.geo[v]))) * a.tab->unit_r[l];
+      const double UX = a.UJ[gp] + a.tab->rv[lp * kRvStride + l] * w;
+      a.UJ[v] = UX + Rv * w;
+    }
+  }
   return tv - bv;
 }
 
@@ -900,15 +926,6 @@ __global__ void __launch_bounds__(256, 1) k_dp_tail(LayerInfo li, DPArgs a, cons
   }
 }
 
-struct BtArgs {
-  int LD;
-  const DevTables* tab;
-  const int32_t* parent_g;
-  const int8_t *pin, *ent, *sb, *st;
-  int8_t *layer, *b, *t;
-  Stats* stats;
-};
-
 __global__ void __launch_bounds__(256) k_backtrack_bignets(BtArgs a, BigArgs g) {
   __shared__ int s_q;
   __shared__ int8_t s_ld[kMaxL];
@@ -926,8 +943,7 @@ __global__ void __launch_bounds__(256) k_backtrack_bignets(BtArgs a, BigArgs g) 
     for (int h = g.net_H[n]; h >= 0; --h) {
       const int lo = ho[h], cnt = ho[h + 1] - lo;
       for (int t = threadIdx.x; t < cnt; t += blockDim.x)
-        vias += backtrack_node(g.bl_nodes[base + lo + t], a.LD, s_ld, a.parent_g, a.pin, a.ent, a.sb, a.st, a.layer,
-                               a.b, a.t);
+        vias += backtrack_node(a, s_ld, g.bl_nodes[base + lo + t]);
       __syncthreads();
     }
   }
@@ -1046,7 +1062,7 @@ __global__ void __launch_bounds__(256) k_backtrack_level(Ranges r, BtArgs a) {
   if (j < r.total) {
     int k = 0;
     while (k < kClasses - 1 && j >= r.cnt[k]) j -= r.cnt[k++];
-    vias = backtrack_node(int(r.lo[k] + j), a.LD, s_ld, a.parent_g, a.pin, a.ent, a.sb, a.st, a.layer, a.b, a.t);
+    vias = backtrack_node(a, s_ld, int(r.lo[k] + j));
   }
   add_vias(a.stats, vias);
 }
@@ -1070,8 +1086,7 @@ __global__ void __launch_bounds__(256) k_backtrack_tail(BtArgs a, const int64_t*
       int64_t r = t;
       int cls = 0;
       while (cls < kClasses - 1 && r >= s_n[cls]) r -= s_n[cls++];
-      vias += backtrack_node(int(s_lo[cls] + r), a.LD, s_ld, a.parent_g, a.pin, a.ent, a.sb, a.st, a.layer, a.b,
-                             a.t);
+      vias += backtrack_node(a, s_ld, int(s_lo[cls] + r));
     }
     __syncthreads();
   }
@@ -1080,7 +1095,10 @@ __global__ void __launch_bounds__(256) k_backtrack_tail(BtArgs a, const int64_t*
 
 static BtArgs bt_args(la_ctx* c) {
   Forest& f = c->forest;
-  return BtArgs{c->LD, c->grid.tab_dev, f.parent_g, f.pin, f.ent, f.sb, f.st, f.layer, f.b, f.t, c->d_stats};
+  BtArgs a{c->LD, c->grid.tab_dev, f.parent_g, f.pin, f.ent, f.sb, f.st, f.layer, f.b, f.t, c->d_stats,
+           f.geo, f.net_of, f.r_drv, f.W_adj, nullptr};
+  if (c->fuse_adjoint) a.UJ = f.rho_adj;
+  return a;
 }
 
 void launch_backtrack_level(la_ctx* c, int level, int kmax, cudaStream_t s) {

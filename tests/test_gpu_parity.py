@@ -843,3 +843,55 @@ def test_slack_driven_ordering_end_to_end(la):
         D, H, prev = got["D"], got["H"], got["layer"]
     a.close()
     b.close()
+
+
+def _adjoint_rounds(la, grid, forest, mode, fused, rounds=3, **kw):
+    """Rounds with adjoint weights after the first; the weights come from the
+    round itself (fused) or from la_reweight_adjoint after it."""
+    a = _assigner(la, grid, forest)
+    out = []
+    for r in range(rounds):
+        src = la.LA_WEIGHTS_ADJOINT if r > 0 else la.LA_WEIGHTS_EQ4
+        st = a.assign_round(mode=mode, reset=(r == 0), weights=src, reweight_adjoint=fused, **kw,
+                            **la.DEFAULT_WEIGHTS)
+        if not fused:
+            a.reweight_adjoint()
+        W, rho = (x.cpu().numpy() for x in a.get_weights(la.LA_WEIGHTS_ADJOINT))
+        got = dict(layer=a.get_assignment()[0].cpu().numpy(), J=a.get_net_cost().cpu().numpy(), W=W, rho=rho,
+                   stats=st)
+        out.append(got)
+    a.close()
+    return out
+
+
+@pytest.mark.parametrize("case", ["plain", "batched", "batched_big_nets", "batched_tail", "plain_batches",
+                                  "batched_batches"])
+def test_reweighting_fused_into_the_backtrack(la, case):
+    """reweight_adjoint = 1 leaves the same W and r_est, bit for bit, as
+    la_reweight_adjoint after the round (the top-down pass done by every
+    backtrack kernel: level waves, the tail kernel, the persistent big-net
+    kernel, sequential batches), so the rounds that follow are the same too."""
+    cfg, nets, kw = {"plain": (2, 20000, {}), "batched": (5, 100000, {}),
+                     "batched_big_nets": (4, 20000, dict(force_split=4)),
+                     "batched_tail": (2, 20000, dict(tail_threshold=8192)),
+                     "plain_batches": (2, 12000, {}), "batched_batches": (2, 12000, {})}[case]
+    wl = fg.WORKLOADS[cfg].scaled(nets)
+    grid, forest = fg.make_grid(wl, 23), fg.make_forest(wl, 23)
+    if case.endswith("batches"):
+        N = int(forest["num_nets"])
+        forest = dict(forest, batch=(np.arange(N) % 3).astype(np.int32))
+    mode = la.LA_MODE_PLAIN if case.startswith("plain") else la.LA_MODE_BATCHED
+    sep = _adjoint_rounds(la, grid, forest, mode, False, **kw)
+    fus = _adjoint_rounds(la, grid, forest, mode, True, **kw)
+    for r, (p, q) in enumerate(zip(sep, fus)):
+        for k in ("W", "rho", "layer", "J"):
+            assert np.array_equal(p[k], q[k]), (case, r, k)
+    if case == "batched_big_nets":
+        assert fus[0]["stats"]["batch_big_nets"] > 0
+    if case == "batched_tail":
+        assert fus[0]["stats"]["batch_tail_level"] < fus[0]["stats"]["batch_levels"]
+    a = _assigner(la, grid, forest)
+    with pytest.raises(la.LaError) as e:
+        a.assign_round(mode=mode, reset=True, reweight_adjoint=2, **la.DEFAULT_WEIGHTS)
+    assert e.value.status == la.LA_ERR_INVALID
+    a.close()
