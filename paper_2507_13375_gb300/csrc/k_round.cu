@@ -10,6 +10,7 @@
 // doubles compare their bit patterns as int64 (exact, and it keeps the
 // comparisons off the FP64 pipe, which GB300 runs at 1/64 of FP32).
 #include <algorithm>
+#include <cfloat>
 #include <climits>
 
 #include "gapla_internal.cuh"
@@ -392,6 +393,22 @@ __device__ __forceinline__ double penalty_to_double(long long K) {
   return double(K);
 }
 
+// Float bounds of FP64 values, for an exact argmin filter on the FP32 pipe.
+// f32_lo(x): the largest float <= x for x >= 0 (the double's bits truncated
+// to a float's: 0 below 2^-126, FLT_MAX from 2^128 on).  f32_up(lo): a float
+// >= every x whose lower bound is lo (the next float up; FLT_MIN above a 0).
+// Integer instructions only.
+__device__ __forceinline__ float f32_lo(double x) {
+  const unsigned hi = unsigned(__double2hiint(x)), lo = unsigned(__double2loint(x));
+  const unsigned e = hi >> 20;  // biased exponent (the sign bit is 0)
+  if (e <= 1023u - 127u) return 0.0f;
+  if (e >= 1023u + 128u) return FLT_MAX;
+  return __uint_as_float(((hi - ((1023u - 127u) << 20)) << 3) | (lo >> 29));
+}
+__device__ __forceinline__ float f32_up(float lo) {
+  return lo == 0.0f ? FLT_MIN : __uint_as_float(__float_as_uint(lo) + 1u);
+}
+
 // Sons of a several-son node whose choices per stack top are recorded.
 constexpr int kRecSons = 4;
 
@@ -417,12 +434,14 @@ __device__ __forceinline__ void load_round_tabs(RoundTabs& rt, const DPArgs& a, 
 // CACHED: read the batched form's constant caches instead of recomputing.
 // PINK: 1 the node has a pin, 0 it has none, 2 read it (mixed classes).
 // STAGED (one son, not a root): the son and its table row (B, M, A, Cc) come
-// in `so`, already copied to shared memory by the node's threads.
+// in `so`, already copied to shared memory by the node's threads, with float
+// bounds of B and M, and the block's float bounds of the Rvia table.
 struct Son1 {
   int c, dc;
   const double *B, *M, *A, *Cc;
-  const double* T;  // no pin: the node's tail costs T(k) = fma(k, sigma_v, 0.0), k < L
-  long long* K;     // the thread's son keys by son layer index, stride 256 (shared memory)
+  const float *Blo, *Bup, *Mlo, *Mup;  // f32_lo / f32_up of the son's B and M
+  const float *rlo, *rup;              // of Rvia(a, b), at [a * L + b]
+  long long* K;                        // the thread's son keys by son layer index, stride 256 (shared memory)
 };
 // One son of a several-son node in the scan of the stacks with bottom b: its
 // keys on its own direction's layers go to keyL by layer ([t][thread], the
@@ -490,7 +509,7 @@ __device__ __forceinline__ void dp_node(const DPArgs& a, const DevTables& s, con
   if (PINK == 1 || (PINK == 2 && pin >= 0)) {
     Cs = a.sink_cap[v];
     sinkf = ((CACHED ? nc[1] : a.w_d * a.kappa[v]) * rvl[pin]) * Cs;
-    z = fma(wd_rho, Cs, sinkf);
+    if constexpr (!STAGED) z = fma(wd_rho, Cs, sinkf);  // staged: only where the filter falls back
   }
   const int lo_req = pin >= 0 ? min(l, pin) : l;
   const int hi_req = pin >= 0 ? max(l, pin) : l;
@@ -523,65 +542,110 @@ __device__ __forceinline__ void dp_node(const DPArgs& a, const DevTables& s, con
       Ac = a.A + int64_t(c) * LD; Ccc = a.Cc + int64_t(c) * LD;
     }
     const int nldc = s.nld[dc];
-    long long key[LDM];
-    int p = 0, q = 0;  // son layer indices [p, q) lie in [lo_req, hi_req]
-#pragma unroll
-    for (int j = 0; j < LDM; ++j) {
-      if (j < nldc) {
-        const int lc = s.lay[dc][j];
-        p += lc < lo_req;
-        q += lc <= hi_req;
-        key[j] = dbits(fma(Mc[j], rvl[lc], Bc[j]));
-        if constexpr (STAGED && PINK == 0) so.K[j * 256] = key[j];
+    int bj = -1;
+    if constexpr (STAGED) {
+      // Exact filter on the FP32 pipe.  With f_j = RN(key_j + tail(via count
+      // of the hull of l, the pin and the son layer j)), every stack costs at
+      // least the f_j of its son's choice j (the tails grow with the via
+      // count), so if one f_j is below every other, its hull is the stack
+      // Kernel 2 picks, with j the son's choice in it (a larger stack with
+      // the same choice costs no less and has more vias).  Bounds of every
+      // f_j from float bounds of the operands with directed rounding
+      // (everything is >= 0, and RN is monotone); if they separate one j
+      // from the rest it is the winner, else the FP64 search below decides.
+      const float slo = f32_lo(sigma_v), sup = f32_up(slo);
+      float zlo = 0.0f, zup = 0.0f;
+      if constexpr (PINK == 1) {
+        const float wlo = f32_lo(wd_rho), clo = f32_lo(Cs), flo = f32_lo(sinkf);
+        zlo = __fmaf_rd(wlo, clo, flo);
+        zup = __fmaf_ru(f32_up(wlo), f32_up(clo), f32_up(flo));
       }
-    }
-    long long inmin = LLONG_MAX;
-    int m = -1;
-#pragma unroll
-    for (int j = 0; j < LDM; ++j)
-      if (j >= p && j < q && key[j] < inmin) { inmin = key[j]; m = j; }
-    unsigned cons = m >= 0 ? 1u << m : 0u;
-    long long run = inmin;
-#pragma unroll
-    for (int j = LDM - 1; j >= 0; --j)
-      if (j < p) {
-        if (key[j] <= run) cons |= 1u << j;
-        run = min(run, key[j]);
-      }
-    run = inmin;
-#pragma unroll
-    for (int j = 0; j < LDM; ++j)
-      if (j >= q && j < nldc) {
-        if (key[j] < run) cons |= 1u << j;
-        run = min(run, key[j]);
-      }
-    int bj = 0, bk = INT_MAX;
-    if constexpr (STAGED && PINK == 0) {
-      // the consistent candidates only, lowest index first (a warp issues the
-      // most any of its threads has, not the union of theirs; the tail costs
-      // come from the node's table)
-      for (unsigned mm = cons; mm; mm &= mm - 1u) {
-        const int j = __ffs(mm) - 1;
-        const int lcj = s.lay[dc][j];
-        const int b0 = min(lo_req, lcj), t0 = max(hi_req, lcj);
-        const long long f = dbits(__longlong_as_double(so.K[j * 256]) + so.T[t0 - b0]);
-        if (stack_better(f, t0 - b0, b0, bfp, bk, bb)) { bfp = f; bk = t0 - b0; bb = b0; bt = t0; bj = j; }
-      }
-    } else {
+      const float* rlo = so.rlo + l * L;
+      const float* rup = so.rup + l * L;
+      float best_up = INFINITY, lo1 = INFINITY, lo2 = INFINITY;
+      int jb = -1, jlo = -1;
 #pragma unroll
       for (int j = 0; j < LDM; ++j) {
-        if ((cons >> j) & 1u) {
-          const int lcj = s.lay[dc][j];
-          const int b0 = min(lo_req, lcj), t0 = max(hi_req, lcj);
-          const double tail = (STAGED && PINK == 0) ? so.T[t0 - b0] : fma(s.kd[t0 - b0], sigma_v, z);
-          const long long f = dbits(__longlong_as_double(key[j]) + tail);
-          if (stack_better(f, t0 - b0, b0, bfp, bk, bb)) { bfp = f; bk = t0 - b0; bb = b0; bt = t0; bj = j; }
+        if (j < nldc) {
+          const int lc = s.lay[dc][j];
+          const float kf = float(max(hi_req, lc) - min(lo_req, lc));
+          const float klo = __fmaf_rd(so.Mlo[j], rlo[lc], so.Blo[j]);
+          const float kup = __fmaf_ru(so.Mup[j], rup[lc], so.Bup[j]);
+          const float tlo = PINK == 1 ? __fmaf_rd(kf, slo, zlo) : __fmul_rd(kf, slo);
+          const float tup = PINK == 1 ? __fmaf_ru(kf, sup, zup) : __fmul_ru(kf, sup);
+          const float flo = __fadd_rd(klo, tlo), fup = __fadd_ru(kup, tup);
+          if (fup < best_up) { best_up = fup; jb = j; }
+          if (flo < lo1) { lo2 = lo1; lo1 = flo; jlo = j; } else if (flo < lo2) { lo2 = flo; }
         }
       }
+      if (jb >= 0 && best_up < (jlo == jb ? lo2 : lo1)) {
+        bj = jb;
+        const int lc = s.lay[dc][jb];
+        bb = min(lo_req, lc);
+        bt = max(hi_req, lc);
+      }
     }
-    if (bfp == LLONG_MAX) {  // cannot happen (the least key overall is consistent); report it
-      dev_error(a.err, DE_NOSTACK, v);
-      return;
+    if (bj < 0) {
+      if constexpr (STAGED && PINK == 1) z = fma(wd_rho, Cs, sinkf);
+      long long key[LDM];
+      int p = 0, q = 0;  // son layer indices [p, q) lie in [lo_req, hi_req]
+#pragma unroll
+      for (int j = 0; j < LDM; ++j) {
+        if (j < nldc) {
+          const int lc = s.lay[dc][j];
+          p += lc < lo_req;
+          q += lc <= hi_req;
+          key[j] = dbits(fma(Mc[j], rvl[lc], Bc[j]));
+          if constexpr (STAGED && PINK == 0) so.K[j * 256] = key[j];
+        }
+      }
+      long long inmin = LLONG_MAX;
+      int m = -1;
+#pragma unroll
+      for (int j = 0; j < LDM; ++j)
+        if (j >= p && j < q && key[j] < inmin) { inmin = key[j]; m = j; }
+      unsigned cons = m >= 0 ? 1u << m : 0u;
+      long long run = inmin;
+#pragma unroll
+      for (int j = LDM - 1; j >= 0; --j)
+        if (j < p) {
+          if (key[j] <= run) cons |= 1u << j;
+          run = min(run, key[j]);
+        }
+      run = inmin;
+#pragma unroll
+      for (int j = 0; j < LDM; ++j)
+        if (j >= q && j < nldc) {
+          if (key[j] < run) cons |= 1u << j;
+          run = min(run, key[j]);
+        }
+      int bk = INT_MAX;
+      bj = 0;
+      if constexpr (STAGED && PINK == 0) {
+        // the consistent candidates only, lowest index first (a warp issues
+        // the most any of its threads has, not the union of theirs)
+        for (unsigned mm = cons; mm; mm &= mm - 1u) {
+          const int j = __ffs(mm) - 1;
+          const int lcj = s.lay[dc][j];
+          const int b0 = min(lo_req, lcj), t0 = max(hi_req, lcj);
+          const long long f = dbits(__longlong_as_double(so.K[j * 256]) + fma(s.kd[t0 - b0], sigma_v, 0.0));
+          if (stack_better(f, t0 - b0, b0, bfp, bk, bb)) { bfp = f; bk = t0 - b0; bb = b0; bt = t0; bj = j; }
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < LDM; ++j) {
+          if ((cons >> j) & 1u) {
+            const int lcj = s.lay[dc][j];
+            const int b0 = min(lo_req, lcj), t0 = max(hi_req, lcj);
+            const long long f = dbits(__longlong_as_double(key[j]) + fma(s.kd[t0 - b0], sigma_v, z));
+            if (stack_better(f, t0 - b0, b0, bfp, bk, bb)) { bfp = f; bk = t0 - b0; bb = b0; bt = t0; bj = j; }
+          }
+        }
+      }
+      if (bfp == LLONG_MAX) {  // cannot happen (the least key overall is consistent); report it
+        dev_error(a.err, DE_NOSTACK, v);
+        return;
+      }
     }
     const int lc = s.lay[dc][bj];
     a.ent[int64_t(c) * LD + ldi] = int8_t(lc);
@@ -714,33 +778,43 @@ __global__ void __launch_bounds__(256, (DEG == 1 && !ROOT && PINK == 0 ? 5 : (DE
   load_tables(s, a.tab);
   if constexpr (DEG == 1 && !ROOT) {
     // whole nodes per block (256 / LD of them): the node's threads copy the
-    // son's table row to shared memory, one entry each per array
-    // (a node without a pin also tabulates its tail costs T(k), k < L, once)
+    // son's table row to shared memory, one entry each per array, with
+    // float bounds of its B and M; the block's threads bound the Rvia table
     __shared__ double s_son[4][256];
-    __shared__ double s_T[PINK == 0 ? 512 : 1];  // (256 / LD) nodes x L <= 512 since LD >= L / 2
+    __shared__ float s_sf[4][256];
+    __shared__ float s_rf[2][kMaxL * kMaxL];
     __shared__ long long s_key[PINK == 0 ? LDM : 1][256];
-    const int LD = a.LD, npb = 256 / LD;
+    const int LD = a.LD, npb = 256 / LD, L = li.L;
+    for (int i = threadIdx.x; i < L * L; i += blockDim.x) {
+      const float r = f32_lo(s.rv[(i / L) * kRvStride + i % L]);
+      s_rf[0][i] = r;
+      s_rf[1][i] = f32_up(r);
+    }
     const int gi = int(threadIdx.x) / LD, ldi = int(threadIdx.x) - gi * LD;
     const int64_t node_i = int64_t(blockIdx.x) * npb + gi;
     const bool in = gi < npb && node_i < a.count;
     const int v = int(a.base + (in ? node_i : 0));
     Son1 so{};
     so.K = &s_key[0][threadIdx.x];
+    so.rlo = s_rf[0];
+    so.rup = s_rf[1];
     if (in) {
       so.c = a.child_list[a.child_start[v]];
       so.dc = geo_dir(a.geo[so.c]);
       const int64_t o = int64_t(so.c) * LD + ldi;
-      s_son[0][threadIdx.x] = a.B[o];
-      s_son[1][threadIdx.x] = a.M[o];
+      const double Bo = a.B[o], Mo = a.M[o];
+      s_son[0][threadIdx.x] = Bo;
+      s_son[1][threadIdx.x] = Mo;
       s_son[2][threadIdx.x] = a.A[o];
       s_son[3][threadIdx.x] = a.Cc[o];
-      so.B = &s_son[0][gi * LD]; so.M = &s_son[1][gi * LD]; so.A = &s_son[2][gi * LD]; so.Cc = &s_son[3][gi * LD];
-      if constexpr (PINK == 0) {
-        const double sig = CACHED ? a.nround[2 * int64_t(v) + 1] : fma(a.w_d * a.rho[v], li.via_c, a.sigma0);
-        double* T = &s_T[gi * li.L];
-        for (int k2 = ldi; k2 < li.L; k2 += LD) T[k2] = fma(s.kd[k2], sig, 0.0);
-        so.T = T;
-      }
+      const float bl = f32_lo(Bo), ml = f32_lo(Mo);
+      s_sf[0][threadIdx.x] = bl;
+      s_sf[1][threadIdx.x] = f32_up(bl);
+      s_sf[2][threadIdx.x] = ml;
+      s_sf[3][threadIdx.x] = f32_up(ml);
+      const int r0 = gi * LD;
+      so.B = &s_son[0][r0]; so.M = &s_son[1][r0]; so.A = &s_son[2][r0]; so.Cc = &s_son[3][r0];
+      so.Blo = &s_sf[0][r0]; so.Bup = &s_sf[1][r0]; so.Mlo = &s_sf[2][r0]; so.Mup = &s_sf[3][r0];
     }
     __syncthreads();
     if (!in) return;
