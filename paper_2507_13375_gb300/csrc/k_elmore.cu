@@ -49,8 +49,17 @@ struct ElmArgs {
   const double *sink_cap, *r_drv, *R, *C, *g;
   const DevTables* tab;
   double *CdJ, *Ws, *dJ, *delay, *UJ, *dR, *dC;
-  double *HC, *RS;  // forward: C_seg / 2 and R_seg of every node, kept by the bottom-up pass
+  double *CX, *RS;  // forward: C_seg / 2 + Cd_J and R_seg of every node, kept by the bottom-up pass
+  double vck[kMaxL];  // via_c x k, k = 0 .. kMaxL - 1 (the products the expressions take)
 };
+
+// 0.5 x: exact for a finite x >= 0, by one less in the exponent where the
+// result stays normal (GB300 issues FP64 at 1/64 of FP32; this is integer).
+__device__ __forceinline__ double half_exact(double x) {
+  const long long b = __double_as_longlong(x);
+  const long long e = b >> 52;  // biased exponent (x >= 0)
+  return (e >= 2 && e < 2047) ? __longlong_as_double(b - (1LL << 52)) : 0.5 * x;
+}
 
 // R_seg and C_seg of node v: the given arrays, or the assignment's len x unit
 // R / unit C of v's layer (the expressions of k_rc; 0 at roots).
@@ -65,25 +74,26 @@ __device__ __forceinline__ double seg_c(const ElmArgs& a, int v) {
 
 // Bottom-up: Cd_J(v) = C_seg[v]/2 + vc (t - b) + Cs_v + sum over sons of
 // (C_seg[c]/2 + Cd_J(c)); with g, also Ws(v) = g_v + sum over sons of Ws(c).
-// With HC (the forward pass) the node's C_seg/2, and with RS its R_seg, are
-// kept for its parent and for the top-down pass (the same values the
-// expressions would compute again).
+// With CX (the forward pass) the node's C_seg/2 + Cd_J, and with RS its
+// R_seg, are kept for its parent and for the top-down pass (the values the
+// expressions would compute again).  A node without a pin has Cs = 0, and
+// s + 0.0 = s for the s >= 0 here, so that term is added at pins only.
 __global__ void k_elm_up(ElmArgs a) {
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= a.count) return;
   const int v = int(a.base + i);
-  const double hcv = a.parent_g[v] < 0 ? 0.0 : 0.5 * seg_c(a, v);
-  if (a.HC) a.HC[v] = hcv;
+  const double hcv = a.parent_g[v] < 0 ? 0.0 : half_exact(seg_c(a, v));
   if (a.RS) a.RS[v] = seg_r(a, v);
   double s = hcv;
-  s = s + a.tab->via_c * a.tab->kd[a.t[v] - a.b[v]];
-  s = s + a.sink_cap[v];
+  s = s + a.vck[a.t[v] - a.b[v]];
+  if (a.pin[v] >= 0) s = s + a.sink_cap[v];
   const int cs = a.child_start[v], nc = a.nch[v];
   for (int j = 0; j < nc; ++j) {
     const int c = a.child_list[cs + j];
-    s = s + ((a.HC ? a.HC[c] : 0.5 * seg_c(a, c)) + a.CdJ[c]);
+    s = s + (a.CX ? a.CX[c] : half_exact(seg_c(a, c)) + a.CdJ[c]);
   }
   a.CdJ[v] = s;
+  if (a.CX) a.CX[v] = hcv + s;
   if (a.Ws) {
     double w = a.g[v];
     for (int j = 0; j < nc; ++j) w = w + a.Ws[a.child_list[cs + j]];
@@ -114,8 +124,8 @@ __global__ void k_elm_delay(ElmArgs a) {
   if (p < 0) {
     dj = a.r_drv[a.net_of[v]] * a.CdJ[v];
   } else {
-    const double hcv = a.HC ? a.HC[v] : 0.5 * seg_c(a, v);
-    const double dX = a.dJ[p] + a.tab->rv[a.layer[p] * kRvStride + lv] * (hcv + a.CdJ[v]);
+    const double cx = a.CX ? a.CX[v] : half_exact(seg_c(a, v)) + a.CdJ[v];
+    const double dX = a.dJ[p] + a.tab->rv[a.layer[p] * kRvStride + lv] * cx;
     dj = dX + (a.RS ? a.RS[v] : seg_r(a, v)) * a.CdJ[v];
   }
   a.dJ[v] = dj;
@@ -143,7 +153,7 @@ __global__ void k_elm_adj(ElmArgs a) {
   a.UJ[v] = uj;
   if (a.dR) {
     a.dR[v] = a.CdJ[v] * w;
-    a.dC[v] = 0.5 * (UX + uj);
+    a.dC[v] = half_exact(UX + uj);
   }
 }
 
@@ -153,6 +163,7 @@ static ElmArgs elm_args(la_ctx* c, const double* R, const double* C) {
   a.parent_g = f.parent_g; a.child_start = f.child_start; a.nch = f.nch; a.child_list = f.child_list;
   a.net_of = f.net_of; a.layer = f.layer; a.b = f.b; a.t = f.t; a.pin = f.pin; a.sink_cap = f.sink_cap;
   a.r_drv = f.r_drv; a.R = R; a.C = C; a.tab = c->grid.tab_dev; a.geo = f.geo;
+  for (int k = 0; k < kMaxL; ++k) a.vck[k] = c->grid.li.via_c * double(k);
   return a;
 }
 
@@ -179,7 +190,7 @@ void launch_elmore_fwd(la_ctx* c, const double* R, const double* C, double* dela
   ElmArgs a = elm_args(c, f.s3, f.s4);
   a.CdJ = f.s0;
   a.dJ = f.s1;
-  a.HC = f.s2;
+  a.CX = f.s2;
   a.delay = delay;
   a.out_perm = f.lvl_nodes;
   per_level(c, a, k_elm_up, true, s);
@@ -193,7 +204,7 @@ void launch_elmore_assignment(la_ctx* c, double* delay_input_order, cudaStream_t
   ElmArgs a = elm_args(c, nullptr, nullptr);
   a.CdJ = f.s0;
   a.dJ = f.s1;
-  a.HC = f.s2;
+  a.CX = f.s2;
   a.RS = f.s3;
   a.delay = delay_input_order;
   a.out_perm = f.lvl_nodes;

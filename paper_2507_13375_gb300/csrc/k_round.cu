@@ -440,8 +440,16 @@ struct Son1 {
   int c, dc;
   const double *B, *M, *A, *Cc;
   const float *Blo, *Bup, *Mlo, *Mup;  // f32_lo / f32_up of the son's B and M
-  const float *rlo, *rup;              // of Rvia(a, b), at [a * L + b]
+  const float *rlo, *rup;              // of Rvia(a, b), at [a * kRvStride + b]
   long long* K;                        // the thread's son keys by son layer index, stride 256 (shared memory)
+  // the thread's own node data, loaded before the block's barrier: geometry,
+  // pin, sink cap; cached: {w_d W, w_d kappa}, {w_d r_est, sigma}, the
+  // parent's w_d r_est, {alpha, gamma, C} (else W, kappa, r_est, the parent's
+  // r_est); the two prefix values of the segment on the candidate layer
+  uint64_t gv;
+  int pin;
+  double Cs, nc0, nc1, nr0, nr1, rp, sc0, sc1, sc2;
+  long long Kseg;  // P[end] - P[start]: the segment's penalty sum on the candidate layer
 };
 // One son of a several-son node in the scan of the stacks with bottom b: its
 // keys on its own direction's layers go to keyL by layer ([t][thread], the
@@ -491,8 +499,8 @@ __device__ __forceinline__ void dp_node(const DPArgs& a, const DevTables& s, con
                                         int8_t* chbuf = nullptr) {
   static_assert(!STAGED || (DEG == 1 && !ROOT), "staged son rows are for one-son non-root nodes");
   const int LD = a.LD;
-  const int pin = PINK == 0 ? -1 : a.pin[v];
-  const uint64_t gv = a.geo[v];
+  const int pin = PINK == 0 ? -1 : (STAGED ? so.pin : a.pin[v]);
+  const uint64_t gv = STAGED ? so.gv : a.geo[v];
   const int d = geo_dir(gv);
   int l;
   if constexpr (ROOT) {
@@ -503,12 +511,12 @@ __device__ __forceinline__ void dp_node(const DPArgs& a, const DevTables& s, con
   }
   const double* rvl = &s.rv[l * kRvStride];
   const double* nc = CACHED ? a.ncache + 2 * int64_t(v) : nullptr;
-  const double wd_rho = CACHED ? a.nround[2 * int64_t(v)] : a.w_d * a.rho[v];
-  const double sigma_v = CACHED ? a.nround[2 * int64_t(v) + 1] : fma(wd_rho, s.via_c, a.sigma0);
+  const double wd_rho = CACHED ? (STAGED ? so.nr0 : a.nround[2 * int64_t(v)]) : a.w_d * (STAGED ? so.nr0 : a.rho[v]);
+  const double sigma_v = CACHED ? (STAGED ? so.nr1 : a.nround[2 * int64_t(v) + 1]) : fma(wd_rho, s.via_c, a.sigma0);
   double Cs = 0.0, sinkf = 0.0, z = 0.0;  // a node without a pin: all exactly 0
   if (PINK == 1 || (PINK == 2 && pin >= 0)) {
-    Cs = a.sink_cap[v];
-    sinkf = ((CACHED ? nc[1] : a.w_d * a.kappa[v]) * rvl[pin]) * Cs;
+    Cs = STAGED ? so.Cs : a.sink_cap[v];
+    sinkf = ((CACHED ? (STAGED ? so.nc1 : nc[1]) : a.w_d * (STAGED ? so.nc1 : a.kappa[v])) * rvl[pin]) * Cs;
     if constexpr (!STAGED) z = fma(wd_rho, Cs, sinkf);  // staged: only where the filter falls back
   }
   const int lo_req = pin >= 0 ? min(l, pin) : l;
@@ -560,8 +568,8 @@ __device__ __forceinline__ void dp_node(const DPArgs& a, const DevTables& s, con
         zlo = __fmaf_rd(wlo, clo, flo);
         zup = __fmaf_ru(f32_up(wlo), f32_up(clo), f32_up(flo));
       }
-      const float* rlo = so.rlo + l * L;
-      const float* rup = so.rup + l * L;
+      const float* rlo = so.rlo + l * kRvStride;
+      const float* rup = so.rup + l * kRvStride;
       float best_up = INFINITY, lo1 = INFINITY, lo2 = INFINITY;
       int jb = -1, jlo = -1;
 #pragma unroll
@@ -739,7 +747,12 @@ __device__ __forceinline__ void dp_node(const DPArgs& a, const DevTables& s, con
   } else {
     const int len = geo_len(gv), line = geo_line(gv), lo = geo_lo(gv);
     double C, wdW, alpha, gamma;
-    if constexpr (CACHED) {
+    if constexpr (CACHED && STAGED) {
+      alpha = so.sc0;
+      gamma = so.sc1;
+      C = so.sc2;
+      wdW = so.nc0;
+    } else if constexpr (CACHED) {
       const double* sc3 = a.scache + 3 * o;
       alpha = sc3[0];
       gamma = sc3[1];
@@ -750,26 +763,38 @@ __device__ __forceinline__ void dp_node(const DPArgs& a, const DevTables& s, con
       const double R = lenf * s.unit_r[l];
       C = lenf * s.unit_c[l];
       const double Ch = lenf * s.half_c[l];
-      wdW = a.w_d * a.W[v];
+      wdW = a.w_d * (STAGED ? so.nc0 : a.W[v]);
       alpha = wdW * R;
       gamma = fma(alpha, Ch, a.w_cap * C);
     }
-    const int nldd = s.nld[d];
-    const int64_t pb = s.grid_off[d] + int64_t(line) * s.npos[d] * nldd + ldi;
-    const int64_t K = a.P[pb + int64_t(lo + len) * nldd] - a.P[pb + int64_t(lo) * nldd];
+    int64_t K;
+    if constexpr (STAGED) {
+      K = so.Kseg;
+    } else {
+      const int nldd = s.nld[d];
+      const int64_t pb = s.grid_off[d] + int64_t(line) * s.npos[d] * nldd + ldi;
+      K = a.P[pb + int64_t(lo + len) * nldd] - a.P[pb + int64_t(lo) * nldd];
+    }
     const double seg = fma(a.w_cong_s, penalty_to_double(K), gamma);
     const double Av = fma(alpha, cv, fv + seg);
     const double ccv = C + cv;
     a.A[o] = Av;
     a.Cc[o] = ccv;
     a.M[o] = wdW * ccv;
-    const int p = a.parent_g[v];
-    a.B[o] = fma(CACHED ? a.nround[2 * int64_t(p)] : a.w_d * a.rho[p], ccv, Av);
+    double rp;
+    if constexpr (STAGED) {
+      rp = CACHED ? so.rp : a.w_d * so.rp;
+    } else {
+      const int p = a.parent_g[v];
+      rp = CACHED ? a.nround[2 * int64_t(p)] : a.w_d * a.rho[p];
+    }
+    a.B[o] = fma(rp, ccv, Av);
   }
 }
 
-// Leaves and one-son nodes fit 64 registers (4 blocks of 256 per SM); the
-// several-sons case keeps 2 blocks.
+// Leaves and one-son nodes fit 64 registers (4 blocks of 256 per SM), the
+// bends 48 (5 blocks); the several-sons case keeps 3 blocks (capping it at
+// 5 blocks of 32 x LD threads spilled and ran 15% slower).
 template <int LMAX, int LDM, int DEG, bool ROOT, bool CACHED, int PINK>
 __global__ void __launch_bounds__(256, (DEG == 1 && !ROOT && PINK == 0 ? 5 : (DEG <= 1 ? 4 : 3))) k_dp_level(LayerInfo li, DPArgs a) {
   __shared__ DevTables s;
@@ -782,11 +807,11 @@ __global__ void __launch_bounds__(256, (DEG == 1 && !ROOT && PINK == 0 ? 5 : (DE
     // float bounds of its B and M; the block's threads bound the Rvia table
     __shared__ double s_son[4][256];
     __shared__ float s_sf[4][256];
-    __shared__ float s_rf[2][kMaxL * kMaxL];
+    __shared__ float s_rf[2][kMaxL * kRvStride];  // odd row stride: a node's threads (rows l) on distinct banks
     __shared__ long long s_key[PINK == 0 ? LDM : 1][256];
-    const int LD = a.LD, npb = 256 / LD, L = li.L;
-    for (int i = threadIdx.x; i < L * L; i += blockDim.x) {
-      const float r = f32_lo(s.rv[(i / L) * kRvStride + i % L]);
+    const int LD = a.LD, npb = 256 / LD;
+    for (int i = threadIdx.x; i < kMaxL * kRvStride; i += blockDim.x) {
+      const float r = f32_lo(s.rv[i]);
       s_rf[0][i] = r;
       s_rf[1][i] = f32_up(r);
     }
@@ -799,6 +824,36 @@ __global__ void __launch_bounds__(256, (DEG == 1 && !ROOT && PINK == 0 ? 5 : (DE
     so.rlo = s_rf[0];
     so.rup = s_rf[1];
     if (in) {
+      // the thread's own loads first, so that their latency overlaps the
+      // staging of the son's row
+      const uint64_t gv = a.geo[v];
+      const int d = geo_dir(gv), nldd = s.nld[d];
+      so.gv = gv;
+      so.pin = PINK == 0 ? -1 : a.pin[v];
+      if constexpr (PINK == 1) so.Cs = a.sink_cap[v];
+      const int p = a.parent_g[v];
+      if constexpr (CACHED) {
+        so.nc0 = a.ncache[2 * int64_t(v)];
+        so.nc1 = a.ncache[2 * int64_t(v) + 1];
+        so.nr0 = a.nround[2 * int64_t(v)];
+        so.nr1 = a.nround[2 * int64_t(v) + 1];
+        so.rp = a.nround[2 * int64_t(p)];
+      } else {
+        so.nc0 = a.W[v];
+        so.nc1 = a.kappa[v];
+        so.nr0 = a.rho[v];
+        so.rp = a.rho[p];
+      }
+      if (ldi < nldd) {
+        if constexpr (CACHED) {
+          const double* sc3 = a.scache + 3 * (int64_t(v) * LD + ldi);
+          so.sc0 = sc3[0];
+          so.sc1 = sc3[1];
+          so.sc2 = sc3[2];
+        }
+        const int64_t pb = s.grid_off[d] + int64_t(geo_line(gv)) * s.npos[d] * nldd + ldi;
+        so.Kseg = a.P[pb + int64_t(geo_lo(gv) + geo_len(gv)) * nldd] - a.P[pb + int64_t(geo_lo(gv)) * nldd];
+      }
       so.c = a.child_list[a.child_start[v]];
       so.dc = geo_dir(a.geo[so.c]);
       const int64_t o = int64_t(so.c) * LD + ldi;
