@@ -618,7 +618,7 @@ la_status la_load_nets(la_ctx* c, const la_net_desc* nd) {
   // internal order
   GETK(nf.root_of_net, N); GETK(nf.parent_g, V); GETK(nf.net_of, V); GETK(nf.pin, V); GETK(nf.sink_cap, V);
   GETK(nf.kappa, V); GETK(nf.gk, V); GETK(nf.geo, V); GETK(nf.child_start, V); GETK(nf.nch, V);
-  GETK(nf.child_list, V); GETK(nf.W_eq4, V); GETK(nf.rho_eq4, V);
+  GETK(nf.child_list, V); GETK(nf.son0, V); GETK(nf.W_eq4, V); GETK(nf.rho_eq4, V);
   GETK(nf.A, V * LD); GETK(nf.Cc, V * LD); GETK(nf.M, V * LD); GETK(nf.B, V * LD); GETK(nf.sb, V * LD);
   GETK(nf.st, V * LD); GETK(nf.ent, V * LD); GETK(nf.Jroot, V); GETK(nf.layer, V); GETK(nf.b, V); GETK(nf.t, V);
   GETK(nf.s0, V); GETK(nf.s1, V); GETK(nf.s2, V); GETK(nf.s3, V); GETK(nf.s4, V); GETK(nf.W_adj, V);
@@ -633,14 +633,15 @@ la_status la_load_nets(la_ctx* c, const la_net_desc* nd) {
     // every array the kernels below and the rounds use must exist
     const void* need[] = {nf.net_ptr, nf.r_drv, nf.lvl_nodes, nf.bl_nodes, nf.bl_hoff, nf.net_H, nf.queue_ctr,
                           nf.big_queue, nf.root_of_net, nf.parent_g, nf.net_of, nf.pin, nf.sink_cap, nf.kappa,
-                          nf.gk, nf.geo, nf.child_start, nf.nch, nf.child_list, nf.W_eq4, nf.rho_eq4, nf.A, nf.Cc,
+                          nf.gk, nf.geo, nf.child_start, nf.nch, nf.child_list, nf.son0, nf.W_eq4, nf.rho_eq4, nf.A, nf.Cc,
                           nf.M, nf.B, nf.sb, nf.st, nf.ent, nf.Jroot, nf.layer, nf.b, nf.t, nf.s0, nf.s1, nf.s2,
                           nf.s3, nf.s4, nf.W_adj, nf.rho_adj, nf.red, in2int};
     for (const void* q : need)
       if (!q) return fail(set_err(c, LA_ERR_STATE, "la_load_nets: internal allocation missing"));
   }
   launch_renumber(tf, in2int, key_of, int64_t(nbk), nf, s);
-  ++c->launches;
+  launch_first_son(nf, s);
+  c->launches += 2;
   {
     // the segments by (direction, line), for the demand pass
     const int nl0 = c->grid.li.nlines[0], nkeys = nl0 + c->grid.li.nlines[1];
@@ -732,7 +733,7 @@ static uint64_t round_signature(la_ctx* c, int si, const double* W, const double
   const BatchPlan& bp = c->plan;
   const void* ptrs[] = {f.bl_nodes, f.bl_hoff, f.net_H, f.big_queue, f.queue_ctr, f.net_ptr, f.root_of_net,
                         f.parent_g, f.net_of, f.pin, f.sink_cap, f.kappa, f.gk, f.r_drv, f.geo, f.child_start,
-                        f.nch, f.child_list, f.W_eq4, f.rho_eq4, f.W_adj, f.rho_adj, f.A, f.Cc, f.M, f.B,
+                        f.nch, f.child_list, f.son0, f.W_eq4, f.rho_eq4, f.W_adj, f.rho_adj, f.A, f.Cc, f.M, f.B,
                         f.ncache[si], f.scache[si], f.sb, f.st, f.ent, f.Jroot, f.layer, f.b, f.t, f.red,
                         f.seg_node, f.seg_geo, f.seg_off, f.range_tab, f.layer_old,
                         g.cap, g.D, g.H, g.diff, g.P, g.T_dev, g.tofT_dev, g.tab_dev, c->d_stats, c->d_err};

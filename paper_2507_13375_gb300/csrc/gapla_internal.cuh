@@ -146,6 +146,7 @@ struct Forest {
   int32_t* child_start = nullptr;       // first son slot in child_list
   int32_t* nch = nullptr;               // number of sons
   int32_t* child_list = nullptr;        // son ids, increasing within a parent
+  int32_t* son0 = nullptr;              // internal order: the first son's id (-1 at a leaf)
   int32_t* height = nullptr;
   int32_t* lvl_nodes = nullptr;         // internal -> input node id
   double* W_eq4 = nullptr;
@@ -312,6 +313,8 @@ void launch_check_assignment(la_ctx* c, const int8_t* layer, const int8_t* b, co
 // out.lvl_nodes[internal id] = input id
 void launch_renumber(const Forest& in, const int32_t* in2int, const int32_t* key_of, int64_t nkeys, Forest& out,
                      cudaStream_t s);
+// f.son0[v] = f.child_list[f.child_start[v]] (-1 without sons), internal order
+void launch_first_son(const Forest& f, cudaStream_t s);
 // dst[i] = src[perm[i]] (gather into internal order) or dst[perm[i]] = src[i] (scatter)
 void launch_permute8(int64_t V, const int32_t* perm, const int8_t* src, int8_t* dst, bool gather, cudaStream_t s);
 void launch_permute64(int64_t V, const int32_t* perm, const double* src, double* dst, bool gather, cudaStream_t s);

@@ -665,6 +665,19 @@ void launch_renumber(const Forest& in, const int32_t* in2int, const int32_t* key
   }
 }
 
+// The first son of every node (internal order), so that a one-son node reaches
+// its son's table row in one dependent load instead of two.
+__global__ void k_first_son(int64_t V, const int32_t* __restrict__ child_start, const int32_t* __restrict__ nch,
+                            const int32_t* __restrict__ child_list, int32_t* __restrict__ son0) {
+  const int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (v >= V) return;
+  son0[v] = nch[v] > 0 ? child_list[child_start[v]] : -1;
+}
+
+void launch_first_son(const Forest& f, cudaStream_t s) {
+  k_first_son<<<(unsigned)((f.V + 255) / 256), 256, 0, s>>>(f.V, f.child_start, f.nch, f.child_list, f.son0);
+}
+
 // One thread per net of size class >= kMinBigSc: a stable counting sort of
 // its nodes by height (internal ids), and the net's height.
 __global__ void k_net_levels(int64_t N, const int64_t* __restrict__ net_ptr, const int32_t* __restrict__ height,

@@ -367,7 +367,7 @@ struct DPArgs {
   int LD;
   int64_t base;          // first node of the (level, class) bucket
   int64_t count;
-  const int32_t *parent_g, *child_start, *nch, *child_list;
+  const int32_t *parent_g, *child_start, *nch, *child_list, *son0;
   const int8_t* pin;
   const double *sink_cap, *kappa, *W, *rho;
   const uint64_t* geo;
@@ -854,7 +854,7 @@ __global__ void __launch_bounds__(256, (DEG == 1 && !ROOT && PINK == 0 ? 5 : (DE
         const int64_t pb = s.grid_off[d] + int64_t(geo_line(gv)) * s.npos[d] * nldd + ldi;
         so.Kseg = a.P[pb + int64_t(geo_lo(gv) + geo_len(gv)) * nldd] - a.P[pb + int64_t(geo_lo(gv)) * nldd];
       }
-      so.c = a.child_list[a.child_start[v]];
+      so.c = a.son0[v];
       so.dc = geo_dir(a.geo[so.c]);
       const int64_t o = int64_t(so.c) * LD + ldi;
       const double Bo = a.B[o], Mo = a.M[o];
@@ -1135,6 +1135,7 @@ static DPArgs dp_args(la_ctx* c, const RoundW& w, const double* W, const double*
   DPArgs a;
   a.LD = c->LD;
   a.parent_g = f.parent_g; a.child_start = f.child_start; a.nch = f.nch; a.child_list = f.child_list;
+  a.son0 = f.son0;
   a.pin = f.pin; a.sink_cap = f.sink_cap; a.kappa = f.kappa; a.W = W; a.rho = rho; a.geo = f.geo;
   a.P = c->grid.P; a.tab = c->grid.tab_dev;
   a.A = f.A; a.Cc = f.Cc; a.M = f.M; a.B = f.B; a.Jroot = f.Jroot; a.sb = f.sb; a.st = f.st; a.ent = f.ent;
