@@ -478,7 +478,7 @@ def bench_gpu(args):
     out_host = [torch.empty(V, dtype=torch.int8).pin_memory() for _ in range(3)]
     h2d = sum_over_ranks(sum(t.numel() * t.element_size() for t in host.values()), dist, red_dev)
     d2h = sum_over_ranks(3 * V, dist, red_dev)
-    e2e_steps = max(1, min(args.steps, 3))
+    e2e_steps = max(1, args.steps)
     # the host-to-device copies spread over four streams (several copy engines)
     main_s = torch.cuda.current_stream()
     copy_s = [torch.cuda.Stream() for _ in range(4)]

@@ -41,7 +41,7 @@ void launch_rc_from_assignment(la_ctx* c, double* R, double* C, const int32_t* p
 }
 
 struct ElmArgs {
-  const int32_t *parent_g, *child_start, *nch, *child_list, *net_of;
+  const int32_t *parent_g, *child_start, *nch, *child_list, *son0, *net_of;
   const uint64_t* geo;  // R or C null: R_seg / C_seg from the geometry and the layer
   const int32_t* out_perm;  // k_elm_delay: delay[out_perm[v]] (input order), or delay[v]
   int64_t base, count;
@@ -87,8 +87,13 @@ __global__ void k_elm_up(ElmArgs a) {
   double s = hcv;
   s = s + a.vck[a.t[v] - a.b[v]];
   if (a.pin[v] >= 0) s = s + a.sink_cap[v];
-  const int cs = a.child_start[v], nc = a.nch[v];
-  for (int j = 0; j < nc; ++j) {
+  // the first son straight from son0 (one dependent load instead of two),
+  // the others from the son list
+  const int nc = a.nch[v];
+  const int c0 = a.son0[v];
+  if (nc > 0) s = s + (a.CX ? a.CX[c0] : half_exact(seg_c(a, c0)) + a.CdJ[c0]);
+  const int cs = nc > 1 ? a.child_start[v] : 0;
+  for (int j = 1; j < nc; ++j) {
     const int c = a.child_list[cs + j];
     s = s + (a.CX ? a.CX[c] : half_exact(seg_c(a, c)) + a.CdJ[c]);
   }
@@ -96,7 +101,8 @@ __global__ void k_elm_up(ElmArgs a) {
   if (a.CX) a.CX[v] = hcv + s;
   if (a.Ws) {
     double w = a.g[v];
-    for (int j = 0; j < nc; ++j) w = w + a.Ws[a.child_list[cs + j]];
+    if (nc > 0) w = w + a.Ws[c0];
+    for (int j = 1; j < nc; ++j) w = w + a.Ws[a.child_list[cs + j]];
     a.Ws[v] = w;
   }
 }
@@ -107,9 +113,11 @@ __global__ void k_wsum(ElmArgs a) {
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= a.count) return;
   const int v = int(a.base + i);
-  const int cs = a.child_start[v], nc = a.nch[v];
+  const int nc = a.nch[v];
   double w = a.g[v];
-  for (int j = 0; j < nc; ++j) w = w + a.Ws[a.child_list[cs + j]];
+  if (nc > 0) w = w + a.Ws[a.son0[v]];
+  const int cs = nc > 1 ? a.child_start[v] : 0;
+  for (int j = 1; j < nc; ++j) w = w + a.Ws[a.child_list[cs + j]];
   a.Ws[v] = w;
 }
 
@@ -161,6 +169,7 @@ static ElmArgs elm_args(la_ctx* c, const double* R, const double* C) {
   Forest& f = c->forest;
   ElmArgs a{};
   a.parent_g = f.parent_g; a.child_start = f.child_start; a.nch = f.nch; a.child_list = f.child_list;
+  a.son0 = f.son0;
   a.net_of = f.net_of; a.layer = f.layer; a.b = f.b; a.t = f.t; a.pin = f.pin; a.sink_cap = f.sink_cap;
   a.r_drv = f.r_drv; a.R = R; a.C = C; a.tab = c->grid.tab_dev; a.geo = f.geo;
   for (int k = 0; k < kMaxL; ++k) a.vck[k] = c->grid.li.via_c * double(k);

@@ -799,22 +799,18 @@ template <int LMAX, int LDM, int DEG, bool ROOT, bool CACHED, int PINK>
 __global__ void __launch_bounds__(256, (DEG == 1 && !ROOT && PINK == 0 ? 5 : (DEG <= 1 ? 4 : 3))) k_dp_level(LayerInfo li, DPArgs a) {
   __shared__ DevTables s;
   __shared__ RoundTabs rt;
-  load_round_tabs(rt, a, li.via_c);
-  load_tables(s, a.tab);
   if constexpr (DEG == 1 && !ROOT) {
     // whole nodes per block (256 / LD of them): the node's threads copy the
     // son's table row to shared memory, one entry each per array, with
-    // float bounds of its B and M; the block's threads bound the Rvia table
+    // float bounds of its B and M; the block's threads bound the Rvia table.
+    // The node's own loads and its son's row are issued before the block
+    // copies the grid tables, so that their latencies overlap (the line
+    // geometry of the prefix index comes from the kernel's LayerInfo).
     __shared__ double s_son[4][256];
     __shared__ float s_sf[4][256];
     __shared__ float s_rf[2][kMaxL * kRvStride];  // odd row stride: a node's threads (rows l) on distinct banks
     __shared__ long long s_key[PINK == 0 ? LDM : 1][256];
     const int LD = a.LD, npb = 256 / LD;
-    for (int i = threadIdx.x; i < kMaxL * kRvStride; i += blockDim.x) {
-      const float r = f32_lo(s.rv[i]);
-      s_rf[0][i] = r;
-      s_rf[1][i] = f32_up(r);
-    }
     const int gi = int(threadIdx.x) / LD, ldi = int(threadIdx.x) - gi * LD;
     const int64_t node_i = int64_t(blockIdx.x) * npb + gi;
     const bool in = gi < npb && node_i < a.count;
@@ -823,11 +819,11 @@ __global__ void __launch_bounds__(256, (DEG == 1 && !ROOT && PINK == 0 ? 5 : (DE
     so.K = &s_key[0][threadIdx.x];
     so.rlo = s_rf[0];
     so.rup = s_rf[1];
+    double Bo = 0.0, Mo = 0.0, Ao = 0.0, Cco = 0.0;
     if (in) {
-      // the thread's own loads first, so that their latency overlaps the
-      // staging of the son's row
       const uint64_t gv = a.geo[v];
-      const int d = geo_dir(gv), nldd = s.nld[d];
+      const int d = geo_dir(gv);
+      const int nldd = d ? li.nld[1] : li.nld[0];
       so.gv = gv;
       so.pin = PINK == 0 ? -1 : a.pin[v];
       if constexpr (PINK == 1) so.Cs = a.sink_cap[v];
@@ -851,17 +847,30 @@ __global__ void __launch_bounds__(256, (DEG == 1 && !ROOT && PINK == 0 ? 5 : (DE
           so.sc1 = sc3[1];
           so.sc2 = sc3[2];
         }
-        const int64_t pb = s.grid_off[d] + int64_t(geo_line(gv)) * s.npos[d] * nldd + ldi;
+        const int64_t pb = (d ? li.grid_off[1] : li.grid_off[0]) +
+                           int64_t(geo_line(gv)) * (d ? li.npos[1] : li.npos[0]) * nldd + ldi;
         so.Kseg = a.P[pb + int64_t(geo_lo(gv) + geo_len(gv)) * nldd] - a.P[pb + int64_t(geo_lo(gv)) * nldd];
       }
       so.c = a.son0[v];
       so.dc = geo_dir(a.geo[so.c]);
       const int64_t o = int64_t(so.c) * LD + ldi;
-      const double Bo = a.B[o], Mo = a.M[o];
+      Bo = a.B[o];
+      Mo = a.M[o];
+      Ao = a.A[o];
+      Cco = a.Cc[o];
+    }
+    load_round_tabs(rt, a, li.via_c);
+    load_tables(s, a.tab);
+    for (int i = threadIdx.x; i < kMaxL * kRvStride; i += blockDim.x) {
+      const float r = f32_lo(s.rv[i]);
+      s_rf[0][i] = r;
+      s_rf[1][i] = f32_up(r);
+    }
+    if (in) {
       s_son[0][threadIdx.x] = Bo;
       s_son[1][threadIdx.x] = Mo;
-      s_son[2][threadIdx.x] = a.A[o];
-      s_son[3][threadIdx.x] = a.Cc[o];
+      s_son[2][threadIdx.x] = Ao;
+      s_son[3][threadIdx.x] = Cco;
       const float bl = f32_lo(Bo), ml = f32_lo(Mo);
       s_sf[0][threadIdx.x] = bl;
       s_sf[1][threadIdx.x] = f32_up(bl);
@@ -875,6 +884,8 @@ __global__ void __launch_bounds__(256, (DEG == 1 && !ROOT && PINK == 0 ? 5 : (DE
     if (!in) return;
     dp_node<LMAX, LDM, DEG, ROOT, CACHED, PINK, true>(a, s, rt, li.L, v, ldi, so);
   } else if constexpr (DEG == 2 && !ROOT && LDM <= 8) {
+    load_round_tabs(rt, a, li.via_c);
+    load_tables(s, a.tab);
     // 32 nodes per block of 32 x LD threads, warp w evaluating candidate
     // index w of each: a warp's threads share l, so the scans over the stack
     // tops above it have one length per warp
@@ -885,6 +896,8 @@ __global__ void __launch_bounds__(256, (DEG == 1 && !ROOT && PINK == 0 ? 5 : (DE
     __shared__ int8_t s_ch[kRecSons * LMAX * 256];
     dp_node<LMAX, LDM, DEG, ROOT, CACHED, PINK>(a, s, rt, li.L, int(a.base + node_i), ldi, Son1{}, s_keyL, s_ch);
   } else {
+    load_round_tabs(rt, a, li.via_c);
+    load_tables(s, a.tab);
     // a node's candidate layers side by side (they share its sons' rows)
     const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     const int64_t node_i = ROOT ? k : k / a.LD;
