@@ -450,7 +450,18 @@ struct Son1 {
   int pin;
   double Cs, nc0, nc1, nr0, nr1, rp, sc0, sc1, sc2;
   long long Kseg;  // P[end] - P[start]: the segment's penalty sum on the candidate layer
+  // several sons, staged (SSON): son j < kStageSons of the thread's node in
+  // shared memory, its id at sc[j * 32], direction at sd[j * 32], B and M
+  // rows at sB / sM + (j * LDM + jj) * 32 (the pointers already offset by
+  // the node's lane)
+  const int* sc;
+  const int8_t* sd;
+  const double *sB, *sM;
 };
+
+// Sons of a several-son node staged in shared memory by its block (the
+// first kStageSons of each node; most several-son nodes have two).
+constexpr int kStageSons = 2;
 // One son of a several-son node in the scan of the stacks with bottom b: its
 // keys on its own direction's layers go to keyL by layer ([t][thread], the
 // other layers hold LLONG_MAX), then for every top t = hi_req + i (i < nt) its
@@ -459,20 +470,17 @@ struct Son1 {
 // layer keeps a tie.  The loop over tops ends at the last one, so threads
 // with the same hi_req run it the same number of times.
 template <int LMAX, int LDM, bool FIRST>
-__device__ __forceinline__ void son_scan(const DPArgs& a, const DevTables& s, const double* rvl, int c, int b,
-                                         int hi_req, int nt, long long* keyL, int8_t* chj, double (&S)[LMAX],
-                                         unsigned& okm) {
-  const int dc = geo_dir(a.geo[c]);
+__device__ __forceinline__ void son_scan(const DevTables& s, const double* rvl, int dc, const double* Bc,
+                                         const double* Mc, int str, int b, int hi_req, int nt, long long* keyL,
+                                         int8_t* chj, double (&S)[LMAX], unsigned& okm) {
   const int nldc = s.nld[dc];
-  const double* Bc = a.B + int64_t(c) * a.LD;
-  const double* Mc = a.M + int64_t(c) * a.LD;
 #pragma unroll
   for (int t = 0; t < LMAX; ++t) keyL[t * 256] = LLONG_MAX;
 #pragma unroll
   for (int jj = 0; jj < LDM; ++jj) {
     if (jj < nldc) {
       const int lc = s.lay[dc][jj];
-      keyL[lc * 256] = dbits(fma(Mc[jj], rvl[lc], Bc[jj]));
+      keyL[lc * 256] = dbits(fma(Mc[jj * str], rvl[lc], Bc[jj * str]));
     }
   }
   long long rbits = LLONG_MAX;
@@ -493,11 +501,32 @@ __device__ __forceinline__ void son_scan(const DPArgs& a, const DevTables& s, co
   }
 }
 
-template <int LMAX, int LDM, int DEG, bool ROOT, bool CACHED, int PINK, bool STAGED = false>
+// Son j of a several-son node: its id, direction and B, M rows (stride str):
+// staged in shared memory for j < kStageSons (SSON), else from the tables.
+template <int LDM, bool SSON>
+__device__ __forceinline__ void son_row(const DPArgs& a, const Son1& so, int cs, int j, int& c, int& dc,
+                                        const double*& Bc, const double*& Mc, int& str) {
+  if (SSON && j < kStageSons) {
+    c = so.sc[j * 32];
+    dc = so.sd[j * 32];
+    Bc = so.sB + j * LDM * 32;
+    Mc = so.sM + j * LDM * 32;
+    str = 32;
+  } else {
+    c = a.child_list[cs + j];
+    dc = geo_dir(a.geo[c]);
+    Bc = a.B + int64_t(c) * a.LD;
+    Mc = a.M + int64_t(c) * a.LD;
+    str = 1;
+  }
+}
+
+template <int LMAX, int LDM, int DEG, bool ROOT, bool CACHED, int PINK, bool STAGED = false, bool SSON = false>
 __device__ __forceinline__ void dp_node(const DPArgs& a, const DevTables& s, const RoundTabs& rt, int L, int v,
                                         int ldi, const Son1& so = Son1{}, long long* keybuf = nullptr,
                                         int8_t* chbuf = nullptr) {
   static_assert(!STAGED || (DEG == 1 && !ROOT), "staged son rows are for one-son non-root nodes");
+  static_assert(!SSON || (DEG == 2 && !ROOT), "staged sons are for several-son non-root nodes");
   const int LD = a.LD;
   const int pin = PINK == 0 ? -1 : (STAGED ? so.pin : a.pin[v]);
   const uint64_t gv = STAGED ? so.gv : a.geo[v];
@@ -679,10 +708,16 @@ __device__ __forceinline__ void dp_node(const DPArgs& a, const DevTables& s, con
       unsigned okm = ~0u;  // bit i: every son has a layer in [b, hi_req + i]
 #pragma unroll
       for (int i = 0; i < LMAX; ++i) S[i] = 0.0;
-      son_scan<LMAX, LDM, true>(a, s, rvl, a.child_list[cs], b, hi_req, nt, keyL, rec ? chL : nullptr, S, okm);
-      for (int j = 1; j < nc; ++j)
-        son_scan<LMAX, LDM, false>(a, s, rvl, a.child_list[cs + j], b, hi_req, nt, keyL,
-                                   rec ? chL + j * LMAX * 256 : nullptr, S, okm);
+      for (int j = 0; j < nc; ++j) {
+        int c, dc, str;
+        const double *Bc, *Mc;
+        son_row<LDM, SSON>(a, so, cs, j, c, dc, Bc, Mc, str);
+        if (j == 0)
+          son_scan<LMAX, LDM, true>(s, rvl, dc, Bc, Mc, str, b, hi_req, nt, keyL, rec ? chL : nullptr, S, okm);
+        else
+          son_scan<LMAX, LDM, false>(s, rvl, dc, Bc, Mc, str, b, hi_req, nt, keyL,
+                                     rec ? chL + j * LMAX * 256 : nullptr, S, okm);
+      }
 #pragma unroll
       for (int i = 0; i < LMAX; ++i) {
         if (i >= nt) break;
@@ -696,11 +731,10 @@ __device__ __forceinline__ void dp_node(const DPArgs& a, const DevTables& s, con
     // each son's layer inside the winning stack (its own layers, ascending:
     // the lowest layer wins ties)
     for (int j = 0; j < nc; ++j) {
-      const int c = a.child_list[cs + j];
-      const int dc = geo_dir(a.geo[c]);
+      int c, dc, str;
+      const double *Bc, *Mc;
+      son_row<LDM, SSON>(a, so, cs, j, c, dc, Bc, Mc, str);
       const int nldc = s.nld[dc];
-      const double* Bc = a.B + int64_t(c) * LD;
-      const double* Mc = a.M + int64_t(c) * LD;
       long long rbits = LLONG_MAX;
       int rj = -1;
       if (rec) {
@@ -711,7 +745,7 @@ __device__ __forceinline__ void dp_node(const DPArgs& a, const DevTables& s, con
           if (jj < nldc) {
             const int lc = s.lay[dc][jj];
             if (lc >= bb && lc <= bt) {
-              const long long kb = dbits(fma(Mc[jj], rvl[lc], Bc[jj]));
+              const long long kb = dbits(fma(Mc[jj * str], rvl[lc], Bc[jj * str]));
               if (rj < 0 || kb < rbits) { rj = jj; rbits = kb; }
             }
           }
@@ -723,7 +757,7 @@ __device__ __forceinline__ void dp_node(const DPArgs& a, const DevTables& s, con
       }
       const int rl = s.lay[dc][rj];
       a.ent[int64_t(c) * LD + ldi] = int8_t(rl);
-      const double g = fma(Mc[rj], rvl[rl], a.A[int64_t(c) * LD + rj]);
+      const double g = fma(Mc[rj * str], rvl[rl], a.A[int64_t(c) * LD + rj]);
       sg = j == 0 ? g : sg + g;
       sc = j == 0 ? a.Cc[int64_t(c) * LD + rj] : sc + a.Cc[int64_t(c) * LD + rj];
     }
@@ -884,17 +918,61 @@ __global__ void __launch_bounds__(256, (DEG == 1 && !ROOT && PINK == 0 ? 5 : (DE
     if (!in) return;
     dp_node<LMAX, LDM, DEG, ROOT, CACHED, PINK, true>(a, s, rt, li.L, v, ldi, so);
   } else if constexpr (DEG == 2 && !ROOT && LDM <= 8) {
-    load_round_tabs(rt, a, li.via_c);
-    load_tables(s, a.tab);
     // 32 nodes per block of 32 x LD threads, warp w evaluating candidate
     // index w of each: a warp's threads share l, so the scans over the stack
-    // tops above it have one length per warp
-    const int ldi = int(threadIdx.x >> 5);
-    const int64_t node_i = int64_t(blockIdx.x) * 32 + (threadIdx.x & 31);
-    if (node_i >= a.count) return;
+    // tops above it have one length per warp.  Where the static shared
+    // memory allows it, warp j < kStageSons first copies son j of every
+    // node (id, direction, B and M rows) to shared memory: the sons' rows
+    // are gathered at once, before the grid tables, instead of one son after
+    // another inside the search.
+    constexpr bool kSt = size_t(LMAX) * 256 * 8 + size_t(kRecSons) * LMAX * 256 + 2 * kStageSons * LDM * 32 * 8 +
+                             sizeof(DevTables) + sizeof(RoundTabs) + 512 <= 48 * 1024;
+    const int ldi = int(threadIdx.x >> 5), lane = int(threadIdx.x & 31);
+    const int64_t node_i = int64_t(blockIdx.x) * 32 + lane;
+    const bool in = node_i < a.count;
     __shared__ long long s_keyL[LMAX * 256];
     __shared__ int8_t s_ch[kRecSons * LMAX * 256];
-    dp_node<LMAX, LDM, DEG, ROOT, CACHED, PINK>(a, s, rt, li.L, int(a.base + node_i), ldi, Son1{}, s_keyL, s_ch);
+    __shared__ double s_sr[kSt ? 2 * kStageSons * LDM * 32 : 1];
+    __shared__ int s_sc[kSt ? kStageSons * 32 : 1];
+    __shared__ int8_t s_sd[kSt ? kStageSons * 32 : 1];
+    Son1 so{};
+    if constexpr (kSt) {
+      // warp w stages sons w, w + LD, ... (a block of one warp stages both)
+      for (int j = ldi; j < kStageSons; j += a.LD) {
+        int c = -1;
+        if (in) {
+          const int v = int(a.base + node_i);
+          if (a.nch[v] > j) c = a.child_list[a.child_start[v] + j];
+        }
+        s_sc[j * 32 + lane] = c;
+        if (c >= 0) {
+          const int dc = geo_dir(a.geo[c]);
+          const double* Bc = a.B + int64_t(c) * a.LD;
+          const double* Mc = a.M + int64_t(c) * a.LD;
+          double rb[LDM], rm[LDM];
+#pragma unroll
+          for (int jj = 0; jj < LDM; ++jj) {
+            rb[jj] = jj < a.LD ? Bc[jj] : 0.0;
+            rm[jj] = jj < a.LD ? Mc[jj] : 0.0;
+          }
+          s_sd[j * 32 + lane] = int8_t(dc);
+#pragma unroll
+          for (int jj = 0; jj < LDM; ++jj) {
+            s_sr[(j * LDM + jj) * 32 + lane] = rb[jj];
+            s_sr[((kStageSons + j) * LDM + jj) * 32 + lane] = rm[jj];
+          }
+        }
+      }
+      so.sc = s_sc + lane;
+      so.sd = s_sd + lane;
+      so.sB = s_sr + lane;
+      so.sM = s_sr + kStageSons * LDM * 32 + lane;
+    }
+    load_round_tabs(rt, a, li.via_c);
+    load_tables(s, a.tab);
+    if (!in) return;
+    dp_node<LMAX, LDM, DEG, ROOT, CACHED, PINK, false, kSt>(a, s, rt, li.L, int(a.base + node_i), ldi, so, s_keyL,
+                                                            s_ch);
   } else {
     load_round_tabs(rt, a, li.via_c);
     load_tables(s, a.tab);
