@@ -365,6 +365,7 @@ void launch_local_demand(la_ctx* c, double hist_w, double* tof_part, cudaStream_
 // ---------------------------------------------------------------------------
 struct DPArgs {
   int LD;
+  int ld_magic;          // ceil(2^16 / LD): t / LD = (t ld_magic) >> 16 for 0 <= t < 256
   int64_t base;          // first node of the (level, class) bucket
   int64_t count;
   const int32_t *parent_g, *child_start, *nch, *child_list, *son0;
@@ -599,27 +600,33 @@ __device__ __forceinline__ void dp_node(const DPArgs& a, const DevTables& s, con
       }
       const float* rlo = so.rlo + l * kRvStride;
       const float* rup = so.rup + l * kRvStride;
-      float best_up = INFINITY, lo1 = INFINITY, lo2 = INFINITY;
-      int jb = -1, jlo = -1;
+      // Only the least lower bound can win: a j whose upper bound is below
+      // every other lower bound has the least lower bound itself.  So the
+      // lower bounds of every j, then the upper bound of the first least one
+      // (jlo) against the second least lower bound (lo2).
+      float lo1 = INFINITY, lo2 = INFINITY;
+      int jlo = -1;
 #pragma unroll
       for (int j = 0; j < LDM; ++j) {
         if (j < nldc) {
           const int lc = s.lay[dc][j];
           const float kf = float(max(hi_req, lc) - min(lo_req, lc));
           const float klo = __fmaf_rd(so.Mlo[j], rlo[lc], so.Blo[j]);
-          const float kup = __fmaf_ru(so.Mup[j], rup[lc], so.Bup[j]);
           const float tlo = PINK == 1 ? __fmaf_rd(kf, slo, zlo) : __fmul_rd(kf, slo);
-          const float tup = PINK == 1 ? __fmaf_ru(kf, sup, zup) : __fmul_ru(kf, sup);
-          const float flo = __fadd_rd(klo, tlo), fup = __fadd_ru(kup, tup);
-          if (fup < best_up) { best_up = fup; jb = j; }
+          const float flo = __fadd_rd(klo, tlo);
           if (flo < lo1) { lo2 = lo1; lo1 = flo; jlo = j; } else if (flo < lo2) { lo2 = flo; }
         }
       }
-      if (jb >= 0 && best_up < (jlo == jb ? lo2 : lo1)) {
-        bj = jb;
-        const int lc = s.lay[dc][jb];
-        bb = min(lo_req, lc);
-        bt = max(hi_req, lc);
+      if (jlo >= 0) {
+        const int lc = s.lay[dc][jlo];
+        const float kf = float(max(hi_req, lc) - min(lo_req, lc));
+        const float kup = __fmaf_ru(so.Mup[jlo], rup[lc], so.Bup[jlo]);
+        const float tup = PINK == 1 ? __fmaf_ru(kf, sup, zup) : __fmul_ru(kf, sup);
+        if (__fadd_ru(kup, tup) < lo2) {
+          bj = jlo;
+          bb = min(lo_req, lc);
+          bt = max(hi_req, lc);
+        }
       }
     }
     if (bj < 0) {
@@ -845,7 +852,8 @@ __global__ void __launch_bounds__(256, (DEG == 1 && !ROOT && PINK == 0 ? 5 : (DE
     __shared__ float s_rf[2][kMaxL * kRvStride];  // odd row stride: a node's threads (rows l) on distinct banks
     __shared__ long long s_key[PINK == 0 ? LDM : 1][256];
     const int LD = a.LD, npb = 256 / LD;
-    const int gi = int(threadIdx.x) / LD, ldi = int(threadIdx.x) - gi * LD;
+    // threadIdx.x / LD as a multiply and shift (exact below 256 for LD <= 16)
+    const int gi = int((threadIdx.x * unsigned(a.ld_magic)) >> 16), ldi = int(threadIdx.x) - gi * LD;
     const int64_t node_i = int64_t(blockIdx.x) * npb + gi;
     const bool in = gi < npb && node_i < a.count;
     const int v = int(a.base + (in ? node_i : 0));
@@ -1225,6 +1233,7 @@ static DPArgs dp_args(la_ctx* c, const RoundW& w, const double* W, const double*
   Forest& f = c->forest;
   DPArgs a;
   a.LD = c->LD;
+  a.ld_magic = (65536 + c->LD - 1) / c->LD;
   a.parent_g = f.parent_g; a.child_start = f.child_start; a.nch = f.nch; a.child_list = f.child_list;
   a.son0 = f.son0;
   a.pin = f.pin; a.sink_cap = f.sink_cap; a.kappa = f.kappa; a.W = W; a.rho = rho; a.geo = f.geo;
