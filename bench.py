@@ -243,6 +243,80 @@ def dp_capture_record(workload_name, forest=None):
                  f"({covered} of {int(forest['num_nodes'])} nodes in the captured classes)")
 
 
+# the DP node-class kernels: k_dp_level<LMAX, LDM, DEG, ROOT, CACHED, PINK>;
+# class = min(sons, 2) + 0 (pin) / 3 (root) / 6 (no pin)
+DP_RECORD_METRICS = ("dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum,"
+                     "sm__inst_executed_pipe_fp64.sum,sm__inst_executed.sum,"
+                     "sm__pipe_fp64_cycles_active.avg.pct_of_peak_sustained_active,launch__grid_size,"
+                     "launch__block_size,sm__warps_active.avg.pct_of_peak_sustained_active,"
+                     "gpu__dram_throughput.avg.pct_of_peak_sustained_elapsed,"
+                     "smsp__issue_active.avg.pct_of_peak_sustained_active,"
+                     "smsp__average_warps_issue_stalled_long_scoreboard_per_issue_active.ratio")
+_UNIT = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "ns": 1e-3, "nsecond": 1e-3, "us": 1.0,
+         "usecond": 1.0, "ms": 1e3, "msecond": 1e3}
+
+
+def write_dp_record(csv_path, workload_name, LD, how, out_path=None):
+    """Turn an ncu CSV of DP node-class launches (the DP_RECORD_METRICS, one
+    row per launch and metric) into the capture record dp_capture_record
+    reads: per class, DRAM bytes and issued FP64 warp instructions per node,
+    with the hash of the DP sources they were taken on.  Nodes per launch
+    follow from the grid: whole nodes of 256 // LD per block for one-son
+    nodes, 32 per block for several-son nodes, 256 / LD for leaves, 256 for
+    roots."""
+    import csv
+    import re
+
+    rows = list(csv.reader(open(csv_path)))
+    hi = next(i for i, r in enumerate(rows) if "Kernel Name" in r and "Metric Name" in r)
+    h = rows[hi]
+    col = {k: h.index(k) for k in ("ID", "Kernel Name", "Metric Name", "Metric Unit", "Metric Value")}
+    launches = {}
+    for r in rows[hi + 1:]:
+        if len(r) < len(h):
+            continue
+        m = re.search(r"k_dp_level<(\d+), (\d+), (\d+), (\d+), (\d+), (\d+)>", r[col["Kernel Name"]])
+        if not m:
+            continue
+        deg, root, pink = int(m.group(3)), int(m.group(4)), int(m.group(6))
+        cls = deg + (3 if root else (0 if pink == 1 else 6))
+        d = launches.setdefault(r[col["ID"]], {"cls": cls, "kernel": "dp_level<%s>" % ",".join(m.groups())})
+        v = float(r[col["Metric Value"]].replace(",", ""))
+        d[r[col["Metric Name"]]] = v * _UNIT.get(r[col["Metric Unit"]], 1.0)
+    per = {}
+    for d in launches.values():
+        g = d["launch__grid_size"]
+        cls = d["cls"]
+        nodes = (g * (256 // LD) if cls in (1, 7) else g * 32 if cls in (2, 8) else g * 256 / LD if cls in (0, 6)
+                 else g * 256)
+        c = per.setdefault(cls, {"kernel": d["kernel"], "launches": 0, "nodes": 0.0, "dram_bytes": 0.0, "us": 0.0,
+                                 "fp64_inst": 0.0, "w": {}})
+        c["launches"] += 1
+        c["nodes"] += nodes
+        c["dram_bytes"] += d["dram__bytes_read.sum"] + d["dram__bytes_write.sum"]
+        c["us"] += d["gpu__time_duration.sum"]
+        c["fp64_inst"] += d["sm__inst_executed_pipe_fp64.sum"]
+        for k, name in (("fp64_pipe_pct", "sm__pipe_fp64_cycles_active.avg.pct_of_peak_sustained_active"),
+                        ("dram_pct", "gpu__dram_throughput.avg.pct_of_peak_sustained_elapsed"),
+                        ("warps_active_pct", "sm__warps_active.avg.pct_of_peak_sustained_active"),
+                        ("issue_active_pct", "smsp__issue_active.avg.pct_of_peak_sustained_active"),
+                        ("long_scoreboard_per_issue",
+                         "smsp__average_warps_issue_stalled_long_scoreboard_per_issue_active.ratio")):
+            c["w"][k] = c["w"].get(k, 0.0) + d[name] * d["gpu__time_duration.sum"]
+    rec = {"workload": workload_name,
+           "bytes_per_node": {str(k): round(c["dram_bytes"] / c["nodes"], 2) for k, c in sorted(per.items())},
+           "fp64_warp_inst_per_node": {str(k): round(c["fp64_inst"] / c["nodes"], 4) for k, c in sorted(per.items())},
+           "source_sha256": dp_source_hash(), "how": how, "captures": {}}
+    for k, c in sorted(per.items()):
+        rec["captures"][str(k)] = dict({"kernel": c["kernel"], "launches": c["launches"], "nodes": int(c["nodes"]),
+                                        "dram_bytes": int(c["dram_bytes"]), "us": round(c["us"], 1)},
+                                       **{n: round(w / c["us"], 2) for n, w in c["w"].items()})
+    out_path = out_path or os.path.join(ROOT, "profiles", "dp_traffic.json")
+    with open(out_path, "w") as fh:
+        json.dump(rec, fh, indent=1)
+    return rec
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -843,10 +917,21 @@ def main():
                          "the NVTX range load_timed)")
     ap.add_argument("--nets", type=int, default=0,
                     help="--profile / --ablation: the workload's shape scaled to this many nets")
+    ap.add_argument("--dp-record", metavar="CSV",
+                    help="write profiles/dp_traffic.json from an ncu CSV of the DP class kernels "
+                         "(--metrics DP_RECORD_METRICS) of a --profile run of --workload")
     ap.add_argument("--ablation", action="store_true",
                     help="look-ahead ablation and w_d x w_cap sweep (quality metrics, not timed)")
     args = ap.parse_args()
-    if args.ablation:
+    if args.dp_record:
+        import forestgen as fg
+
+        wl = fg.WORKLOADS[args.workload]
+        LD = max(sum(1 for d in wl.dirs if d == 0), sum(1 for d in wl.dirs if d == 1))
+        how = (f"ncu --metrics DP_RECORD_METRICS of the DP class kernels of a bench.py --profile run of "
+               f"{wl.name} scaled to {args.nets or wl.num_nets} nets, the steady-state round")
+        print(json.dumps(write_dp_record(args.dp_record, wl.name, LD, how)["bytes_per_node"]))
+    elif args.ablation:
         ablation(args)
     elif args.profile:
         profile_case(args)

@@ -59,3 +59,38 @@ def test_node_class_counts():
     f["pin_layer"] = f["pin_layer"].astype(np.int8)
     c = bench.node_class_counts(f)
     assert list(c) == [2, 0, 0, 0, 2, 0, 0, 2, 0]
+
+
+def test_dp_capture_record_from_ncu_csv(tmp_path):
+    """The capture record from an ncu CSV in ncu's own layout: launches grouped
+    by ID, classes from the template arguments, nodes from the grid, units
+    converted; a launch of another kernel is ignored."""
+    hdr = ["ID", "Process ID", "Process Name", "Host Name", "Kernel Name", "Context", "Stream", "Block Size",
+           "Grid Size", "Device", "CC", "Section Name", "Metric Name", "Metric Unit", "Metric Value"]
+    base = {"dram__bytes_read.sum": ("Mbyte", 1.0), "dram__bytes_write.sum": ("Kbyte", 500.0),
+            "gpu__time_duration.sum": ("us", 10.0), "sm__inst_executed_pipe_fp64.sum": ("inst", 4200.0),
+            "sm__inst_executed.sum": ("inst", 1e5), "launch__grid_size": ("", 100.0), "launch__block_size": ("", 256.0),
+            "sm__pipe_fp64_cycles_active.avg.pct_of_peak_sustained_active": ("%", 40.0),
+            "gpu__dram_throughput.avg.pct_of_peak_sustained_elapsed": ("%", 30.0),
+            "sm__warps_active.avg.pct_of_peak_sustained_active": ("%", 50.0),
+            "smsp__issue_active.avg.pct_of_peak_sustained_active": ("%", 45.0),
+            "smsp__average_warps_issue_stalled_long_scoreboard_per_issue_active.ratio": ("", 7.0)}
+    lines = ['==PROF== Connected to process 1', ",".join(f'"{h}"' for h in hdr)]
+    kernels = {"1": "void k_dp_level<12, 6, 1, 0, 1, 0>(LayerInfo, DPArgs)",   # bends: class 7
+               "2": "void k_dp_level<12, 6, 2, 1, 1, 1>(LayerInfo, DPArgs)",   # root, several sons: class 5
+               "3": "void k_scan_lines<6, 1>(const DevTables *, ScanArgs)"}
+    for i, k in kernels.items():
+        for name, (unit, val) in base.items():
+            row = [i, "1", "python3", "h", k, "1", "7", "(256, 1, 1)", "(100, 1, 1)", "0", "10.3", "m", name, unit,
+                   f"{val:,.1f}"]
+            lines.append(",".join(f'"{x}"' for x in row))
+    p = tmp_path / "dp.csv"
+    p.write_text("\n".join(lines) + "\n")
+    rec = bench.write_dp_record(str(p), "w", 6, "test", out_path=str(tmp_path / "rec.json"))
+    assert sorted(rec["bytes_per_node"]) == ["5", "7"]
+    # 1.5 MB over 100 blocks x 42 nodes (bends) and 100 x 256 roots
+    assert abs(rec["bytes_per_node"]["7"] - 1.5e6 / 4200) < 0.01
+    assert abs(rec["bytes_per_node"]["5"] - 1.5e6 / 25600) < 0.01
+    assert rec["fp64_warp_inst_per_node"]["7"] == 1.0
+    assert rec["captures"]["7"]["us"] == 10.0 and rec["captures"]["7"]["fp64_pipe_pct"] == 40.0
+    assert rec["source_sha256"] == bench.dp_source_hash()
