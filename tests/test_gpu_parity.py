@@ -291,6 +291,42 @@ def _rounds(a, la, mode, n, weights=None, adjoint=False, tail_threshold=0):
     return out
 
 
+@pytest.mark.parametrize("mode", ["plain", "batched"])
+def test_pins_on_upper_layers(la, mode):
+    """Every pin on a random layer (the generator puts them on layer 0): a
+    several-son node with a pin above layer 0 and a root whose driver pin is
+    there enumerate several stack bottoms (the scan over b repeats for every
+    son, without the per-top record), with its first sons staged in shared
+    memory; two rounds against the oracle, the second from the GPU's
+    snapshot."""
+    wl = fg.WORKLOADS[2].scaled(30000)
+    grid, forest = fg.make_grid(wl, 11), fg.make_forest(wl, 11)
+    rng = np.random.default_rng(11)
+    pin = forest["pin_layer"].copy()
+    on = pin >= 0
+    pin[on] = rng.integers(0, wl.L, int(on.sum())).astype(pin.dtype)
+    forest = dict(forest, pin_layer=pin)
+    # the case is there: several-son nodes with a pin above layer 0
+    par, ptr = forest["parent"], forest["net_ptr"]
+    net_of = np.repeat(np.arange(len(ptr) - 1), np.diff(ptr))
+    gp = np.where(par >= 0, ptr[net_of] + par, -1)
+    sons = np.bincount(gp[gp >= 0], minlength=len(par))
+    assert int(((sons >= 2) & (pin > 0) & (par >= 0)).sum()) > 100
+    assert int(((sons >= 2) & (pin > 0) & (par < 0)).sum()) > 100
+    m = la.LA_MODE_PLAIN if mode == "plain" else la.LA_MODE_BATCHED
+    a = _assigner(la, grid, forest)
+    D = H = None
+    for r in range(2):
+        st = a.assign_round(mode=m, reset=(r == 0), **la.DEFAULT_WEIGHTS)
+        layer, b, t = (x.cpu().numpy() for x in a.get_assignment())
+        Dg, Hg = (x.cpu().numpy() for x in a.get_state())
+        got = dict(layer=layer, b=b, t=t, D=Dg, H=Hg, J=a.get_net_cost().cpu().numpy(), stats=st)
+        ref = ref_round(grid, forest, la.DEFAULT_WEIGHTS, D=D, H=H)
+        assert_same_round(got, ref, f"{mode} round {r}")
+        D, H = Dg, Hg
+    a.close()
+
+
 @pytest.mark.parametrize("cfg,nets", [(2, 60000), (4, 20000), (5, 100000)])
 def test_batched_equals_plain(la, cfg, nets):
     wl = fg.WORKLOADS[cfg].scaled(nets)
