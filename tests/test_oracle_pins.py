@@ -35,9 +35,20 @@ def _net_assignment(forest, out, n):
     return lay, bt, W
 
 
-def _check_against_brute(wl, weights, seed, zero_via=False, max_seg=6, expect_exact=True):
+def _random_pin_layers(forest, L, seed):
+    """The forest with every pin moved to a random layer (the generator puts
+    them on layer 0)."""
+    pin = forest["pin_layer"].copy()
+    on = pin >= 0
+    pin[on] = np.random.default_rng(seed).integers(0, L, int(on.sum())).astype(pin.dtype)
+    return dict(forest, pin_layer=pin)
+
+
+def _check_against_brute(wl, weights, seed, zero_via=False, max_seg=6, expect_exact=True, pins_random=False):
     grid = fg.make_grid(wl, seed)
     forest = fg.make_forest(wl, seed)
+    if pins_random:
+        forest = _random_pin_layers(forest, wl.L, seed)
     if zero_via:
         grid["via_r"] = np.zeros_like(grid["via_r"])
     ww = dict(W_ALL, **weights)
@@ -75,6 +86,27 @@ def test_dp_equals_brute_force_when_lookahead_is_exact():
     """All unit R equal and zero via R: the distance-based r_est is the exact
     weighted upstream resistance, so f' orders candidates exactly (Sec. III-D)."""
     _check_against_brute(tiny(unit_r=(3.0, 3.0, 3.0, 3.0)), dict(w_d=5e-3), seed=12, zero_via=True)
+
+
+def test_dp_equals_brute_force_with_pins_on_upper_layers():
+    """Every pin on a random layer: a node with a pin above layer 0 has several
+    stack bottoms, and the root's junction sits above layer 0.  Exact cases:
+    w_d = 0 (separable) and the exact look-ahead."""
+    wl = tiny()
+    forest = _random_pin_layers(fg.make_forest(wl, 14), wl.L, 14)
+    # the shapes are there among the small nets: several-son nodes and roots
+    # with a pin above layer 0
+    nets = [n for n in br.nets_of(forest) if n.m - 1 <= 6]
+    multi = sum(1 for n in nets for v in range(n.m)
+                if n.pin_layer[v] > 0 and sum(1 for u in range(n.m) if n.parent[u] == v) >= 2)
+    assert multi >= 20
+    _check_against_brute(wl, dict(w_d=0.0), seed=14, pins_random=True)
+    _check_against_brute(tiny(unit_r=(3.0, 3.0, 3.0, 3.0)), dict(w_d=5e-3), seed=15, zero_via=True,
+                         pins_random=True)
+    # and with via R and a strong delay weight (the pin's via delay term is
+    # live): J(brute) <= J(DP), and the DP's J is the cost of its own assignment
+    _check_against_brute(tiny(pin_a=3, pin_b=5, num_nets=250, unit_r=(40.0, 30.0, 2.0, 1.0)),
+                         dict(w_d=0.05, w_cong=1e-3), seed=16, max_seg=7, expect_exact=False, pins_random=True)
 
 
 def test_dp_equals_brute_force_on_single_segment_nets():
