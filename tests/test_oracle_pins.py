@@ -218,6 +218,13 @@ def test_eq4_weights_and_rest_by_hand():
     r7 = r6 + k7 * 2 * rV        # 6 -> 7: vertical, 2 edges
     for n, want in {3: r3, 4: r4, 5: r5, 6: r6, 7: r7}.items():
         assert rho[loc[n]] == pytest.approx(want, rel=1e-15)
+    # only sinks carry a criticality: a large kappa on a node without a pin
+    # changes neither W nor r_est
+    nopin = forest["pin_layer"] < 0
+    assert nopin.any()
+    f2 = dict(forest, kappa=np.where(nopin, 5.0, forest["kappa"]))
+    W2, rho2 = oracle.weights_eq4(grid, f2)
+    assert np.array_equal(W2, W) and np.array_equal(rho2, rho)
 
 
 # ---------------------------------------------------------------------------
@@ -447,6 +454,81 @@ def test_sequential_batches_oracle():
     sel2 = batch[net_of] == 2
     assert np.array_equal(out["layer"][sel2], r1["layer"][sel2])
     assert not np.array_equal(r1["layer"], ref["layer"])  # the order changes the outcome
+
+
+def test_sequential_batches_from_a_previous_assignment():
+    """A round after a previous one, in sequential batches (Sec. III-A): batch
+    k sees the nets of batches < k on their new layers and every other net on
+    its previous layer, against the round's start history.  The map the last
+    batch sees is rebuilt here from that composite assignment by the demand
+    count alone."""
+    import forestgen as fg
+
+    wl = fg.WORKLOADS[2].scaled(3000)
+    grid, forest = fg.make_grid(wl, 6), fg.make_forest(wl, 6)
+    N = int(forest["num_nets"])
+    prev = oracle.assign_round(grid, forest)
+    # one batch from the previous state is the snapshot round
+    one = oracle.assign_round_batches(grid, forest, np.zeros(N, np.int32), D=prev["D"], H=prev["H"],
+                                      layer_prev=prev["layer"])
+    snap = oracle.assign_round(grid, forest, D=prev["D"], H=prev["H"])
+    for k in ("layer", "b", "t", "D", "H"):
+        assert np.array_equal(one[k], snap[k])
+    batch = np.random.default_rng(2).integers(0, 3, N).astype(np.int32)
+    r = oracle.assign_round_batches(grid, forest, batch, D=prev["D"], H=prev["H"], layer_prev=prev["layer"])
+    net_of = np.repeat(np.arange(N), np.diff(forest["net_ptr"]))
+    last = batch[net_of] == 2
+    seen = np.where(last, prev["layer"], r["layer"]).astype(np.int8)
+    D_seen, _, _ = oracle.demand(grid, forest, seen, r["b"], r["t"], np.zeros_like(prev["D"]))
+    pen = oracle.penalty(grid, D_seen, prev["H"], oracle.DEFAULT_WEIGHTS["hist_w"])
+    W, rho = oracle.weights_eq4(grid, forest)
+    out = oracle.dp(grid, forest, oracle.DEFAULT_WEIGHTS, pen, W, rho)
+    assert np.array_equal(out["layer"][last], r["layer"][last])
+    assert not np.array_equal(r["layer"], snap["layer"])  # the batches change the outcome
+
+
+def test_history_raises_the_penalty_of_a_round():
+    """Negotiation (Sec. I, Eq. 3's penalty with the history term): a 2-pin
+    straight net on an empty map takes the lowest horizontal layer (no vias);
+    with history on that layer's edges of the route it moves to the other
+    horizontal layer, and history elsewhere changes nothing."""
+    grid = simple_grid(12, 6, 4, (1.0, 1.0, 1.0, 1.0), (0.2, 0.2, 0.2, 0.2), (1.0, 1.0, 1.0), 0.05)
+    forest = forest_from_rows([(-1, 2, 3, 0, 0.0, 0.0), (0, 8, 3, 0, 1.0, 0.5)], r_drv=100.0)
+    E = oracle.num_edges(grid)
+    zero = np.zeros(E, np.int32)
+    base = oracle.assign_round(grid, forest, D=zero, H=zero)
+    assert int(base["layer"][1]) == 0
+    # layer 0 (H) is the first block of the public layout: row y = 3, edges x = 2 .. 7
+    per_row = grid["X"] - 1
+    H = zero.copy()
+    H[3 * per_row + 2: 3 * per_row + 8] = 50
+    moved = oracle.assign_round(grid, forest, D=zero, H=H)
+    assert int(moved["layer"][1]) == 2
+    H_off = zero.copy()
+    H_off[1 * per_row + 2: 1 * per_row + 8] = 50  # another row
+    same = oracle.assign_round(grid, forest, D=zero, H=H_off)
+    assert int(same["layer"][1]) == 0 and same["J"][0] == base["J"][0]
+
+
+def test_adjoint_weights_come_from_sinks_only():
+    """The adjoint weights (g = kappa at the sinks): W(v) = the sum of the
+    sinks' kappa below v, whatever kappa a node without a pin carries."""
+    forest, loc = _fig6_forest()
+    grid = simple_grid(8, 8, 4, (4.0, 3.0, 2.0, 1.0), (0.2, 0.2, 0.2, 0.2), (1.0, 1.0, 1.0), 0.05)
+    nopin = forest["pin_layer"] < 0
+    assert nopin.any()
+    f2 = dict(forest, kappa=np.where(nopin, 5.0, forest["kappa"]))
+    out = oracle.assign_round(grid, f2)
+    Ws, _ = oracle.adjoint_weights(grid, f2, out["layer"], out["b"], out["t"])
+    par = f2["parent"]
+    for v in range(len(par)):
+        want, stack = 0.0, [v]
+        while stack:  # the subtree of v, by its parent links
+            u = stack.pop()
+            if f2["pin_layer"][u] >= 0:
+                want += float(f2["kappa"][u])
+            stack += [c for c in range(len(par)) if par[c] == u]
+        assert Ws[v] == pytest.approx(want, rel=1e-15), v
 
 
 # ---------------------------------------------------------------------------
