@@ -170,6 +170,23 @@ def test_penalty_table_closed_form():
     assert T[0, 0, 0] == 0                                      # e^-32 2^24 rounds to 0
 
 
+def test_penalty_clamps_the_overflow_at_minus_64():
+    """The reading clamps k = D + 1 - C to [-64, 64]: with a large overflow
+    weight the entries near the low end are non-zero, ofw e^{k/2} 2^24 rounded
+    (1e8 e^-32 2^24 = 21.25, 1e8 e^-31.5 2^24 = 35.03), and every k below
+    -64 takes the k = -64 value."""
+    grid = simple_grid(4, 4, 2, (1, 1), (1, 1), (1,), 0.0)
+    grid["ofw"] = np.array([1e8, 1.0])
+    E = oracle.num_edges(grid)
+    cap = np.full(E, 200, np.int32)
+    D = np.zeros(E, np.int32)
+    D[1] = 136   # k = -63
+    D[2] = 135   # k = -64
+    grid["cap"] = cap
+    pen = oracle.penalty(grid, D, np.zeros(E, np.int32), hist_w=1.0)
+    assert pen[0] == 21 and pen[2] == 21 and pen[1] == 35   # k = -199 clamps to -64
+
+
 def test_penalty_values_and_saturation():
     grid = simple_grid(3, 3, 2, (1, 1), (1, 1), (1,), 0.0)
     E = oracle.num_edges(grid)
@@ -272,6 +289,14 @@ def test_demand_invariants():
     assert st["relu_overflow"] == np.maximum(over, 0).sum()
     s = np.where(grid["cap"] > 0, 0.5, 1.5)
     assert st["tof"] == pytest.approx(np.sum(np.exp(s * over)), rel=1e-12)
+    # Eq. 3 is linear in the per-layer overflow weights: the totals with one
+    # layer weighted at a time, scaled and summed, give the total of any weights
+    w = np.linspace(0.5, 3.0, L)
+    tof_w = oracle.demand(grid | dict(ofw=w), forest, out["layer"], out["b"], out["t"], H0)[2]["tof"]
+    parts = [oracle.demand(grid | dict(ofw=np.eye(L)[l]), forest, out["layer"], out["b"], out["t"], H0)[2]["tof"]
+             for l in range(L)]
+    assert tof_w == pytest.approx(float(np.dot(w, parts)), rel=1e-12)
+    assert max(parts) < st["tof"]
 
 
 # ---------------------------------------------------------------------------
