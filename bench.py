@@ -702,14 +702,34 @@ def cpu_baseline(wl, grid, forest, budget_s: float):
     threads = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     return ({"value": M / t, "unit": "nets/s", "cores": threads, "kind": "oracle",
              "sample": f"first {M} of {wl.num_nets} nets, 1 round (penalty + DP + backtrack + demand + adjoint "
-                       f"reweighting) of {wl.name}, {t:.1f} s"}, out)
+                       f"reweighting) of {wl.name}, {t:.1f} s",
+             "hardware_concurrency": os.cpu_count(), "affinity": threads,
+             "single_thread": oracle_single_thread()}, out)
 
 
-def _time_oracle_round(grid, forest, keep=False):
+def oracle_single_thread(nets2: int = 20000) -> dict:
+    """The oracle on one thread: config 1 whole, and the first `nets2` nets
+    of config 2 (one round plus the adjoint, as above), nets/s."""
+    import numpy as np
+
+    import forestgen as fg
+
+    res = {}
+    for w, n in ((fg.WORKLOADS[1], None), (fg.WORKLOADS[2], nets2)):
+        grid, forest = fg.make_grid(w, 0), fg.make_forest(w, 0)
+        if n is not None and n < w.num_nets:
+            forest = fg.subset_forest(forest, np.arange(n))
+        t = _time_oracle_round(grid, forest, threads=1)
+        res[w.name] = {"nets": int(forest["num_nets"]), "s": round(t, 3),
+                       "nets_per_s": round(int(forest["num_nets"]) / t, 1)}
+    return res
+
+
+def _time_oracle_round(grid, forest, keep=False, threads=0):
     import oracle
 
     t0 = time.perf_counter()
-    out = oracle.assign_round(grid, forest, oracle.DEFAULT_WEIGHTS)
+    out = oracle.assign_round(grid, forest, oracle.DEFAULT_WEIGHTS, threads=threads)
     oracle.adjoint_weights(grid, forest, out["layer"], out["b"], out["t"])
     t = time.perf_counter() - t0
     return (t, out) if keep else t
